@@ -1,0 +1,378 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms from the paper's appendix, textbook
+optics, brute force, or an independent quadrature. None needs a GPU.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_23412_gb300 import scenes
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --- Philox ------------------------------------------------------------------
+
+def test_philox_known_answers():
+    """Random123 / SC'11 known-answer vectors for Philox-4x32-10."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox_kat.txt")) if not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+# --- reciprocal estimator (Sec. 4.2, Appendix) --------------------------------
+
+# fn 0: f = 1 + sin(2 pi x)/2, q uniform: int f = 1, max f/q = 1.5
+# fn 1: f = 3x^2, q uniform: int f = 1, max f/q = 3
+# fn 2: f = 3x^2, q = (1 + 2x)/2: int f = 1, max f/q = 2
+CASES = [(0, 1.5), (0, 3.0), (0, 1.0), (0, 0.6), (1, 3.0), (1, 2.0), (2, 2.0), (2, 1.2)]
+
+
+@pytest.mark.parametrize("fn,B", CASES)
+def test_reciprocal_mean_is_one_over_integral(fn, B):
+    """App. "Expectation": E[I~] = E[I] = 1 / int f, for B at, above and below
+    max f/q (signs and splitting), as long as (1/B) int f lies in (0, 2)."""
+    n = 200000
+    t, i, nodes, tr = O.recip_1d(fn, B, n, seed=11)
+    assert tr == 0
+    for x in (t, i):
+        se = x.std() / math.sqrt(n)
+        assert abs(x.mean() - 1.0) < 4 * se + 1e-12, (x.mean(), se)
+
+
+def _moments_g(fn, B, m=2_000_000):
+    """E[g], E[g^2] by midpoint quadrature (independent of the estimator)."""
+    x = (np.arange(m) + 0.5) / m
+    if fn == 0:
+        f, q = 1 + 0.5 * np.sin(2 * np.pi * x), np.ones_like(x)
+        g = 1 - f / (B * q)
+        return g.mean(), (g * g).mean()
+    if fn == 1:
+        g = 1 - 3 * x * x / B
+        return g.mean(), (g * g).mean()
+    q = 0.5 + x
+    g = 1 - 3 * x * x / (B * q)
+    return (g * q).mean(), (g * g * q).mean()
+
+
+@pytest.mark.parametrize("fn,B", [(0, 1.5), (0, 3.0), (1, 3.0), (2, 2.0)])
+def test_sign_estimator_is_geometric_when_B_is_max(fn, B):
+    """App. "Optimal value for B": with B >= max f/q, I = (#trials)/B with a
+    geometric trial count, C = 1/(1-q) and V[I] = q/(B - Bq)^2, q = E[g]."""
+    n = 300000
+    t, i, nodes, tr = O.recip_1d(fn, B, n, seed=5)
+    qg, _ = _moments_g(fn, B)
+    np.testing.assert_allclose(i, nodes / B, rtol=0, atol=1e-12)
+    c_exact = 1 / (1 - qg)
+    assert abs(nodes.mean() - c_exact) < 4 * nodes.std() / math.sqrt(n)
+    v_exact = qg / (B - B * qg) ** 2
+    assert abs(i.var() / v_exact - 1) < 0.03
+
+
+@pytest.mark.parametrize("fn,B", [(0, 1.5), (0, 3.0), (1, 3.0), (2, 2.0)])
+def test_main_estimator_variance_closed_form(fn, B):
+    """With B >= max f/q the estimator is a chain, I~ = (1 + S)/B with
+    S = sum of g over the visited nodes, and (from the chain recursion)
+    E[S] = e/(1-e), E[S^2] = (E[g^2] + 2 E[g^2] E[S]) / (1-e), e = E[g]."""
+    n = 300000
+    t, i, nodes, tr = O.recip_1d(fn, B, n, seed=9)
+    e, e2 = _moments_g(fn, B)
+    es = e / (1 - e)
+    es2 = (e2 + 2 * e2 * es) / (1 - e)
+    v_exact = (es2 - es * es) / (B * B)
+    assert abs(t.var() / v_exact - 1) < 0.03
+
+
+@pytest.mark.parametrize("fn,B", CASES)
+def test_main_estimator_beats_sign_estimator(fn, B):
+    """App. "Comparison between I and I~": V[I~] <= V[I]."""
+    t, i, nodes, tr = O.recip_1d(fn, B, 100000, seed=3)
+    assert t.var() <= i.var() * 1.001
+
+
+def test_estimator_diverges_outside_convergence_domain():
+    """App. "Convergence Condition": (1/B) int f must lie in (0, 2); at
+    B = 0.45 (ratio 2.2) the splitting tree grows without bound and hits
+    the node cap."""
+    t, i, nodes, tr = O.recip_1d(0, 0.45, 200, seed=1, cap=1 << 12)
+    assert tr > 20
+
+
+# --- materials -------------------------------------------------------------------
+
+def _sphere_grid(nt=240, npf=480):
+    th = (np.arange(nt) + 0.5) / nt * np.pi
+    ph = (np.arange(npf) + 0.5) / npf * 2 * np.pi
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    d = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)
+    dw = (np.sin(T) * (np.pi / nt) * (2 * np.pi / npf)).reshape(-1)
+    return d, dw
+
+
+MATS = {
+    "lambert": scenes.material(scenes.LAMBERT, (0.6, 0.6, 0.6)),
+    "conductor": scenes.material(scenes.CONDUCTOR, (0.9, 0.9, 0.9), rough=0.5),
+    "dielectric": scenes.material(scenes.DIELECTRIC, (1, 1, 1), rough=0.5, ior=1.5),
+}
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("side", [1, -1])
+def test_bsdf_sampling_matches_quadrature(name, side):
+    """The sampler and its pdf are consistent and the pdf integrates to the
+    sampler's success rate; E[f |cos| / pdf] equals the quadrature of
+    int f |cos| dw (radiance leaving toward w_g under unit illumination)."""
+    mat = MATS[name]
+    if name == "conductor" and side < 0:
+        pytest.skip("one-sided")
+    n = np.array([0.0, 0.0, 1.0])
+    wg = np.array([0.5, 0.1, side * 0.7])
+    wg /= np.linalg.norm(wg)
+    d, dw = _sphere_grid()
+    pdfs = np.array([O.bsdf_pdf(mat, n, wg, w) for w in d])
+    fs = np.array([O.bsdf_eval(mat, n, w, wg)[0] for w in d])
+    quad_pdf = (pdfs * dw).sum()
+    quad_alb = (fs * np.abs(d[:, 2]) * dw).sum()
+    rng = np.random.default_rng(1)
+    u = rng.random((20000, 3))
+    est, ok = [], 0
+    for a, b, c in u:
+        good, ws = O.bsdf_sample(mat, n, wg, a, b, c)
+        if not good:
+            est.append(0.0)
+            continue
+        ok += 1
+        p = O.bsdf_pdf(mat, n, wg, ws)
+        assert p > 0
+        est.append(O.bsdf_eval(mat, n, ws, wg)[0] * abs(ws[2]) / p)
+    est = np.array(est)
+    assert abs(quad_pdf - ok / len(u)) < 0.01
+    assert abs(est.mean() - quad_alb) < 4 * est.std() / math.sqrt(len(est)) + 2e-3
+
+
+def test_bsdf_reciprocity():
+    """Helmholtz reciprocity for reflection; generalized reciprocity
+    f(a,b)/eta_b^2 = f(b,a)/eta_a^2 for refraction (Veach thesis Sec. 5.2)."""
+    rng = np.random.default_rng(0)
+    n = np.array([0.0, 0.0, 1.0])
+    for name in ("conductor", "dielectric", "lambert"):
+        mat = MATS[name]
+        for _ in range(200):
+            a, b = rng.normal(size=3), rng.normal(size=3)
+            a, b = a / np.linalg.norm(a), b / np.linalg.norm(b)
+            if name == "conductor":
+                a[2], b[2] = abs(a[2]), abs(b[2])
+            fab = O.bsdf_eval(mat, n, a, b)[0]
+            fba = O.bsdf_eval(mat, n, b, a)[0]
+            ea = 1.0 if a[2] > 0 else 1.5
+            eb = 1.0 if b[2] > 0 else 1.5
+            if name == "dielectric":
+                np.testing.assert_allclose(fab / eb ** 2, fba / ea ** 2, rtol=1e-9, atol=1e-12)
+            else:
+                np.testing.assert_allclose(fab, fba, rtol=1e-9, atol=1e-12)
+
+
+def test_dielectric_smooth_limit_textbook_fresnel():
+    """Near-smooth dielectric (roughness 0.01): at normal incidence the
+    reflected share is ((n-1)/(n+1))^2 = 0.04 and the transmitted radiance
+    is scaled by (1 - 0.04) / n^2; beyond the critical angle asin(1/1.5)
+    inside the glass everything is reflected (total internal reflection)."""
+    mat = scenes.material(scenes.DIELECTRIC, (1, 1, 1), rough=0.01, ior=1.5)
+    n = np.array([0.0, 0.0, 1.0])
+    rng = np.random.default_rng(2)
+    refl, trans = [], []
+    for a, b, c in rng.random((20000, 3)):
+        good, ws = O.bsdf_sample(mat, n, n.copy(), a, b, c)
+        val = O.bsdf_eval(mat, n, ws, n)[0] * abs(ws[2]) / O.bsdf_pdf(mat, n, n, ws) if good else 0.0
+        (refl if ws[2] > 0 else trans).append(val)
+    tot = np.array(refl + trans)
+    assert abs(len(refl) / len(tot) - 0.04) < 0.006
+    assert abs(tot.mean() - (0.04 + 0.96 / 2.25)) < 0.01
+    wg = np.array([math.sin(math.radians(50)), 0, -math.cos(math.radians(50))])
+    for a, b, c in rng.random((2000, 3)):
+        good, ws = O.bsdf_sample(mat, n, wg, a, b, c)
+        if good:
+            assert ws[2] < 0  # stays inside
+
+
+def test_conductor_smooth_limit_is_F0():
+    mat = scenes.material(scenes.CONDUCTOR, (0.8, 0.8, 0.8), rough=0.01)
+    n = np.array([0.0, 0.0, 1.0])
+    rng = np.random.default_rng(3)
+    vals = []
+    for a, b, c in rng.random((5000, 3)):
+        good, ws = O.bsdf_sample(mat, n, n.copy(), a, b, c)
+        vals.append(O.bsdf_eval(mat, n, ws, n)[0] * ws[2] / O.bsdf_pdf(mat, n, n, ws) if good else 0)
+    assert abs(np.mean(vals) - 0.8) < 0.005
+
+
+# --- ray queries --------------------------------------------------------------
+
+def test_closest_hit_single_triangle_analytic():
+    sc = scenes.pin_square_light(a=0.1, h=0.5)
+    o = O.Oracle(sc)
+    # straight down through the light quad's centre: light first at t = 0.5
+    out = o.closest(np.array([[0.0, 1.0, 0.0]]), np.array([[0.0, -1.0, 0.0]]))
+    assert out[0, 0] in (0, 1) and abs(out[0, 1] - 0.5) < 1e-12
+    # below the light, onto the tiny specular triangle at the origin
+    out = o.closest(np.array([[0.0, 0.3, 0.0]]), np.array([[0.0, -1.0, 0.0]]))
+    assert out[0, 0] == 2 and abs(out[0, 1] - 0.3) < 1e-12
+
+
+def test_hierarchy_matches_brute_force():
+    sc = scenes.cornell(8, 8)
+    o = O.Oracle(sc)
+    rng = np.random.default_rng(4)
+    orig = rng.uniform(0.05, 0.95, (4000, 3))
+    d = rng.normal(size=(4000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    a = o.closest(orig, d)
+    O.lib().or_set_brute(o.h, 1)
+    b = o.closest(orig, d)
+    O.lib().or_set_brute(o.h, 0)
+    np.testing.assert_array_equal(a, b)
+    p1, p2 = rng.uniform(0.05, 0.95, (4000, 3)), rng.uniform(0.05, 0.95, (4000, 3))
+    oa = o.occluded(p1, p2, -1, -1)
+    O.lib().or_set_brute(o.h, 1)
+    ob = o.occluded(p1, p2, -1, -1)
+    np.testing.assert_array_equal(oa, ob)
+    assert 0 < oa.mean() < 1
+
+
+# --- incomplete sub-path density (Sec. 5.2, Eq. reciprocalFinal) ------------------
+
+def _corner(A, B, h):
+    a, b = math.hypot(A, h), math.hypot(B, h)
+    return 0.5 * (A / a * math.atan(B / a) + B / b * math.atan(A / b))
+
+
+def test_reciprocal_of_incomplete_pdf_square_light_closed_form():
+    """L S, u = 1: P(y_1) = int p_L (cos0/pi) cos1/d^2 dA(y_0). For a point
+    under the centre of a square light of half-size a at height h this is
+    (1/(pi A)) * 4 * int_0^a int_0^a h^2 / (x^2+y^2+h^2)^2 (the parallel
+    point-to-rectangle form factor integral). The estimator's mean must be
+    1/P."""
+    a, h = 0.1, 0.5
+    sc = scenes.pin_square_light(a=a, h=h)
+    o = O.Oracle(sc)
+    P = (1.0 / (4 * a * a)) * (1 / math.pi) * 4 * _corner(a, a, h)
+    e = O.Entry(2, 1 / 3, 1 / 3, 1, 0, -1, 0.0, 0.0)
+    f, q = o.entry_fq(e, 20000)
+    ratio = np.where(q > 0, f / np.where(q > 0, q, 1.0), 0.0)
+    assert abs(ratio.mean() - P) < 4 * ratio.std() / math.sqrt(len(ratio))
+    t, i, nodes, tr = o.entry_recip(e, B=1.2 * ratio.max(), n=40000)
+    assert tr == 0
+    assert abs(t.mean() - 1 / P) < 4 * t.std() / math.sqrt(len(t))
+    assert abs(i.mean() - 1 / P) < 4 * i.std() / math.sqrt(len(i))
+
+
+def test_reciprocal_of_incomplete_pdf_diffuse_control_vertex_quadrature():
+    """L D S, u = 1, h_c on the light: P = int over the floor of the light
+    tracer's densities (cosine emission, then cosine reflection) toward y_2,
+    evaluated here by a midpoint rule over the floor."""
+    sc = scenes.pin_floor_light(a=0.1, h=1.0, floor=1.0, ypos=(0.5, 0.3, 0.0))
+    o = O.Oracle(sc)
+    v = sc["verts"].astype(np.float64)[sc["tris"][0]]
+    H = v[0] + 0.5 * (v[1] - v[0]) + 0.5 * (v[2] - v[0])   # h_c on the light, barycentrics (0.5, 0.5)
+    Y = sc["verts"].astype(np.float64)[sc["tris"][4]].mean(0)
+    m = 600
+    xs = (np.arange(m) + 0.5) / m * 2 - 1
+    X, Z = np.meshgrid(xs, xs, indexing="ij")
+    y1 = np.stack([X, np.zeros_like(X), Z], -1)
+    dH = H - y1
+    dY = Y - y1
+    lH, lY = np.linalg.norm(dH, axis=-1), np.linalg.norm(dY, axis=-1)
+    cosH = dH[..., 1] / lH          # at the light (normal -y), toward y1
+    cos1H = dH[..., 1] / lH         # at the floor (normal +y), toward H
+    cos1Y = dY[..., 1] / lY
+    cosY = dY[..., 1] / lY          # Y faces -y
+    integrand = (cosH / np.pi) * cos1H / lH ** 2 * (cos1Y / np.pi) * cosY / lY ** 2
+    P = integrand.sum() * (2.0 / m) ** 2
+    # entry: y_{s-1} at the tiny triangle's centroid (index 4), h_c as above
+    e = O.Entry(4, 1 / 3, 1 / 3, 1, 1, 0, 0.5, 0.5)
+    f, q = o.entry_fq(e, 20000)
+    ratio = np.where(q > 0, f / np.where(q > 0, q, 1.0), 0.0)
+    assert abs(ratio.mean() - P) < 4 * ratio.std() / math.sqrt(len(ratio)) + 1e-3 * P
+    t, i, nodes, tr = o.entry_recip(e, B=1.2 * ratio.max(), n=20000)
+    assert tr == 0
+    assert abs(t.mean() - 1 / P) < 4 * t.std() / math.sqrt(len(t)) + 2e-3 / P
+
+
+# --- whole estimator ------------------------------------------------------------
+
+def _render_mean(sc, tab, n_iter, **kw):
+    o = O.Oracle(sc)
+    p = O.params(**kw)
+    film, st = o.render(p, o.tables(tab), 0, n_iter)
+    return film / n_iter, st
+
+
+def test_white_furnace_diffuse_enclosure():
+    """All six inward walls emit Le and reflect with albedo rho; the camera
+    sees Le * sum_{j<K} rho^j through paths of at most K segments, whatever
+    the mix of strategies (PT hits, NEE, subspace connections) and weights."""
+    rho, Le, K = 0.5, 1.0, 4
+    sc = scenes.furnace(rho=rho, Le=Le, W=6, H=6)
+    tab = scenes.random_tables(sc, KT=8, KS=8, KSp=4, KC=2)
+    img, st = _render_mean(sc, tab, 24, max_depth=K, M=300, M_p=300, proxy=1)
+    exact = Le * sum(rho ** j for j in range(K))
+    per = img.mean(1)
+    assert abs(per.mean() - exact) < 0.01 * exact
+    assert st["n_conn"] > 0
+
+
+def test_furnace_with_glass_sphere_converges_to_closed_form():
+    """A rough-glass sphere (roughness 0.1) inside the furnace does not change
+    the radiance Le/(1-rho) seen in the limit of long paths: refraction
+    preserves radiance up to eta^2 factors that cancel on exit; microfacet
+    energy loss at alpha = 0.01 is far below the tolerance."""
+    rho, Le, K = 0.5, 1.0, 24
+    sc = scenes.furnace(rho=rho, Le=Le, W=6, H=6, spheres=True)
+    tab = scenes.random_tables(sc, KT=8, KS=8, KSp=4, KC=2, B=50.0, mis=0.5)
+    img, st = _render_mean(sc, tab, 12, max_depth=K, M=200, M_p=100, proxy=0)
+    exact = Le / (1 - rho) * (1 - rho ** K)
+    assert abs(img.mean() - exact) < 0.02 * exact
+
+
+def test_proxy_on_off_and_path_tracing_agree_per_pixel():
+    """Unbiasedness (Sec. 4.1, 5.2): with independent seeds, proxy on,
+    proxy off, and plain PT+NEE give per-pixel means of a caustic scene that
+    agree within their standard errors (z-scores of an N(0,1) family)."""
+    sc = scenes.caustic_mini(8, 8)
+    o = O.Oracle(sc)
+    tab = scenes.random_tables(sc, KT=8, KS=8, KSp=4, KC=2)
+    tab = o.learn(O.params(M=300, M_p=300, max_depth=4), tab, 1000, 2, n_bsamples=64)
+    td = o.tables(tab)
+
+    def run(seed, n, **kw):
+        pp = O.params(seed=seed, M=300, M_p=300, max_depth=4, **kw)
+        vals, nproxy = [], 0
+        for it in range(n):
+            tri, bary = o.light_pass(pp, it)
+            r = o.iteration(pp, td, it, tri, bary)
+            vals.append(r["rgb"].mean(1))
+            nproxy += r["stats"]["n_proxy_ok"]
+        v = np.array(vals)
+        return v.mean(0), v.var(0, ddof=1) / n, nproxy
+
+    n = 2000
+    m_on, v_on, k_on = run(7, n, proxy=1)
+    m_off, v_off, _ = run(8, n, proxy=0)
+    m_pt, v_pt, _ = run(9, n, proxy=0, conn=0)
+    assert k_on > 500
+    for m, v in ((m_on, v_on), (m_off, v_off)):
+        den = np.sqrt(v + v_pt)
+        live = den > 0
+        z = (m[live] - m_pt[live]) / den[live]
+        assert np.abs(z).max() < 5.0
+        assert (z * z).mean() < 2.0
+        assert np.all(m[~live] == m_pt[~live])
