@@ -1,0 +1,155 @@
+/* proxybdpt -- C ABI of a GB300 (sm_103a) renderer for proxy-tracing BDPT.
+ *
+ * Method: "Proxy Tracing: Unbiased Reciprocal Estimation for Optimized
+ * Sampling in BDPT" (arXiv 2503.23412). The renderer estimates the pixel
+ * measurement I = int f(x) dmu(x) of the path-integral formulation (Sec. 3.1,
+ * Eq. path intergral) with a probabilistic-connection bidirectional path
+ * tracer (Sec. 3.2), adds the proxy strategy for light sub-paths that end on
+ * specular vertices (Sec. 5.1-5.2) weighted by the reciprocal estimator
+ * (Sec. 4.2, Appendix Alg. "Estimator I~") and the MIS weight for estimated
+ * pdfs (Sec. 5.4, Eq. MIS_1), with subspace-based selection (Sec. 5.5).
+ *
+ * Conventions for every entry point:
+ *  - Returns pb_status; PB_OK on success. No call aborts the process; on an
+ *    error pb_last_error() returns a one-line description.
+ *  - Pointers named host_* are host memory owned by the caller; the library
+ *    copies from/to them before returning. The context owns all device memory
+ *    it allocates and frees it in pb_destroy().
+ *  - Calls are synchronous with respect to the host on return (work is issued
+ *    on the context's stream and waited for), unless stated otherwise.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PROXYBDPT_H
+#define PROXYBDPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pb_ctx pb_ctx;
+
+typedef enum {
+    PB_OK = 0,
+    PB_ERR_ARG = 1,        /* invalid argument or size */
+    PB_ERR_OOM = 2,        /* device allocation failed */
+    PB_ERR_CUDA = 3,       /* a CUDA call failed */
+    PB_ERR_TIMEOUT = 4,    /* a bounded device loop gave up */
+    PB_ERR_TRUNCATED = 5,  /* a reciprocal estimate hit its node cap (result still written) */
+    PB_ERR_STATE = 6       /* call made in the wrong order (e.g. render before scene upload) */
+} pb_status;
+
+/* Scene (Sec. 3.1: surfaces, BSDFs, emitters, camera). Arrays are read
+ * during the call only. Layout (float32 / int32, C order):
+ *   verts[nv*3], uvs[nv*2] (may be NULL), tris[nt*3], tri_mat[nt],
+ *   mats[nm*12]: kind(0 Lambert, 1 GGX conductor, 2 GGX dielectric),
+ *     colour rgb, roughness (alpha = r^2; conductor/dielectric with r < 0.2
+ *     is a specular vertex, Sec. 1 footnote), ior, Le rgb (front side),
+ *     textured flag, 2 reserved;
+ *   tex[tex_h*tex_w*3] emission texture (may be NULL when tex_w == 0);
+ *   cam[12]: position, look-at, up, vertical fov (degrees), width, height.
+ * Errors: PB_ERR_ARG on empty or inconsistent sizes, out-of-range indices. */
+typedef struct {
+    int nv, nt, nm;
+    const float *verts;
+    const float *uvs;
+    const int32_t *tris;
+    const int32_t *tri_mat;
+    const float *mats;
+    int tex_w, tex_h;
+    const float *tex;
+    const float *cam;
+} pb_scene_desc;
+
+/* Frozen subspace tables (Sec. 5.4-5.5, Eq. subspaceApproximate):
+ * centroids of the eye (T), light (S), specular (S') and control (C)
+ * subspaces in bbox-normalised feature space (T, S: position, normal flipped
+ * toward the incident direction, incident direction; S': position, normal;
+ * C: position), the selection matrices Gamma[T,S] and Gamma'[T,S'], the
+ * per-cell bound B(u,S',C) and MIS scale 1/(E[R^2] Pbar) (C = KC means "no
+ * control vertex"), and the per-tile proxy probability. All float32. */
+typedef struct {
+    int KT, KS, KSp, KC;
+    const float *bbox_lo, *bbox_hi;   /* 3 each */
+    const float *cent_T;              /* KT*9 */
+    const float *cent_S;              /* KS*9 */
+    const float *cent_Sp;             /* KSp*6 */
+    const float *cent_C;              /* KC*3 */
+    const float *gamma_conn;          /* KT*KS, rows positive */
+    const float *gamma_proxy;         /* KT*KSp */
+    const float *B_tab;               /* 4*KSp*(KC+1), > 0 */
+    const float *mis_tab;             /* 4*KSp*(KC+1), >= 0 */
+    int tile, grid_w, grid_h;
+    const float *pi_grid;             /* grid_h*grid_w, in [0,1] */
+} pb_tables_desc;
+
+/* Render configuration. Iterations [iter0, iter0 + spp) are traced; each
+ * iteration is one sample per pixel (Sec. 6: one iteration = 1 spp). */
+typedef struct {
+    uint32_t seed;
+    int spp;
+    int max_depth;     /* maximum number of path segments */
+    int M;             /* light sub-paths per iteration (paper: 10,000) */
+    int M_p;           /* light sub-paths scanned for incomplete sub-paths */
+    int repeats;       /* reciprocal estimates averaged (paper: 5) */
+    int proxy;         /* 1: proxy strategy on */
+    int conn;          /* 1: subspace connections on (0 leaves PT + NEE) */
+    int trial_cap;     /* node cap per reciprocal estimate (e.g. 65536) */
+    int iter0;
+    int batch;         /* iterations in flight per launch wave (0: automatic) */
+} pb_config;
+
+typedef struct {
+    double ms;                 /* device time of the call */
+    double mpaths_per_s;       /* W*H*spp / seconds */
+    int64_t n_entries;         /* incomplete light sub-paths estimated */
+    int64_t n_truncated;       /* estimates that hit trial_cap */
+    int64_t n_nodes;           /* estimator nodes evaluated (trials) */
+    int64_t n_conn, n_proxy, n_proxy_ok;
+    int64_t n_node_fetch, n_tri_test;   /* traversal counters (when enabled) */
+} pb_stats;
+
+pb_status pb_create(pb_ctx **out, int device, void *cuda_stream /* NULL: own stream */);
+void pb_destroy(pb_ctx *ctx);
+const char *pb_last_error(const pb_ctx *ctx);
+
+/* Builds the BVH on the host (binned SAH) and uploads scene and BVH. */
+pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *scene);
+pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *tables);
+
+/* Traces cfg->spp iterations and adds them to the film. PB_ERR_TRUNCATED
+ * if any estimate hit the cap (the film is still updated). */
+pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats_or_null);
+pb_status pb_film_clear(pb_ctx *ctx);
+/* Mean radiance per pixel, W*H*3 floats (host_rgb must hold n_floats). */
+pb_status pb_film_readback(pb_ctx *ctx, float *host_rgb, size_t n_floats);
+/* Device pointer of the film sum (W*H*3 float32) and its iteration count. */
+pb_status pb_film_device(pb_ctx *ctx, float **dev_sum, int64_t *iterations);
+
+/* ---- queries used by the parity tests ------------------------------------ */
+/* Closest hits: host_rays n*7 (origin, direction, skip tri); host_hits n*4
+ * (tri or -1, t, b1, b2). Stackless BVH traversal. */
+pb_status pb_trace(pb_ctx *ctx, const float *host_rays, int n, float *host_hits);
+/* Occlusion of segments a->b: host_seg n*8 (a, b, skip_a, skip_b). */
+pb_status pb_occluded(pb_ctx *ctx, const float *host_seg, int n, int32_t *host_out);
+/* Light pass of one iteration: geometry [M][max_depth-1] (tri, b1 b2). */
+pb_status pb_light_pass(pb_ctx *ctx, const pb_config *cfg, int iteration, int32_t *host_tri,
+                        float *host_bary);
+/* One iteration on given light geometry: pool build, reciprocal estimation
+ * (or host_rhat_override if not NULL: M*(max_depth-1) doubles of which the
+ * first n_entries, in (light path, vertex) order, are used), eye pass.
+ * Triangle indices must lie in [-1, nt) (PB_ERR_ARG otherwise). Outputs per
+ * pixel: this sample's radiance (W*H*3) and path signature (W*H); per entry
+ * up to cap: estimate, signature, nodes. */
+pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const int32_t *host_tri,
+                       const float *host_bary, const double *host_rhat_override,
+                       float *host_pix_rgb, uint32_t *host_pix_sig, int cap, int *n_entries,
+                       float *host_entry_rhat, uint32_t *host_entry_sig, float *host_entry_nodes,
+                       pb_stats *stats_or_null);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,714 @@
+// C ABI of the renderer (declared in include/proxybdpt.h): context, scene and
+// table upload, the render loop over iteration waves, film readback, and the
+// single-stage entry points the parity tests drive.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/proxybdpt.h"
+#include "pb_bvh.h"
+#include "pb_kernels.h"
+
+struct pb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 1;
+    std::string err;
+    std::vector<void *> scene_mem, table_mem, pool_mem;
+    bool has_scene = false, has_tables = false;
+    DScene S{};
+    DTables T{};
+    float3 bbox_lo{}, bbox_hi{};
+    // pool capacity
+    Pool B{};
+    int cap_slots = 0, cap_ML = 0, cap_rep = 0, cap_KT = 0, cap_KS = 0, cap_KSp = 0;
+    float4 *Lbuf = nullptr;
+    uint32_t *sigbuf = nullptr;
+    int cap_Lslots = 0;
+    float *film = nullptr;
+    int64_t film_iters = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+pb_status fail(pb_ctx *c, pb_status s, const std::string &m) {
+    if (c) c->err = m;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? PB_ERR_OOM : PB_ERR_CUDA,  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(std::vector<void *> &owner, T **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    owner.push_back(q);
+    *p = (T *)q;
+    return cudaSuccess;
+}
+
+void free_all(std::vector<void *> &v) {
+    for (void *p : v) cudaFree(p);
+    v.clear();
+}
+
+template <class T>
+cudaError_t upload(pb_ctx *c, std::vector<void *> &owner, T **dst, const T *src, size_t n) {
+    cudaError_t e = dalloc(owner, dst, n);
+    if (e != cudaSuccess) return e;
+    if (n) e = cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+    return e;
+}
+
+pb_status ensure_pool(pb_ctx *ctx, int slots, int ML, int repeats, int npix) {
+    const DTables &T = ctx->T;
+    if (slots <= ctx->cap_slots && ML <= ctx->cap_ML && repeats <= ctx->cap_rep && T.KT <= ctx->cap_KT &&
+        T.KS <= ctx->cap_KS && T.KSp <= ctx->cap_KSp && ctx->Lbuf && slots <= ctx->cap_Lslots &&
+        ctx->B.ML == ML) {
+        // Lbuf also depends on npix; it is sized at scene upload time
+        (void)npix;
+        return PB_OK;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_all(ctx->pool_mem);
+    Pool &B = ctx->B;
+    B = Pool{};
+    B.slots = slots;
+    B.ML = ML;
+    size_t n = (size_t)slots * ML;
+    auto &o = ctx->pool_mem;
+    CK(dalloc(o, &B.gtri, n));
+    CK(dalloc(o, &B.gbary, n));
+    CK(dalloc(o, &B.vpos, n));
+    CK(dalloc(o, &B.vnrm, n));
+    CK(dalloc(o, &B.vwl, n));
+    CK(dalloc(o, &B.valpha, n));
+    CK(dalloc(o, &B.vmis, n));
+    CK(dalloc(o, &B.vlabel, n));
+    CK(dalloc(o, &B.elabel, n));
+    CK(dalloc(o, &B.einfo, n));
+    CK(dalloc(o, &B.pool_idx, n));
+    CK(dalloc(o, &B.bitems, n));
+    CK(dalloc(o, &B.ent_idx, n));
+    CK(dalloc(o, &B.eitems, n));
+    CK(dalloc(o, &B.bstart, (size_t)slots * (T.KS + 1)));
+    CK(dalloc(o, &B.estart, (size_t)slots * (T.KSp + 1)));
+    CK(dalloc(o, &B.npool, (size_t)slots));
+    CK(dalloc(o, &B.nent, (size_t)slots));
+    CK(dalloc(o, &B.cdfC, (size_t)slots * T.KT * T.KS));
+    CK(dalloc(o, &B.ZC, (size_t)slots * T.KT));
+    CK(dalloc(o, &B.cdfP, (size_t)slots * T.KT * T.KSp));
+    CK(dalloc(o, &B.ZP, (size_t)slots * T.KT));
+    CK(dalloc(o, &B.rep, n * repeats));
+    CK(dalloc(o, &B.repn, n * repeats));
+    CK(dalloc(o, &B.reptr, n * repeats));
+    CK(dalloc(o, &B.rhat, n));
+    CK(dalloc(o, &B.esig, n));
+    CK(dalloc(o, &B.work, (size_t)slots + 2));
+    CK(dalloc(o, &B.scratch, 2 * n));
+    CK(dalloc(o, &B.counters, (size_t)CNT_N));
+    CK(dalloc(o, &ctx->Lbuf, (size_t)slots * ctx->S.W * ctx->S.H));
+    CK(dalloc(o, &ctx->sigbuf, (size_t)slots * ctx->S.W * ctx->S.H));
+    ctx->cap_slots = slots;
+    ctx->cap_ML = ML;
+    ctx->cap_rep = repeats;
+    ctx->cap_KT = T.KT;
+    ctx->cap_KS = T.KS;
+    ctx->cap_KSp = T.KSp;
+    ctx->cap_Lslots = slots;
+    return PB_OK;
+}
+
+pb_status check_cfg(pb_ctx *ctx, const pb_config *c) {
+    if (!ctx->has_scene) return fail(ctx, PB_ERR_STATE, "no scene uploaded");
+    if (!ctx->has_tables) return fail(ctx, PB_ERR_STATE, "no tables uploaded");
+    if (!c) return fail(ctx, PB_ERR_ARG, "null config");
+    if (c->max_depth < 2 || c->max_depth > 16) return fail(ctx, PB_ERR_ARG, "max_depth must be in [2, 16]");
+    if (c->M < 1 || c->M > (1 << 22)) return fail(ctx, PB_ERR_ARG, "M out of range");
+    if (c->repeats < 1 || c->repeats > 8) return fail(ctx, PB_ERR_ARG, "repeats must be in [1, 8]");
+    if (c->trial_cap < 1) return fail(ctx, PB_ERR_ARG, "trial_cap must be positive");
+    if (c->spp < 0) return fail(ctx, PB_ERR_ARG, "spp must be >= 0");
+    return PB_OK;
+}
+
+KParams kparams(const pb_ctx *ctx, const pb_config *c) {
+    KParams P;
+    P.seed = c->seed;
+    P.max_depth = c->max_depth;
+    P.M = c->M;
+    P.M_p = std::min(std::max(c->M_p, 0), c->M);
+    P.repeats = c->repeats;
+    P.proxy = c->proxy ? 1 : 0;
+    P.conn = c->conn ? 1 : 0;
+    P.trial_cap = c->trial_cap;
+    P.L = c->max_depth - 1;
+    P.npix = ctx->S.W * ctx->S.H;
+    return P;
+}
+
+pb_status run_wave(pb_ctx *ctx, const KParams &P, int slots, uint32_t iter_base, bool with_light, bool with_recip,
+                   uint32_t *sig) {
+    if (with_light) launch_light_pass(ctx->S, P, ctx->B, slots, iter_base, ctx->stream);
+    launch_pool_build(ctx->S, ctx->T, P, ctx->B, slots, ctx->stream);
+    if (with_recip) launch_recip(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->num_sms, ctx->stream);
+    launch_eye(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->Lbuf, sig, ctx->stream);
+    CK(cudaGetLastError());
+    return PB_OK;
+}
+
+// Structural check of a built hierarchy before any kernel walks it: every
+// child index in range, every triangle in exactly one leaf, parent/sibling
+// links consistent, depth small enough for the 64-bit traversal trail.
+bool bvh_valid(const PbBvh &b, int nn, int nt, std::string &why) {
+    std::vector<int> seen(nt, 0);
+    std::vector<int> depth(nn, -1);
+    depth[0] = 0;
+    std::vector<int> stack{0};
+    int visited = 0;
+    while (!stack.empty()) {
+        int n = stack.back();
+        stack.pop_back();
+        ++visited;
+        const int32_t *w = reinterpret_cast<const int32_t *>(&b.nodes[(size_t)n * 16]);
+        int32_t ch[2] = {w[3], w[7]};
+        for (int k = 0; k < 2; ++k) {
+            int32_t c = ch[k];
+            if (c >= 0) {
+                if (c >= nn || c == 0 || depth[c] != -1) { why = "bad child index"; return false; }
+                if (b.parent[c] != n) { why = "parent link"; return false; }
+                depth[c] = depth[n] + 1;
+                if (depth[c] > 62) { why = "hierarchy deeper than 62"; return false; }
+                int32_t o = ch[1 - k];
+                if (o >= 0 ? b.sibling[c] != o : b.sibling[c] != -1) { why = "sibling link"; return false; }
+                stack.push_back(c);
+            } else {
+                int v = -c - 1, first = v >> 4, cnt = v & 15;
+                if (first < 0 || first + cnt > nt) { why = "leaf range"; return false; }
+                for (int i = first; i < first + cnt; ++i) {
+                    int t = b.order[i];
+                    if (t < 0 || t >= nt || seen[t]++) { why = "triangle order"; return false; }
+                }
+            }
+        }
+    }
+    if (visited != nn) { why = "unreachable nodes"; return false; }
+    for (int t = 0; t < nt; ++t)
+        if (seen[t] != 1) { why = "triangle missing from leaves"; return false; }
+    return true;
+}
+
+void read_counters(pb_ctx *ctx, pb_stats *st) {
+    unsigned long long c[CNT_N];
+    cudaMemcpy(c, ctx->B.counters, sizeof(c), cudaMemcpyDeviceToHost);
+    st->n_entries = (int64_t)c[CNT_ENTRIES];
+    st->n_truncated = (int64_t)c[CNT_TRUNC];
+    st->n_nodes = (int64_t)c[CNT_NODES];
+    st->n_conn = (int64_t)c[CNT_CONN];
+    st->n_proxy = (int64_t)c[CNT_PROXY];
+    st->n_proxy_ok = (int64_t)c[CNT_PROXY_OK];
+    st->n_node_fetch = (int64_t)c[CNT_NFETCH];
+    st->n_tri_test = (int64_t)c[CNT_TTEST];
+}
+
+// ---- debug kernels --------------------------------------------------------
+__global__ void k_trace(DScene S, const float *rays, int n, float *hits, int count, unsigned long long *counters) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float *r = rays + 7 * (size_t)i;
+    TravCount tc{0, 0};
+    Hit h = count ? closest_hit<true>(S, f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]), (int)r[6], &tc)
+                  : closest_hit<false>(S, f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]), (int)r[6]);
+    hits[4 * (size_t)i] = (float)h.tri;
+    hits[4 * (size_t)i + 1] = h.tri >= 0 ? h.t : -1.0f;
+    hits[4 * (size_t)i + 2] = h.b1;
+    hits[4 * (size_t)i + 3] = h.b2;
+    if (count) {
+        atomicAdd(&counters[CNT_NFETCH], (unsigned long long)tc.nodes);
+        atomicAdd(&counters[CNT_TTEST], (unsigned long long)tc.tris);
+    }
+}
+
+__global__ void k_occ(DScene S, const float *seg, int n, int32_t *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float *r = seg + 8 * (size_t)i;
+    out[i] = occluded(S, f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]), (int)r[6], (int)r[7]) ? 1 : 0;
+}
+
+}  // namespace
+
+void launch_trace(const DScene &S, const float *rays, int n, float *hits, int count, unsigned long long *counters,
+                  cudaStream_t st) {
+    k_trace<<<(n + 127) / 128, 128, 0, st>>>(S, rays, n, hits, count, counters);
+}
+
+void launch_occluded(const DScene &S, const float *seg, int n, int32_t *out, cudaStream_t st) {
+    k_occ<<<(n + 127) / 128, 128, 0, st>>>(S, seg, n, out);
+}
+
+extern "C" {
+
+pb_status pb_create(pb_ctx **out, int device, void *cuda_stream) {
+    if (!out) return PB_ERR_ARG;
+    *out = nullptr;
+    pb_ctx *ctx = new pb_ctx();
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return PB_ERR_CUDA;
+    }
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return PB_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaEventCreate(&ctx->ev0);
+    cudaEventCreate(&ctx->ev1);
+    *out = ctx;
+    return PB_OK;
+}
+
+void pb_destroy(pb_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_all(ctx->scene_mem);
+    free_all(ctx->table_mem);
+    free_all(ctx->pool_mem);
+    if (ctx->film) cudaFree(ctx->film);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *pb_last_error(const pb_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *d) {
+    if (!ctx) return PB_ERR_ARG;
+    if (!d || d->nv <= 0 || d->nt <= 0 || d->nm <= 0 || !d->verts || !d->tris || !d->tri_mat || !d->mats || !d->cam)
+        return fail(ctx, PB_ERR_ARG, "scene: empty or missing arrays");
+    for (int i = 0; i < 3 * d->nt; ++i)
+        if (d->tris[i] < 0 || d->tris[i] >= d->nv) return fail(ctx, PB_ERR_ARG, "scene: vertex index out of range");
+    for (int i = 0; i < d->nt; ++i)
+        if (d->tri_mat[i] < 0 || d->tri_mat[i] >= d->nm) return fail(ctx, PB_ERR_ARG, "scene: material index out of range");
+    int W = (int)d->cam[10], H = (int)d->cam[11];
+    if (W <= 0 || H <= 0) return fail(ctx, PB_ERR_ARG, "scene: camera resolution must be positive");
+    if (d->tex_w > 0 && (!d->tex || d->tex_h <= 0)) return fail(ctx, PB_ERR_ARG, "scene: texture size without data");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_all(ctx->scene_mem);
+    free_all(ctx->pool_mem);
+    ctx->cap_slots = ctx->cap_ML = 0;
+    ctx->Lbuf = nullptr;
+    ctx->sigbuf = nullptr;
+    ctx->has_scene = false;
+    int nt = d->nt;
+    PbBvh bvh;
+    int nn = pb_bvh_build(d->verts, d->nv, d->tris, nt, &bvh);
+    std::string why;
+    if (!bvh_valid(bvh, nn, nt, why)) return fail(ctx, PB_ERR_STATE, "BVH build produced an invalid tree: " + why);
+    // leaf-ordered intersection records and per-triangle shading records
+    std::vector<float4> itri(3 * (size_t)nt), stri(4 * (size_t)nt);
+    std::vector<float> uv(6 * (size_t)nt, 0.0f);
+    std::vector<int> tri2e(nt, -1);
+    std::vector<float> epw;
+    std::vector<int> etri;
+    double wsum = 0.0;
+    float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+    for (int i = 0; i < d->nv; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], d->verts[3 * (size_t)i + a]);
+            hi[a] = std::max(hi[a], d->verts[3 * (size_t)i + a]);
+        }
+    for (int t = 0; t < nt; ++t) {
+        const float *p0 = d->verts + 3 * (size_t)d->tris[3 * (size_t)t];
+        const float *p1 = d->verts + 3 * (size_t)d->tris[3 * (size_t)t + 1];
+        const float *p2 = d->verts + 3 * (size_t)d->tris[3 * (size_t)t + 2];
+        float e1[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+        float e2[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+        double cx = (double)e1[1] * e2[2] - (double)e1[2] * e2[1];
+        double cy = (double)e1[2] * e2[0] - (double)e1[0] * e2[2];
+        double cz = (double)e1[0] * e2[1] - (double)e1[1] * e2[0];
+        double l = std::sqrt(cx * cx + cy * cy + cz * cz);
+        float n[3] = {0, 0, 1};
+        if (l > 0) {
+            n[0] = (float)(cx / l);
+            n[1] = (float)(cy / l);
+            n[2] = (float)(cz / l);
+        }
+        const float *m = d->mats + 12 * (size_t)d->tri_mat[t];
+        double le = (double)m[6] + m[7] + m[8];
+        if (le > 0 && l > 0) {
+            tri2e[t] = (int)etri.size();
+            etri.push_back(t);
+            double w = 0.5 * l * le;
+            wsum += w;
+            epw.push_back((float)w);
+        }
+        stri[4 * (size_t)t] = make_float4(p0[0], p0[1], p0[2], 0.0f);
+        int mi = d->tri_mat[t];
+        memcpy(&stri[4 * (size_t)t].w, &mi, 4);
+        stri[4 * (size_t)t + 1] = make_float4(e1[0], e1[1], e1[2], 0.0f);
+        stri[4 * (size_t)t + 2] = make_float4(e2[0], e2[1], e2[2], 0.0f);
+        stri[4 * (size_t)t + 3] = make_float4(n[0], n[1], n[2], 0.0f);
+        memcpy(&stri[4 * (size_t)t + 3].w, &tri2e[t], 4);
+        if (d->uvs)
+            for (int k = 0; k < 3; ++k) {
+                uv[6 * (size_t)t + 2 * k] = d->uvs[2 * (size_t)d->tris[3 * (size_t)t + k]];
+                uv[6 * (size_t)t + 2 * k + 1] = d->uvs[2 * (size_t)d->tris[3 * (size_t)t + k] + 1];
+            }
+    }
+    for (size_t i = 0; i < bvh.order.size(); ++i) {
+        int t = bvh.order[i];
+        itri[3 * i] = stri[4 * (size_t)t];
+        memcpy(&itri[3 * i].w, &t, 4);
+        itri[3 * i + 1] = stri[4 * (size_t)t + 1];
+        itri[3 * i + 2] = stri[4 * (size_t)t + 2];
+    }
+    // emitter selection: cumulative power share, last entry exactly 1
+    int ne = (int)etri.size();
+    std::vector<float> ecdf(std::max(ne, 1)), epmf(std::max(ne, 1));
+    double acc = 0.0;
+    for (int e = 0; e < ne; ++e) {
+        acc += epw[e];
+        ecdf[e] = (float)(acc / wsum);
+        epmf[e] = (float)(epw[e] / wsum);
+    }
+    if (ne > 0) ecdf[ne - 1] = 1.0f;
+    std::vector<DMat> mats(d->nm);
+    for (int i = 0; i < d->nm; ++i) {
+        const float *m = d->mats + 12 * (size_t)i;
+        DMat M{};
+        M.kind = (int)m[0];
+        M.cr = m[1]; M.cg = m[2]; M.cb = m[3];
+        M.alpha = m[4] * m[4];
+        M.ior = m[5];
+        M.ler = m[6]; M.leg = m[7]; M.leb = m[8];
+        M.textured = m[9] != 0.0f;
+        M.specular = (M.kind != MK_LAMBERT) && (m[4] < 0.2f);
+        M.emitter = ((double)m[6] + m[7] + m[8]) > 0.0;
+        M.black = (M.kind == MK_LAMBERT) && !(std::max(m[1], std::max(m[2], m[3])) > 0.0f);
+        if (M.kind < 0 || M.kind > 2) return fail(ctx, PB_ERR_ARG, "scene: unknown material kind");
+        mats[i] = M;
+    }
+    DScene S{};
+    auto &o = ctx->scene_mem;
+    float4 *nodes;
+    CK(upload(ctx, o, &nodes, reinterpret_cast<const float4 *>(bvh.nodes.data()), 4 * (size_t)nn));
+    int *par, *sib;
+    CK(upload(ctx, o, &par, bvh.parent.data(), (size_t)nn));
+    CK(upload(ctx, o, &sib, bvh.sibling.data(), (size_t)nn));
+    float4 *it_, *st_;
+    CK(upload(ctx, o, &it_, itri.data(), itri.size()));
+    CK(upload(ctx, o, &st_, stri.data(), stri.size()));
+    float *uvd;
+    CK(upload(ctx, o, &uvd, uv.data(), uv.size()));
+    DMat *md;
+    CK(upload(ctx, o, &md, mats.data(), mats.size()));
+    float *texd = nullptr;
+    if (d->tex_w > 0) CK(upload(ctx, o, &texd, d->tex, 3 * (size_t)d->tex_w * d->tex_h));
+    float *ecd, *epd;
+    int *etd;
+    CK(upload(ctx, o, &ecd, ecdf.data(), ecdf.size()));
+    CK(upload(ctx, o, &epd, epmf.data(), epmf.size()));
+    std::vector<int> etv(etri);
+    if (etv.empty()) etv.push_back(0);
+    CK(upload(ctx, o, &etd, etv.data(), etv.size()));
+    S.nodes = nodes;
+    S.parent = par;
+    S.sibling = sib;
+    S.itri = it_;
+    S.stri = st_;
+    S.uv = uvd;
+    S.mats = md;
+    S.tex = texd;
+    S.ecdf = ecd;
+    S.epmf = epd;
+    S.etri = etd;
+    S.nt = nt;
+    S.nnodes = nn;
+    S.ne = ne;
+    S.tw = d->tex_w > 0 ? d->tex_w : 0;
+    S.th = d->tex_w > 0 ? d->tex_h : 0;
+    S.W = W;
+    S.H = H;
+    float ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    S.eps_t = 1e-5f * ext;
+    const float *c = d->cam;
+    float3 pos = make_float3(c[0], c[1], c[2]);
+    double fx = (double)c[3] - c[0], fy = (double)c[4] - c[1], fz = (double)c[5] - c[2];
+    double fl = std::sqrt(fx * fx + fy * fy + fz * fz);
+    fx /= fl; fy /= fl; fz /= fl;
+    double rx = fy * c[8] - fz * c[7], ry = fz * c[6] - fx * c[8], rz = fx * c[7] - fy * c[6];
+    double rl = std::sqrt(rx * rx + ry * ry + rz * rz);
+    rx /= rl; ry /= rl; rz /= rl;
+    double ux = ry * fz - rz * fy, uy = rz * fx - rx * fz, uz = rx * fy - ry * fx;
+    S.cpos = pos;
+    S.cfwd = make_float3((float)fx, (float)fy, (float)fz);
+    S.cright = make_float3((float)rx, (float)ry, (float)rz);
+    S.cup = make_float3((float)ux, (float)uy, (float)uz);
+    S.tanh_ = (float)std::tan(0.5 * (double)c[9] * M_PI / 180.0);
+    S.aspect = (float)W / (float)H;
+    S.lo = make_float3(0, 0, 0);
+    S.ext = make_float3(1, 1, 1);
+    ctx->S = S;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->film) cudaFree(ctx->film);
+    ctx->film = nullptr;
+    CK(cudaMalloc(&ctx->film, sizeof(float) * 3 * (size_t)W * H));
+    CK(cudaMemset(ctx->film, 0, sizeof(float) * 3 * (size_t)W * H));
+    ctx->film_iters = 0;
+    ctx->has_scene = true;
+    return PB_OK;
+}
+
+pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *t) {
+    if (!ctx) return PB_ERR_ARG;
+    if (!ctx->has_scene) return fail(ctx, PB_ERR_STATE, "upload the scene before the tables");
+    if (!t || t->KT <= 0 || t->KS <= 0 || t->KSp <= 0 || t->KC <= 0 || t->KS > 1023 || t->KSp > 1023 ||
+        t->KC > 1000 || t->tile <= 0 || !t->cent_T || !t->cent_S || !t->cent_Sp || !t->cent_C || !t->gamma_conn ||
+        !t->gamma_proxy || !t->B_tab || !t->mis_tab || !t->pi_grid || !t->bbox_lo || !t->bbox_hi)
+        return fail(ctx, PB_ERR_ARG, "tables: bad sizes or missing arrays (KS, KSp <= 1023)");
+    int gw = (ctx->S.W + t->tile - 1) / t->tile, gh = (ctx->S.H + t->tile - 1) / t->tile;
+    if (t->grid_w != gw || t->grid_h != gh) return fail(ctx, PB_ERR_ARG, "tables: grid size does not match W/H/tile");
+    int ncell = 4 * t->KSp * (t->KC + 1);
+    for (int i = 0; i < ncell; ++i)
+        if (!(t->B_tab[i] > 0.0f)) return fail(ctx, PB_ERR_ARG, "tables: B must be positive");
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_all(ctx->table_mem);
+    DTables T{};
+    T.KT = t->KT; T.KS = t->KS; T.KSp = t->KSp; T.KC = t->KC;
+    auto &o = ctx->table_mem;
+    float *p;
+    CK(upload(ctx, o, &p, t->cent_T, (size_t)t->KT * 9)); T.cT = p;
+    CK(upload(ctx, o, &p, t->cent_S, (size_t)t->KS * 9)); T.cS = p;
+    CK(upload(ctx, o, &p, t->cent_Sp, (size_t)t->KSp * 6)); T.cSp = p;
+    CK(upload(ctx, o, &p, t->cent_C, (size_t)t->KC * 3)); T.cC = p;
+    CK(upload(ctx, o, &p, t->gamma_conn, (size_t)t->KT * t->KS)); T.gC = p;
+    CK(upload(ctx, o, &p, t->gamma_proxy, (size_t)t->KT * t->KSp)); T.gP = p;
+    CK(upload(ctx, o, &p, t->B_tab, (size_t)ncell)); T.Bt = p;
+    CK(upload(ctx, o, &p, t->mis_tab, (size_t)ncell)); T.mis = p;
+    CK(upload(ctx, o, &p, t->pi_grid, (size_t)gw * gh)); T.pi = p;
+    T.tile = t->tile;
+    T.gw = gw;
+    T.gh = gh;
+    ctx->T = T;
+    float3 lo = make_float3(t->bbox_lo[0], t->bbox_lo[1], t->bbox_lo[2]);
+    float ex = t->bbox_hi[0] - t->bbox_lo[0], ey = t->bbox_hi[1] - t->bbox_lo[1], ez = t->bbox_hi[2] - t->bbox_lo[2];
+    ctx->S.lo = lo;
+    ctx->S.ext = make_float3(ex > 0 ? ex : 1.0f, ey > 0 ? ey : 1.0f, ez > 0 ? ez : 1.0f);
+    // pool buffers depend on the table sizes
+    free_all(ctx->pool_mem);
+    ctx->cap_slots = ctx->cap_ML = 0;
+    ctx->Lbuf = nullptr;
+    ctx->sigbuf = nullptr;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->has_tables = true;
+    return PB_OK;
+}
+
+pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
+    if (!ctx) return PB_ERR_ARG;
+    pb_status s = check_cfg(ctx, cfg);
+    if (s != PB_OK) return s;
+    CK(cudaSetDevice(ctx->device));
+    KParams P = kparams(ctx, cfg);
+    int slots = cfg->batch > 0 ? cfg->batch : std::max(1, std::min(32, (1 << 20) / std::max(1, P.npix)));
+    slots = std::max(1, std::min(slots, std::max(1, cfg->spp)));
+    s = ensure_pool(ctx, slots, P.M * P.L, P.repeats, P.npix);
+    if (s != PB_OK) return s;
+    CK(cudaMemsetAsync(ctx->B.counters, 0, sizeof(unsigned long long) * CNT_N, ctx->stream));
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    for (int done = 0; done < cfg->spp;) {
+        int ns = std::min(slots, cfg->spp - done);
+        s = run_wave(ctx, P, ns, (uint32_t)(cfg->iter0 + done), true, true, nullptr);
+        if (s != PB_OK) return s;
+        launch_film_add(P, ns, ctx->Lbuf, ctx->film, ctx->stream);
+        done += ns;
+    }
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev1));
+    CK(cudaGetLastError());
+    ctx->film_iters += cfg->spp;
+    pb_stats st{};
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    st.ms = ms;
+    st.mpaths_per_s = ms > 0 ? (double)P.npix * cfg->spp / (ms * 1e-3) / 1e6 : 0.0;
+    read_counters(ctx, &st);
+    if (stats) *stats = st;
+    if (st.n_truncated > 0) return fail(ctx, PB_ERR_TRUNCATED, "reciprocal estimate hit the trial cap");
+    return PB_OK;
+}
+
+pb_status pb_film_clear(pb_ctx *ctx) {
+    if (!ctx) return PB_ERR_ARG;
+    if (!ctx->has_scene) return fail(ctx, PB_ERR_STATE, "no scene");
+    CK(cudaMemsetAsync(ctx->film, 0, sizeof(float) * 3 * (size_t)ctx->S.W * ctx->S.H, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->film_iters = 0;
+    return PB_OK;
+}
+
+pb_status pb_film_readback(pb_ctx *ctx, float *host_rgb, size_t n) {
+    if (!ctx) return PB_ERR_ARG;
+    if (!ctx->has_scene) return fail(ctx, PB_ERR_STATE, "no scene");
+    size_t need = 3 * (size_t)ctx->S.W * ctx->S.H;
+    if (!host_rgb || n < need) return fail(ctx, PB_ERR_ARG, "film readback: buffer too small");
+    CK(cudaMemcpyAsync(host_rgb, ctx->film, need * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->film_iters > 0) {
+        float inv = 1.0f / (float)ctx->film_iters;
+        for (size_t i = 0; i < need; ++i) host_rgb[i] *= inv;
+    }
+    return PB_OK;
+}
+
+pb_status pb_film_device(pb_ctx *ctx, float **dev_sum, int64_t *iterations) {
+    if (!ctx || !dev_sum || !iterations) return PB_ERR_ARG;
+    if (!ctx->has_scene) return fail(ctx, PB_ERR_STATE, "no scene");
+    *dev_sum = ctx->film;
+    *iterations = ctx->film_iters;
+    return PB_OK;
+}
+
+pb_status pb_trace(pb_ctx *ctx, const float *host_rays, int n, float *host_hits) {
+    if (!ctx) return PB_ERR_ARG;
+    if (!ctx->has_scene) return fail(ctx, PB_ERR_STATE, "no scene");
+    if (n < 0 || (n > 0 && (!host_rays || !host_hits))) return fail(ctx, PB_ERR_ARG, "trace: bad arguments");
+    if (n == 0) return PB_OK;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<void *> tmp;
+    float *dr, *dh;
+    unsigned long long *cnt;
+    CK(upload(ctx, tmp, &dr, host_rays, 7 * (size_t)n));
+    CK(dalloc(tmp, &dh, 4 * (size_t)n));
+    CK(dalloc(tmp, &cnt, (size_t)CNT_N));
+    launch_trace(ctx->S, dr, n, dh, 0, cnt, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_hits, dh, 16 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_all(tmp);
+    return PB_OK;
+}
+
+pb_status pb_occluded(pb_ctx *ctx, const float *host_seg, int n, int32_t *host_out) {
+    if (!ctx) return PB_ERR_ARG;
+    if (!ctx->has_scene) return fail(ctx, PB_ERR_STATE, "no scene");
+    if (n < 0 || (n > 0 && (!host_seg || !host_out))) return fail(ctx, PB_ERR_ARG, "occluded: bad arguments");
+    if (n == 0) return PB_OK;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<void *> tmp;
+    float *ds;
+    int32_t *dout;
+    CK(upload(ctx, tmp, &ds, host_seg, 8 * (size_t)n));
+    CK(dalloc(tmp, &dout, (size_t)n));
+    launch_occluded(ctx->S, ds, n, dout, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_out, dout, 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_all(tmp);
+    return PB_OK;
+}
+
+pb_status pb_light_pass(pb_ctx *ctx, const pb_config *cfg, int iteration, int32_t *host_tri, float *host_bary) {
+    if (!ctx) return PB_ERR_ARG;
+    pb_status s = check_cfg(ctx, cfg);
+    if (s != PB_OK) return s;
+    if (!host_tri || !host_bary) return fail(ctx, PB_ERR_ARG, "light pass: null output");
+    CK(cudaSetDevice(ctx->device));
+    KParams P = kparams(ctx, cfg);
+    s = ensure_pool(ctx, std::max(1, ctx->cap_slots), P.M * P.L, std::max(P.repeats, ctx->cap_rep), P.npix);
+    if (s != PB_OK) return s;
+    launch_light_pass(ctx->S, P, ctx->B, 1, (uint32_t)iteration, ctx->stream);
+    CK(cudaGetLastError());
+    size_t n = (size_t)P.M * P.L;
+    CK(cudaMemcpyAsync(host_tri, ctx->B.gtri, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(host_bary, ctx->B.gbary, 8 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PB_OK;
+}
+
+pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const int32_t *host_tri,
+                       const float *host_bary, const double *host_rhat_override, float *host_pix_rgb,
+                       uint32_t *host_pix_sig, int cap, int *n_entries, float *host_entry_rhat,
+                       uint32_t *host_entry_sig, float *host_entry_nodes, pb_stats *stats) {
+    if (!ctx) return PB_ERR_ARG;
+    pb_status s = check_cfg(ctx, cfg);
+    if (s != PB_OK) return s;
+    if (!host_tri || !host_bary) return fail(ctx, PB_ERR_ARG, "iteration: null geometry");
+    CK(cudaSetDevice(ctx->device));
+    KParams P = kparams(ctx, cfg);
+    for (size_t i = 0; i < (size_t)P.M * P.L; ++i)
+        if (host_tri[i] < -1 || host_tri[i] >= ctx->S.nt) return fail(ctx, PB_ERR_ARG, "iteration: triangle index out of range");
+    s = ensure_pool(ctx, std::max(1, ctx->cap_slots), P.M * P.L, std::max(P.repeats, ctx->cap_rep), P.npix);
+    if (s != PB_OK) return s;
+    size_t n = (size_t)P.M * P.L;
+    CK(cudaMemsetAsync(ctx->B.counters, 0, sizeof(unsigned long long) * CNT_N, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->B.gtri, host_tri, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->B.gbary, host_bary, 8 * n, cudaMemcpyHostToDevice, ctx->stream));
+    launch_pool_build(ctx->S, ctx->T, P, ctx->B, 1, ctx->stream);
+    int ne = 0;
+    CK(cudaMemcpyAsync(&ne, ctx->B.nent, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (host_rhat_override) {
+        std::vector<float> r(std::max(ne, 1));
+        for (int i = 0; i < ne; ++i) r[i] = (float)host_rhat_override[i];
+        CK(cudaMemcpyAsync(ctx->B.rhat, r.data(), 4 * (size_t)ne, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        launch_recip(ctx->S, ctx->T, P, ctx->B, 1, (uint32_t)iteration, ctx->num_sms, ctx->stream);
+    }
+    launch_eye(ctx->S, ctx->T, P, ctx->B, 1, (uint32_t)iteration, ctx->Lbuf, ctx->sigbuf, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (n_entries) *n_entries = ne;
+    int k = std::min(ne, std::max(cap, 0));
+    if (host_pix_rgb) {
+        std::vector<float4> Lh(P.npix);
+        CK(cudaMemcpy(Lh.data(), ctx->Lbuf, sizeof(float4) * P.npix, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < P.npix; ++i) {
+            host_pix_rgb[3 * (size_t)i] = Lh[i].x;
+            host_pix_rgb[3 * (size_t)i + 1] = Lh[i].y;
+            host_pix_rgb[3 * (size_t)i + 2] = Lh[i].z;
+        }
+    }
+    if (host_pix_sig) CK(cudaMemcpy(host_pix_sig, ctx->sigbuf, 4 * (size_t)P.npix, cudaMemcpyDeviceToHost));
+    if (k > 0 && host_entry_rhat) CK(cudaMemcpy(host_entry_rhat, ctx->B.rhat, 4 * (size_t)k, cudaMemcpyDeviceToHost));
+    if (k > 0 && host_entry_sig && !host_rhat_override)
+        CK(cudaMemcpy(host_entry_sig, ctx->B.esig, 4 * (size_t)k, cudaMemcpyDeviceToHost));
+    if (k > 0 && host_entry_nodes && !host_rhat_override) {
+        std::vector<float> rn((size_t)k * P.repeats);
+        CK(cudaMemcpy(rn.data(), ctx->B.repn, 4 * rn.size(), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < k; ++i) {
+            float a = 0;
+            for (int r = 0; r < P.repeats; ++r) a += rn[(size_t)i * P.repeats + r];
+            host_entry_nodes[i] = a;
+        }
+    }
+    pb_stats st{};
+    read_counters(ctx, &st);
+    if (stats) *stats = st;
+    return PB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// Shared declarations of the renderer's kernels and their device buffers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pb_device.cuh"
+
+// Render parameters as the kernels see them.
+struct KParams {
+    uint32_t seed;
+    int max_depth, M, M_p, repeats, proxy, conn, trial_cap;
+    int L;          // light-path vertex slots = max_depth - 1
+    int npix;
+};
+
+// Device buffers of the iterations in flight ("slots"). Per-light-vertex
+// arrays are indexed [slot][l * L + e].
+struct Pool {
+    int slots, ML;  // ML = M * L
+    int32_t *gtri;  // geometry
+    float2 *gbary;
+    float4 *vpos;    // p.xyz, material (int bits)
+    float4 *vnrm;    // n.xyz, triangle (int bits)
+    float4 *vwl;     // w_light.xyz (toward y_{e-1}), fwd_e
+    float4 *valpha;  // alpha rgb (f_y/p_y up to y_e), Lpart = Lsum_{e-2}
+    float4 *vmis;    // fwd_{e-1}, cos_{e-1}, d2(y_{e-1}, y_e), availability bits
+    int32_t *vlabel; // light subspace S of a connectable vertex, else -1
+    int32_t *elabel; // specular subspace S' of an incomplete sub-path end, else -1
+    int32_t *einfo;  // u | type << 3 | C << 4
+    int32_t *pool_idx, *bstart, *bitems, *npool;   // connection pool, (l,e) order and by S
+    int32_t *ent_idx, *estart, *eitems, *nent;     // incomplete sub-paths, (l,e) order and by S'
+    float *cdfC, *ZC, *cdfP, *ZP;                  // selection CDF rows per eye subspace
+    float *rep, *repn;                             // per (entry, repeat): estimate, nodes
+    int32_t *reptr;
+    float *rhat;                                   // per entry: averaged reciprocal estimate
+    uint32_t *esig;
+    int32_t *work;                                 // work counter, per-slot work offsets
+    int32_t *scratch;                              // 2 * slots * ML ints for the bucket sort
+    unsigned long long *counters;                  // stats
+};
+
+enum { CNT_ENTRIES = 0, CNT_TRUNC, CNT_NODES, CNT_CONN, CNT_PROXY, CNT_PROXY_OK, CNT_NFETCH, CNT_TTEST, CNT_N };
+
+void launch_light_pass(const DScene &S, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
+                       cudaStream_t st);
+void launch_pool_build(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
+                       cudaStream_t st);
+void launch_recip(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
+                  uint32_t iter_base, int num_sms, cudaStream_t st);
+void launch_eye(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
+                float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st);
+void launch_film_add(const KParams &P, int slots, const float4 *Lbuf, float *film, cudaStream_t st);
+void launch_trace(const DScene &S, const float *rays, int n, float *hits, int count, unsigned long long *counters,
+                  cudaStream_t st);
+void launch_occluded(const DScene &S, const float *seg, int n, int32_t *out, cudaStream_t st);

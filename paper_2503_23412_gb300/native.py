@@ -1,0 +1,225 @@
+"""ctypes binding of libproxybdpt.so (include/proxybdpt.h).
+
+Argument marshalling only: every step of the render runs in the library's
+CUDA kernels. Functions keep the C names (pb_create, pb_scene_upload, ...);
+`Renderer` bundles a context with the numpy arrays it was fed. Loading fails
+loudly when the compiled library is missing -- there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "_build", "libproxybdpt.so")
+
+PB_OK, PB_ERR_ARG, PB_ERR_OOM, PB_ERR_CUDA, PB_ERR_TIMEOUT, PB_ERR_TRUNCATED, PB_ERR_STATE = range(7)
+
+
+class pb_scene_desc(C.Structure):
+    _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("nm", C.c_int),
+                ("verts", C.c_void_p), ("uvs", C.c_void_p), ("tris", C.c_void_p),
+                ("tri_mat", C.c_void_p), ("mats", C.c_void_p),
+                ("tex_w", C.c_int), ("tex_h", C.c_int), ("tex", C.c_void_p), ("cam", C.c_void_p)]
+
+
+class pb_tables_desc(C.Structure):
+    _fields_ = [("KT", C.c_int), ("KS", C.c_int), ("KSp", C.c_int), ("KC", C.c_int),
+                ("bbox_lo", C.c_void_p), ("bbox_hi", C.c_void_p),
+                ("cent_T", C.c_void_p), ("cent_S", C.c_void_p), ("cent_Sp", C.c_void_p),
+                ("cent_C", C.c_void_p), ("gamma_conn", C.c_void_p), ("gamma_proxy", C.c_void_p),
+                ("B_tab", C.c_void_p), ("mis_tab", C.c_void_p),
+                ("tile", C.c_int), ("grid_w", C.c_int), ("grid_h", C.c_int), ("pi_grid", C.c_void_p)]
+
+
+class pb_config(C.Structure):
+    _fields_ = [("seed", C.c_uint32), ("spp", C.c_int), ("max_depth", C.c_int), ("M", C.c_int),
+                ("M_p", C.c_int), ("repeats", C.c_int), ("proxy", C.c_int), ("conn", C.c_int),
+                ("trial_cap", C.c_int), ("iter0", C.c_int), ("batch", C.c_int)]
+
+
+class pb_stats(C.Structure):
+    _fields_ = [("ms", C.c_double), ("mpaths_per_s", C.c_double), ("n_entries", C.c_int64),
+                ("n_truncated", C.c_int64), ("n_nodes", C.c_int64), ("n_conn", C.c_int64),
+                ("n_proxy", C.c_int64), ("n_proxy_ok", C.c_int64), ("n_node_fetch", C.c_int64),
+                ("n_tri_test", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+EXPORTS = ["pb_create", "pb_destroy", "pb_last_error", "pb_scene_upload", "pb_tables_upload", "pb_render",
+           "pb_film_clear", "pb_film_readback", "pb_film_device", "pb_trace", "pb_occluded", "pb_light_pass",
+           "pb_iteration"]
+
+
+def lib(path=LIB):
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libproxybdpt.so is not built (%s); run paper_2503_23412_gb300.build.build()" % path)
+    L = C.CDLL(path)
+    vp, i32 = C.c_void_p, C.c_int
+    L.pb_create.argtypes = [C.POINTER(vp), i32, vp]
+    L.pb_destroy.argtypes = [vp]
+    L.pb_destroy.restype = None
+    L.pb_last_error.argtypes = [vp]
+    L.pb_last_error.restype = C.c_char_p
+    L.pb_scene_upload.argtypes = [vp, C.POINTER(pb_scene_desc)]
+    L.pb_tables_upload.argtypes = [vp, C.POINTER(pb_tables_desc)]
+    L.pb_render.argtypes = [vp, C.POINTER(pb_config), C.POINTER(pb_stats)]
+    L.pb_film_clear.argtypes = [vp]
+    L.pb_film_readback.argtypes = [vp, vp, C.c_size_t]
+    L.pb_film_device.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_int64)]
+    L.pb_trace.argtypes = [vp, vp, i32, vp]
+    L.pb_occluded.argtypes = [vp, vp, i32, vp]
+    L.pb_light_pass.argtypes = [vp, C.POINTER(pb_config), i32, vp, vp]
+    L.pb_iteration.argtypes = [vp, C.POINTER(pb_config), i32, vp, vp, vp, vp, vp, i32, C.POINTER(i32), vp, vp, vp,
+                               C.POINTER(pb_stats)]
+    for n in EXPORTS:
+        if n not in ("pb_destroy", "pb_last_error"):
+            getattr(L, n).restype = i32
+    _lib = L
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class PBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("proxybdpt status %d: %s" % (status, msg))
+        self.status = status
+
+
+def config(seed=7, spp=1, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, conn=1, trial_cap=1 << 16, iter0=0,
+           batch=0):
+    return pb_config(seed, spp, max_depth, M, M_p, repeats, proxy, conn, trial_cap, iter0, batch)
+
+
+def tables_desc(t, W, H):
+    keep = {k: np.ascontiguousarray(v, np.float32) for k, v in t.items() if isinstance(v, np.ndarray)}
+    tile = int(t["tile"])
+    gh, gw = keep["pi_grid"].shape
+    d = pb_tables_desc(keep["cent_T"].shape[0], keep["cent_S"].shape[0], keep["cent_Sp"].shape[0],
+                       keep["cent_C"].shape[0], _p(keep["bbox_lo"]), _p(keep["bbox_hi"]), _p(keep["cent_T"]),
+                       _p(keep["cent_S"]), _p(keep["cent_Sp"]), _p(keep["cent_C"]), _p(keep["gamma_conn"]),
+                       _p(keep["gamma_proxy"]), _p(keep["B_tab"]), _p(keep["mis_tab"]), tile, gw, gh,
+                       _p(keep["pi_grid"]))
+    d._keep = keep
+    return d
+
+
+class Renderer:
+    """One renderer context on one device with a scene and tables."""
+
+    def __init__(self, scene, tables=None, device=0, stream=None):
+        self.L = lib()
+        self.h = C.c_void_p()
+        st = self.L.pb_create(C.byref(self.h), device, stream)
+        if st != PB_OK:
+            raise PBError(st, "pb_create failed")
+        self.W, self.H = int(scene["cam"][10]), int(scene["cam"][11])
+        self.upload_scene(scene)
+        if tables is not None:
+            self.upload_tables(tables)
+
+    def _check(self, st, ok=(PB_OK,)):
+        if st not in ok:
+            raise PBError(st, self.L.pb_last_error(self.h).decode())
+        return st
+
+    def upload_scene(self, scene):
+        sc = {k: np.ascontiguousarray(v) for k, v in scene.items()}
+        tex = sc["tex"]
+        d = pb_scene_desc(len(sc["verts"]), len(sc["tris"]), len(sc["mats"]), _p(sc["verts"]), _p(sc["uvs"]),
+                          _p(sc["tris"]), _p(sc["tri_mat"]), _p(sc["mats"]), tex.shape[1], tex.shape[0], _p(tex),
+                          _p(sc["cam"]))
+        self._check(self.L.pb_scene_upload(self.h, C.byref(d)))
+        self.scene = sc
+
+    def upload_tables(self, t):
+        d = tables_desc(t, self.W, self.H)
+        self._check(self.L.pb_tables_upload(self.h, C.byref(d)))
+        self.tables = t
+
+    def render(self, cfg, allow_truncated=False):
+        st = pb_stats()
+        ok = (PB_OK, PB_ERR_TRUNCATED) if allow_truncated else (PB_OK,)
+        self._check(self.L.pb_render(self.h, C.byref(cfg), C.byref(st)), ok)
+        return st.as_dict()
+
+    def clear(self):
+        self._check(self.L.pb_film_clear(self.h))
+
+    def film(self):
+        out = np.zeros((self.H * self.W, 3), np.float32)
+        self._check(self.L.pb_film_readback(self.h, _p(out), out.size))
+        return out
+
+    def film_device(self):
+        p = C.c_void_p()
+        n = C.c_int64()
+        self._check(self.L.pb_film_device(self.h, C.byref(p), C.byref(n)))
+        return p.value, n.value
+
+    def trace(self, o, d, skip=None):
+        n = len(o)
+        rays = np.zeros((n, 7), np.float32)
+        rays[:, :3], rays[:, 3:6] = o, d
+        rays[:, 6] = -1 if skip is None else skip
+        hits = np.zeros((n, 4), np.float32)
+        self._check(self.L.pb_trace(self.h, _p(rays), n, _p(hits)))
+        return hits
+
+    def occluded(self, a, b, skip_a, skip_b):
+        n = len(a)
+        seg = np.zeros((n, 8), np.float32)
+        seg[:, :3], seg[:, 3:6], seg[:, 6], seg[:, 7] = a, b, skip_a, skip_b
+        out = np.zeros(n, np.int32)
+        self._check(self.L.pb_occluded(self.h, _p(seg), n, _p(out)))
+        return out
+
+    def light_pass(self, cfg, iteration):
+        Lv = cfg.max_depth - 1
+        tri = np.zeros((cfg.M, Lv), np.int32)
+        bary = np.zeros((cfg.M, Lv, 2), np.float32)
+        self._check(self.L.pb_light_pass(self.h, C.byref(cfg), iteration, _p(tri), _p(bary)))
+        return tri, bary
+
+    def iteration(self, cfg, iteration, tri, bary, rhat=None, cap=100000):
+        tri = np.ascontiguousarray(tri, np.int32)
+        bary = np.ascontiguousarray(bary, np.float32)
+        rgb = np.zeros((self.W * self.H, 3), np.float32)
+        sig = np.zeros(self.W * self.H, np.uint32)
+        ne = C.c_int(0)
+        er = np.zeros(cap, np.float32)
+        es = np.zeros(cap, np.uint32)
+        en = np.zeros(cap, np.float32)
+        st = pb_stats()
+        rh = None
+        if rhat is not None:
+            rh = np.zeros(cfg.M * (cfg.max_depth - 1), np.float64)
+            rh[:len(rhat)] = rhat
+        self._check(self.L.pb_iteration(self.h, C.byref(cfg), iteration, _p(tri), _p(bary), _p(rh), _p(rgb),
+                                        _p(sig), cap, C.byref(ne), _p(er), _p(es), _p(en), C.byref(st)))
+        k = min(ne.value, cap)
+        return dict(rgb=rgb, sig=sig, rhat=er[:k], entry_sig=es[:k], entry_nodes=en[:k], stats=st.as_dict())
+
+    def close(self):
+        if self.h:
+            self.L.pb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
