@@ -1,0 +1,339 @@
+"""Benchmark: Mpaths/s of the proxy-tracing BDPT render on the projector
+workload (256x256, 64 spp, max depth 8, M = 10,000 light sub-paths,
+reciprocal estimates on ~400 incomplete light sub-paths per iteration).
+
+One step = one full render of the workload (64 iterations: light pass, pool
+build, reciprocal estimation, eye pass with connections, proxy retrace and
+MIS, film accumulation) on inputs resident on the device. The subspace
+tables are learned on the device once before timing (the paper's
+preprocessing). Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this build: there is no runnable upstream).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpaths/s and equal-time MAPE vs CPU oracle; learned vs plain proposal, 1 GB300"
+W, H, SPP, DEPTH, M = 256, 256, 64, 8, 10000   # projector workload; --workload small shrinks it
+ENTRY_TARGET = 400          # incomplete light sub-paths estimated per iteration (paper: up to 400)
+WORKLOAD = ("projector 256x256, 64 spp, max depth 8: textured 0.1x0.1 emitter in an absorbing box, "
+            "biconvex GGX dielectric lens (IOR 1.5, ~19.5k triangles), diffuse room; M=10000 light "
+            "sub-paths/iteration, 5 reciprocal repeats, 300 eye / 300 light / 100 specular / 10 control subspaces")
+FALLBACK_HBM = 6800.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def src_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+EYE_SRC = ["paper_2503_23412_gb300/csrc/pb_eye.cu", "paper_2503_23412_gb300/csrc/pb_device.cuh",
+           "paper_2503_23412_gb300/csrc/pb_kernels.h"]
+REC_SRC = ["paper_2503_23412_gb300/csrc/pb_light.cu", "paper_2503_23412_gb300/csrc/pb_estimator.cuh",
+           "paper_2503_23412_gb300/csrc/pb_device.cuh", "paper_2503_23412_gb300/csrc/pb_kernels.h"]
+
+
+def traffic_for(kernel, sha):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("src_sha") != sha:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+def oracle_tables(scene):
+    """Tables for the oracle's timing runs, learned by the oracle itself
+    (random centroids, B / MIS / Gamma / grid from one small learning pass)."""
+    import oracle as O
+    from paper_2503_23412_gb300 import scenes
+    o = O.Oracle(scene)
+    tab = scenes.random_tables(scene, KT=300, KS=300, KSp=100, KC=10)
+    tab = o.learn(O.params(M=1000, M_p=1000, max_depth=DEPTH), tab, 1 << 21, 1, n_bsamples=16)
+    return o, o.tables(tab)
+
+
+def oracle_iteration_rate(o, td, M_p, it, npx):
+    """CPU oracle, one iteration of the workload measured in two parts: the
+    light side (light pass, pool, all reciprocal estimates) and the eye paths
+    of the first `npx` pixels (reusing those estimates). Returns the
+    extrapolated full-iteration rate W*H / (t_light + W*H * t_pixel) in
+    Mpaths/s and the CPU seconds spent."""
+    import oracle as O
+    p = O.params(M=M, M_p=M_p, max_depth=DEPTH)
+    t0 = time.perf_counter()
+    tri, bary = o.light_pass(p, it)
+    r = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0)
+    t_light = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0, rhat=r["rhat"])
+    t_pool = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=npx, rhat=r["rhat"])
+    t_eye = max(time.perf_counter() - t0 - t_pool, 1e-9)
+    rate = W * H / (t_light + W * H * t_eye / npx) / 1e6
+    return rate, t_light + t_pool + t_eye
+
+
+def oracle_sample(scene, M_p, npx=2048):
+    o, td = oracle_tables(scene)
+    rate, secs = oracle_iteration_rate(o, td, M_p, 0, npx)
+    desc = ("1 iteration, 1 thread: light pass (M=%d), reciprocal estimates (M_p=%d) and eye paths of %d of %d "
+            "pixels (%.1f s); extrapolated to the full 256x256 iteration" % (M, M_p, npx, W * H, secs))
+    return rate, desc
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2503_23412_gb300 import scenes
+    sc = scenes.projector(W, H)
+    o, td = oracle_tables(sc)
+    M_p = int(os.environ.get("PB_BENCH_MP", "1400"))
+    npx = 1024
+    vals, secs = [], []
+    for k in range(args.warmup + args.steps):
+        v, sec = oracle_iteration_rate(o, td, M_p, k, npx)
+        if k >= args.warmup:
+            vals.append(v)
+            secs.append(sec)
+    v = float(np.mean(vals))
+    desc = ("per step 1 iteration, 1 thread: light pass (M=%d), reciprocal estimates (M_p=%d), eye paths of %d "
+            "of %d pixels; extrapolated to the full iteration" % (M, M_p, npx, W * H))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpaths/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": desc, "M_p": M_p},
+           "cpu_baseline": {"value": v, "unit": "Mpaths/s", "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": v, "unit": "Mpaths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2503_23412_gb300 import native as N
+    from paper_2503_23412_gb300 import scenes
+
+    sc = scenes.projector(W, H)
+    stream = torch.cuda.current_stream()
+    n_learn = 4 if M >= 10000 else 2
+    r = N.Renderer(sc, None, device=local, stream=stream.cuda_stream)
+    # learn the tables on the device (paper's preprocessing), calibrate M_p for ~400 entries/iteration
+    learn_cfg = N.config(M=M, M_p=M, max_depth=DEPTH, spp=1, seed=7)
+    t0 = time.perf_counter()
+    st = r.prepare(learn_cfg, n_iter=n_learn, iter0=1 << 22, n_bsamples=32, lloyd_iters=8,
+                   KT=300, KS=300, KSp=100, KC=10, tile=10)
+    learn_s = time.perf_counter() - t0
+    frac = st["n_entries"] / float(n_learn * M)
+    M_p = int(min(M, max(1, round(ENTRY_TARGET / max(frac, 1e-9)))))
+    tables = r.tables_readback()
+    base_iter = rank * (1 << 24)
+    cfg = N.config(M=M, M_p=M_p, max_depth=DEPTH, spp=SPP, seed=7)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(i, count=False):
+        cfg.iter0 = base_iter + i * SPP
+        cfg.count_traversal = 1 if count else 0
+        r.clear()
+        return r.render(cfg, allow_truncated=True)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    times, stats = [], []
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats.append(step(args.warmup + i))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    if dist:
+        dist.barrier()
+    total_ms = float(np.sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    paths = W * H * SPP * args.steps * ws
+    value = paths / (total_ms * 1e-3) / 1e6
+    # traversal work of one step (untimed counting run) -> algorithmic bytes
+    cst = step(args.warmup + args.steps, count=True)
+    mean = {k: float(np.mean([s[k] for s in stats])) for k in ("ms_light", "ms_pool", "ms_recip", "ms_eye")}
+    waves = stats[-1]["n_waves"]
+    eye_ms, rec_ms = mean["ms_eye"] / waves, mean["ms_recip"] / waves
+    eye_bytes = (64.0 * cst["eye_nodes"] + 48.0 * cst["eye_tris"]) / waves
+    rec_bytes = (64.0 * cst["rec_nodes"] + 48.0 * cst["rec_tris"]) / waves
+    dom = "k_eye" if eye_ms >= rec_ms else "k_recip"
+    b, ms = (eye_bytes, eye_ms) if dom == "k_eye" else (rec_bytes, rec_ms)
+    peak, peak_kind = peaks()
+    achieved = b / (ms * 1e-3) / 1e9
+    sha = src_sha(EYE_SRC if dom == "k_eye" else REC_SRC)
+    # end to end through the C ABI with host buffers: scene + tables upload, render, film readback
+    h2d = sum(v.nbytes for v in sc.values()) + sum(v.nbytes for v in tables.values() if isinstance(v, np.ndarray))
+    d2h = W * H * 3 * 4
+    e2e_t = []
+    for i in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r.upload_scene(sc)
+        r.upload_tables(tables)
+        cfg.iter0 = base_iter + (args.warmup + args.steps + 1 + i) * SPP
+        cfg.count_traversal = 0
+        r.render(cfg, allow_truncated=True)
+        img = r.film()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = W * H * SPP * ws / float(np.mean(e2e_t)) / 1e6
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu_v, cpu_desc = oracle_sample(sc, M_p)
+    out = {
+        "metric": METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": M, "M_p": M_p, "spp": SPP, "max_depth": DEPTH,
+                   "l2": "256 MiB buffer written before every timed step",
+                   "tables": "learned on the device before timing (%.1f s, %d learning iterations)" % (learn_s, n_learn),
+                   "stage_ms_per_step": mean, "entries_per_iteration": stats[-1]["n_entries"] / SPP,
+                   "truncated_estimates_per_step": stats[-1]["n_truncated"],
+                   "estimator_nodes_per_step": stats[-1]["n_nodes"], "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom, sha),
+                     "algorithmic_bytes_per_launch": b, "launch_ms": ms, "src_sha": sha},
+        "cpu_baseline": {"value": cpu_v, "unit": "Mpaths/s", "cores": 1, "kind": "oracle", "sample": cpu_desc},
+        "e2e": {"value": e2e, "unit": "Mpaths/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+        "clocks": clk.summary(),
+        "gpu_launches": int(sum(s["n_launches"] for s in stats)),
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    global W, H, SPP, M, WORKLOAD
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="projector", choices=["projector", "small"],
+                    help="small: the same scene and pipeline at 64x64, 4 spp, M=2000 (profiling captures)")
+    args = ap.parse_args()
+    if args.workload == "small":
+        W, H, SPP, M = 64, 64, 4, 2000
+        WORKLOAD = WORKLOAD.replace("256x256, 64 spp", "64x64, 4 spp").replace("M=10000", "M=2000")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

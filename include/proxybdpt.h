@@ -99,6 +99,8 @@ typedef struct {
     int trial_cap;     /* node cap per reciprocal estimate (e.g. 65536) */
     int iter0;
     int batch;         /* iterations in flight per launch wave (0: automatic) */
+    int count_traversal; /* 1: count BVH node fetches / triangle tests / rays (slower) */
+    int chain_handoff;   /* estimator nodes a warp walks before a block takes the chain over (0: 512) */
 } pb_config;
 
 typedef struct {
@@ -108,7 +110,11 @@ typedef struct {
     int64_t n_truncated;       /* estimates that hit trial_cap */
     int64_t n_nodes;           /* estimator nodes evaluated (trials) */
     int64_t n_conn, n_proxy, n_proxy_ok;
-    int64_t n_node_fetch, n_tri_test;   /* traversal counters (when enabled) */
+    double ms_light, ms_pool, ms_recip, ms_eye;   /* device time per stage (pb_render) */
+    int64_t n_launches;                           /* kernels launched by the call */
+    int64_t n_waves;                              /* launch waves (iterations in flight per wave) */
+    /* traversal work when count_traversal = 1: eye kernel and estimator kernel */
+    int64_t eye_nodes, eye_tris, eye_rays, rec_nodes, rec_tris, rec_rays;
 } pb_stats;
 
 pb_status pb_create(pb_ctx **out, int device, void *cuda_stream /* NULL: own stream */);
@@ -118,6 +124,39 @@ const char *pb_last_error(const pb_ctx *ctx);
 /* Builds the BVH on the host (binned SAH) and uploads scene and BVH. */
 pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *scene);
 pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *tables);
+
+/* Table learning (Sec. 5.4-5.5): n_iter learning iterations, numbered from
+ * iter0 and never added to the film, build on the device
+ *  - k-means centroids of the eye, light, specular and control subspaces
+ *    (lloyd_iters Lloyd steps from evenly spaced samples), unless
+ *    keep_centroids = 1 keeps those of the uploaded tables;
+ *  - B(u,S',C) = 1.5 x the largest f/q of n_bsamples draws per incomplete
+ *    sub-path (App. "Optimal value for B": B = max f/q);
+ *  - the MIS scale mean(R)/mean(R^2) per cell (Sec. 5.4, Eq. MIS_1);
+ *  - Gamma rows proportional to the accumulated unweighted contribution
+ *    (0.9 x normalised + 0.1 uniform) and the 10x10-tile proxy probability
+ *    (1.0 where the proxy share is >= 5 %, else 0.2; Sec. 6.1.1).
+ * The learned tables replace the current ones. Table sizes KT, KS, KSp, KC
+ * and tile apply when the centroids are learned (KS, KSp <= 1023). */
+typedef struct {
+    int KT, KS, KSp, KC, tile;
+    int n_iter;
+    uint32_t iter0;
+    int n_bsamples;
+    int lloyd_iters;
+    int keep_centroids;
+} pb_learn_desc;
+pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_learn_desc *learn, pb_stats *stats_or_null);
+
+/* Copies the current tables to caller buffers sized as in pb_tables_desc.
+ * Sizes (K*, tile, grid) are always written; if any pointer is NULL only the
+ * sizes are returned. */
+typedef struct {
+    int KT, KS, KSp, KC, tile, grid_w, grid_h;
+    float *bbox_lo, *bbox_hi, *cent_T, *cent_S, *cent_Sp, *cent_C;
+    float *gamma_conn, *gamma_proxy, *B_tab, *mis_tab, *pi_grid;
+} pb_tables_host;
+pb_status pb_tables_readback(pb_ctx *ctx, pb_tables_host *out);
 
 /* Traces cfg->spp iterations and adds them to the film. PB_ERR_TRUNCATED
  * if any estimate hit the cap (the film is still updated). */

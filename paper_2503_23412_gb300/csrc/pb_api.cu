@@ -12,27 +12,7 @@
 #include "pb_bvh.h"
 #include "pb_kernels.h"
 
-struct pb_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int num_sms = 1;
-    std::string err;
-    std::vector<void *> scene_mem, table_mem, pool_mem;
-    bool has_scene = false, has_tables = false;
-    DScene S{};
-    DTables T{};
-    float3 bbox_lo{}, bbox_hi{};
-    // pool capacity
-    Pool B{};
-    int cap_slots = 0, cap_ML = 0, cap_rep = 0, cap_KT = 0, cap_KS = 0, cap_KSp = 0;
-    float4 *Lbuf = nullptr;
-    uint32_t *sigbuf = nullptr;
-    int cap_Lslots = 0;
-    float *film = nullptr;
-    int64_t film_iters = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
+#include "pb_ctx.h"
 
 namespace {
 
@@ -116,7 +96,9 @@ pb_status ensure_pool(pb_ctx *ctx, int slots, int ML, int repeats, int npix) {
     CK(dalloc(o, &B.reptr, n * repeats));
     CK(dalloc(o, &B.rhat, n));
     CK(dalloc(o, &B.esig, n));
-    CK(dalloc(o, &B.work, (size_t)slots + 2));
+    CK(dalloc(o, &B.work, (size_t)slots + 4));
+    B.chain_cap = (int)std::min<size_t>(n * repeats, (size_t)1 << 18);
+    CK(dalloc(o, &B.chains, (size_t)B.chain_cap));
     CK(dalloc(o, &B.scratch, 2 * n));
     CK(dalloc(o, &B.counters, (size_t)CNT_N));
     CK(dalloc(o, &ctx->Lbuf, (size_t)slots * ctx->S.W * ctx->S.H));
@@ -155,6 +137,9 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
     P.trial_cap = c->trial_cap;
     P.L = c->max_depth - 1;
     P.npix = ctx->S.W * ctx->S.H;
+    P.count = c->count_traversal ? 1 : 0;
+    P.handoff = c->chain_handoff > 0 ? ((c->chain_handoff + 31) / 32) * 32 : 512;
+    P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     return P;
 }
 
@@ -218,8 +203,12 @@ void read_counters(pb_ctx *ctx, pb_stats *st) {
     st->n_conn = (int64_t)c[CNT_CONN];
     st->n_proxy = (int64_t)c[CNT_PROXY];
     st->n_proxy_ok = (int64_t)c[CNT_PROXY_OK];
-    st->n_node_fetch = (int64_t)c[CNT_NFETCH];
-    st->n_tri_test = (int64_t)c[CNT_TTEST];
+    st->eye_nodes = (int64_t)c[CNT_EYE_NODES];
+    st->eye_tris = (int64_t)c[CNT_EYE_TRIS];
+    st->eye_rays = (int64_t)c[CNT_EYE_RAYS];
+    st->rec_nodes = (int64_t)c[CNT_REC_NODES];
+    st->rec_tris = (int64_t)c[CNT_REC_TRIS];
+    st->rec_rays = (int64_t)c[CNT_REC_RAYS];
 }
 
 // ---- debug kernels --------------------------------------------------------
@@ -227,7 +216,7 @@ __global__ void k_trace(DScene S, const float *rays, int n, float *hits, int cou
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float *r = rays + 7 * (size_t)i;
-    TravCount tc{0, 0};
+    TravCount tc{0, 0, 0};
     Hit h = count ? closest_hit<true>(S, f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]), (int)r[6], &tc)
                   : closest_hit<false>(S, f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]), (int)r[6]);
     hits[4 * (size_t)i] = (float)h.tri;
@@ -248,6 +237,15 @@ __global__ void k_occ(DScene S, const float *seg, int n, int32_t *out) {
 }
 
 }  // namespace
+
+pb_status pb_ensure_pool(pb_ctx *ctx, int slots, int ML, int repeats) { return ensure_pool(ctx, slots, ML, repeats, 0); }
+pb_status pb_fail(pb_ctx *c, pb_status s, const std::string &m) { return fail(c, s, m); }
+pb_status pb_run_wave(pb_ctx *ctx, const KParams &P, int slots, uint32_t iter_base, bool with_light, bool with_recip,
+                      uint32_t *sig) {
+    return run_wave(ctx, P, slots, iter_base, with_light, with_recip, sig);
+}
+KParams pb_kparams(const pb_ctx *ctx, const pb_config *c) { return kparams(ctx, c); }
+pb_status pb_check_cfg(pb_ctx *ctx, const pb_config *c) { return check_cfg(ctx, c); }
 
 void launch_trace(const DScene &S, const float *rays, int n, float *hits, int count, unsigned long long *counters,
                   cudaStream_t st) {
@@ -452,6 +450,8 @@ pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *d) {
     S.W = W;
     S.H = H;
     float ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    ctx->scene_lo = make_float3(lo[0], lo[1], lo[2]);
+    ctx->scene_hi = make_float3(hi[0], hi[1], hi[2]);
     S.eps_t = 1e-5f * ext;
     const float *c = d->cam;
     float3 pos = make_float3(c[0], c[1], c[2]);
@@ -516,11 +516,7 @@ pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *t) {
     float ex = t->bbox_hi[0] - t->bbox_lo[0], ey = t->bbox_hi[1] - t->bbox_lo[1], ez = t->bbox_hi[2] - t->bbox_lo[2];
     ctx->S.lo = lo;
     ctx->S.ext = make_float3(ex > 0 ? ex : 1.0f, ey > 0 ? ey : 1.0f, ez > 0 ? ez : 1.0f);
-    // pool buffers depend on the table sizes
-    free_all(ctx->pool_mem);
-    ctx->cap_slots = ctx->cap_ML = 0;
-    ctx->Lbuf = nullptr;
-    ctx->sigbuf = nullptr;
+    // pool buffers that depend on the table sizes are re-checked by ensure_pool
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->has_tables = true;
     return PB_OK;
@@ -537,12 +533,26 @@ pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
     s = ensure_pool(ctx, slots, P.M * P.L, P.repeats, P.npix);
     if (s != PB_OK) return s;
     CK(cudaMemsetAsync(ctx->B.counters, 0, sizeof(unsigned long long) * CNT_N, ctx->stream));
+    int waves = (cfg->spp + slots - 1) / slots;
+    std::vector<cudaEvent_t> ev(5 * (size_t)std::max(waves, 0));
+    for (auto &e : ev) CK(cudaEventCreate(&e));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    for (int done = 0; done < cfg->spp;) {
+    int w = 0;
+    for (int done = 0; done < cfg->spp; ++w) {
         int ns = std::min(slots, cfg->spp - done);
-        s = run_wave(ctx, P, ns, (uint32_t)(cfg->iter0 + done), true, true, nullptr);
-        if (s != PB_OK) return s;
+        uint32_t base = (uint32_t)(cfg->iter0 + done);
+        cudaEvent_t *e = &ev[5 * (size_t)w];
+        CK(cudaEventRecord(e[0], ctx->stream));
+        launch_light_pass(ctx->S, P, ctx->B, ns, base, ctx->stream);
+        CK(cudaEventRecord(e[1], ctx->stream));
+        launch_pool_build(ctx->S, ctx->T, P, ctx->B, ns, ctx->stream);
+        CK(cudaEventRecord(e[2], ctx->stream));
+        launch_recip(ctx->S, ctx->T, P, ctx->B, ns, base, ctx->num_sms, ctx->stream);
+        CK(cudaEventRecord(e[3], ctx->stream));
+        launch_eye(ctx->S, ctx->T, P, ctx->B, ns, base, ctx->Lbuf, nullptr, ctx->stream);
+        CK(cudaEventRecord(e[4], ctx->stream));
         launch_film_add(P, ns, ctx->Lbuf, ctx->film, ctx->stream);
+        CK(cudaGetLastError());
         done += ns;
     }
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -554,6 +564,21 @@ pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     st.ms = ms;
     st.mpaths_per_s = ms > 0 ? (double)P.npix * cfg->spp / (ms * 1e-3) / 1e6 : 0.0;
+    for (int i = 0; i < waves; ++i) {
+        float a = 0, b = 0, c = 0, d = 0;
+        cudaEvent_t *e = &ev[5 * (size_t)i];
+        cudaEventElapsedTime(&a, e[0], e[1]);
+        cudaEventElapsedTime(&b, e[1], e[2]);
+        cudaEventElapsedTime(&c, e[2], e[3]);
+        cudaEventElapsedTime(&d, e[3], e[4]);
+        st.ms_light += a;
+        st.ms_pool += b;
+        st.ms_recip += c;
+        st.ms_eye += d;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    st.n_waves = waves;
+    st.n_launches = 10 * (int64_t)waves;  // light, pool, bucket, cdf, offsets, recip x2, finish, eye, film
     read_counters(ctx, &st);
     if (stats) *stats = st;
     if (st.n_truncated > 0) return fail(ctx, PB_ERR_TRUNCATED, "reciprocal estimate hit the trial cap");

@@ -387,6 +387,11 @@ struct Hit {
     float t, b1, b2;
 };
 
+// traversal work counters (node visits of 64 B, triangle tests of 48 B, rays)
+struct TravCount {
+    uint32_t nodes, tris, rays;
+};
+
 __device__ __forceinline__ void tri_test(const DScene &S, int slot, float3 o, float3 d, int skip, Hit &h) {
     const float4 *T = S.itri + 3 * (size_t)slot;
     float4 v0 = __ldg(T), e1 = __ldg(T + 1), e2 = __ldg(T + 2);
@@ -463,16 +468,13 @@ __device__ __forceinline__ float3 safe_inv(float3 d) {
     return f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
 }
 
-struct TravCount {
-    uint32_t nodes, tris;
-};
-
+// closest hit starting from a known candidate `h` (h.tri = -1, h.t = inf for
+// a plain query): only triangles with a smaller t (or the same t and a lower
+// index) replace it, so the result equals the unrestricted closest hit
 template <bool COUNT>
-__device__ __forceinline__ Hit closest_hit(const DScene &S, float3 o, float3 d, int skip, TravCount *cnt = nullptr) {
-    Hit h;
-    h.tri = -1;
-    h.t = INFINITY;
-    h.b1 = h.b2 = 0.0f;
+__device__ __forceinline__ Hit closest_hit_from(const DScene &S, float3 o, float3 d, int skip, Hit h,
+                                                TravCount *cnt = nullptr) {
+    if (COUNT) cnt->rays++;
     float3 inv = safe_inv(d);
     int node = 0;
     uint64_t trail = 0;
@@ -518,10 +520,67 @@ __device__ __forceinline__ Hit closest_hit(const DScene &S, float3 o, float3 d, 
     return h;
 }
 
+template <bool COUNT>
+__device__ __forceinline__ Hit closest_hit(const DScene &S, float3 o, float3 d, int skip, TravCount *cnt = nullptr) {
+    Hit h;
+    h.tri = -1;
+    h.t = INFINITY;
+    h.b1 = h.b2 = 0.0f;
+    return closest_hit_from<COUNT>(S, o, d, skip, h, cnt);
+}
+
+// Closest hit of a ray that only matters if it ends on an emitter: the
+// emitter triangles are tested first (same predicate as the traversal); if
+// none is hit the answer "no emitter is the closest hit" needs no traversal,
+// else the traversal is bounded by the nearest emitter hit. Returns the
+// closest hit when it lies on an emitter, otherwise tri = -1.
+template <bool COUNT>
+__device__ __forceinline__ Hit closest_emitter_hit(const DScene &S, float3 o, float3 d, int skip,
+                                                   TravCount *cnt = nullptr) {
+    Hit e;
+    e.tri = -1;
+    e.t = INFINITY;
+    e.b1 = e.b2 = 0.0f;
+    for (int i = 0; i < S.ne; ++i) {
+        int id = S.etri[i];
+        if (id == skip) continue;
+        const float4 *T = S.stri + 4 * (size_t)id;
+        float3 v0 = xyz(T[0]), E1 = xyz(T[1]), E2 = xyz(T[2]);
+        float3 pv = cross(d, E2);
+        float det = dot(E1, pv);
+        if (det == 0.0f) continue;
+        float inv = 1.0f / det;
+        float3 tv = o - v0;
+        float u = dot(tv, pv) * inv;
+        if (u < 0.0f || u > 1.0f) continue;
+        float3 qv = cross(tv, E1);
+        float v = dot(d, qv) * inv;
+        if (v < 0.0f || u + v > 1.0f) continue;
+        float t = dot(E2, qv) * inv;
+        if (!(t > S.eps_t)) continue;
+        if (t < e.t || (t == e.t && id < e.tri)) {
+            e.tri = id;
+            e.t = t;
+            e.b1 = u;
+            e.b2 = v;
+        }
+    }
+    if (e.tri < 0) return e;
+    Hit h = closest_hit_from<COUNT>(S, o, d, skip, e, cnt);
+    int em = __float_as_int(S.stri[4 * (size_t)h.tri + 3].w);
+    if (em < 0) h.tri = -1;
+    return h;
+}
+
+// emitter lists longer than this use the plain closest hit
+#define PB_EMITTER_LIST_MAX 64
+
 // any hit strictly inside the open segment a -> b (parameter in (1e-4, 1-1e-4))
-__device__ __forceinline__ bool occluded(const DScene &S, float3 a, float3 b, int s1, int s2) {
+template <bool COUNT = false>
+__device__ __forceinline__ bool occluded(const DScene &S, float3 a, float3 b, int s1, int s2, TravCount *cnt = nullptr) {
     float3 d = b - a;
     float3 inv = safe_inv(d);
+    if (COUNT) cnt->rays++;
     int node = 0;
     uint64_t trail = 0;
     for (int guard = 0; guard < (1 << 22); ++guard) {
@@ -529,16 +588,21 @@ __device__ __forceinline__ bool occluded(const DScene &S, float3 a, float3 b, in
         float tl, tr;
         int cl, cr;
         child_boxes(S, node, a, inv, 1.0f, hL, hR, tl, tr, cl, cr);
+        if (COUNT) cnt->nodes++;
         if (hL && cl < 0) {
             int v = -cl - 1, first = v >> 4, n = v & 15;
-            for (int i = 0; i < n; ++i)
+            for (int i = 0; i < n; ++i) {
+                if (COUNT) cnt->tris++;
                 if (seg_test(S, first + i, a, d, s1, s2)) return true;
+            }
             hL = false;
         }
         if (hR && cr < 0) {
             int v = -cr - 1, first = v >> 4, n = v & 15;
-            for (int i = 0; i < n; ++i)
+            for (int i = 0; i < n; ++i) {
+                if (COUNT) cnt->tris++;
                 if (seg_test(S, first + i, a, d, s1, s2)) return true;
+            }
             hR = false;
         }
         if (hL && hR) {

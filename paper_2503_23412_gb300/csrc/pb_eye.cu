@@ -45,12 +45,16 @@ __device__ __forceinline__ int select_cdf(const float *cdf, int K, float u) {
     return lo;
 }
 
+__device__ __forceinline__ float lum(float3 c) { return (c.x + c.y + c.z) * (1.0f / 3.0f); }
+
 __device__ __forceinline__ float mis_cell(const DTables &T, int u, int Sp, int C) {
     return T.mis[((u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base,
                                              float4 *Lbuf, uint32_t *sigbuf) {
+    TravCount tc{0, 0, 0};
     int pix = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = blockIdx.y;
     if (pix >= P.npix) return;
@@ -68,8 +72,6 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
     float3 beta = f3(1, 1, 1);
     int tile = (py / T.tile) * T.gw + (px / T.tile);
     float pi_pix = T.pi[tile];
-    const float eps_pdf = 0.0f;
-    (void)eps_pdf;
     EV zp, zpp;               // z_{a-1}, z_{a-2}
     zp.p = S.cpos;
     zp.nonS = true;
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
     int pstate = 0, f_idx = 0, Sp_f1 = 0;
     float rev_f1 = 1.0f;
     unsigned long long n_conn = 0, n_proxy = 0, n_proxy_ok = 0;
-    Hit h = closest_hit<false>(S, S.cpos, d, -1);
+    Hit h = closest_hit<COUNT>(S, S.cpos, d, -1, &tc);
     int a = 1;
     while (h.tri >= 0) {
         Vtx z = vertex_at(S, h.tri, h.b1, h.b2);
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                     w = 1.0f / (1.0f + Epr + pt);
                 }
                 L = L + mul(beta, Le) * w;
+                if (P.acc.tile_all) atomicAdd(&P.acc.tile_all[tile], lum(mul(beta, Le)) * w);
             }
         }
         if (absorbing(S, z, we)) break;
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                 float b1, b2;
                 sample_light(S, R.u(3), R.u(4), R.u(5), lt, b1, b2);
                 Vtx y = vertex_at(S, lt, b1, b2);
-                bool vis = !occluded(S, z.p, y.p, z.tri, y.tri);
+                bool vis = !occluded<COUNT>(S, z.p, y.p, z.tri, y.tri, &tc);
                 sig = sig_upd(sig, 0xA0000000u | (uint32_t)lt);
                 sig = sig_upd(sig, vis ? 1u : 0u);
                 if (vis) {
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                         }
                         float w = 1.0f / (1.0f + Lsum0 + Ea + pt);
                         L = L + c * w;
+                        if (P.acc.tile_all) atomicAdd(&P.acc.tile_all[tile], lum(c) * w);
                     }
                 }
             }
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                         float4 va = B.valpha[so + fixed], vm = B.vmis[so + fixed];
                         float3 yp = xyz(vp), yn = xyz(vn), ywl = xyz(vw);
                         int ymat = __float_as_int(vp.w), ytri = __float_as_int(vn.w);
-                        bool vis = !occluded(S, z.p, yp, z.tri, ytri);
+                        bool vis = !occluded<COUNT>(S, z.p, yp, z.tri, ytri, &tc);
                         sig = sig_upd(sig, vis ? 1u : 0u);
                         if (vis) {
                             float3 dd = yp - z.p;
@@ -240,6 +244,10 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                                 }
                                 float w = 1.0f / (1.0f + Ls + Ea);
                                 L = L + c * w;
+                                if (P.acc.conn) {
+                                    atomicAdd(&P.acc.tile_all[tile], lum(c) * w);
+                                    atomicAdd(&P.acc.conn[(size_t)Tl * T.KS + Ssel], lum(c));
+                                }
                             }
                         }
                     }
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                         int sl = u + (type ? 2 : 1);
                         int status = 0;
                         if (sl + a > P.max_depth) status = 1;
-                        else if (occluded(S, z.p, gs[0].p, z.tri, gs[0].tri)) status = 2;
+                        else if (occluded<COUNT>(S, z.p, gs[0].p, z.tri, gs[0].tri, &tc)) status = 2;
                         else {
                             float3 prev = z.p;
                             for (int r = 1; r <= u && !status; ++r) {
@@ -286,7 +294,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                                     status = 3;
                                     break;
                                 }
-                                Hit hh = closest_hit<false>(S, g.p, ws, g.tri);
+                                Hit hh = closest_hit<COUNT>(S, g.p, ws, g.tri, &tc);
                                 sig = sig_upd(sig, hh.tri >= 0 ? (uint32_t)hh.tri : 0x0FFFFFFFu);
                                 if (hh.tri < 0) {
                                     status = 4;
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                                 }
                                 prev = g.p;
                             }
-                            if (!status && type && occluded(S, gs[u].p, H.p, gs[u].tri, H.tri)) status = 6;
+                            if (!status && type && occluded<COUNT>(S, gs[u].p, H.p, gs[u].tri, H.tri, &tc)) status = 6;
                         }
                         sig = sig_upd(sig, 0xD0000000u | (uint32_t)status);
                         if (!status) {
@@ -360,6 +368,11 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                                 }
                                 L = L + c * w;
                                 n_proxy_ok++;
+                                if (P.acc.proxy) {
+                                    atomicAdd(&P.acc.tile_all[tile], lum(c) * w);
+                                    atomicAdd(&P.acc.tile_proxy[tile], lum(c) * w);
+                                    atomicAdd(&P.acc.proxy[(size_t)Tl * T.KSp + Ssel], lum(c));
+                                }
                             }
                         }
                     }
@@ -401,7 +414,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
         zp.nonS = nonS;
         zp.rev = rev_a;
         d = wl;
-        h = closest_hit<false>(S, z.p, d, z.tri);
+        h = closest_hit<COUNT>(S, z.p, d, z.tri, &tc);
         ++a;
     }
     size_t o = (size_t)slot * P.npix + pix;
@@ -410,6 +423,11 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
     if (n_conn) atomicAdd(&B.counters[CNT_CONN], n_conn);
     if (n_proxy) atomicAdd(&B.counters[CNT_PROXY], n_proxy);
     if (n_proxy_ok) atomicAdd(&B.counters[CNT_PROXY_OK], n_proxy_ok);
+    if (COUNT) {
+        atomicAdd(&B.counters[CNT_EYE_NODES], (unsigned long long)tc.nodes);
+        atomicAdd(&B.counters[CNT_EYE_TRIS], (unsigned long long)tc.tris);
+        atomicAdd(&B.counters[CNT_EYE_RAYS], (unsigned long long)tc.rays);
+    }
 }
 
 __global__ void k_film_add(KParams P, int slots, const float4 *Lbuf, float *film) {
@@ -432,7 +450,8 @@ __global__ void k_film_add(KParams P, int slots, const float4 *Lbuf, float *film
 void launch_eye(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                 float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st) {
     dim3 grid((P.npix + 127) / 128, slots);
-    k_eye<<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
+    if (P.count) k_eye<true><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
+    else k_eye<false><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
 }
 
 void launch_film_add(const KParams &P, int slots, const float4 *Lbuf, float *film, cudaStream_t st) {

@@ -5,12 +5,36 @@
 
 #include "pb_device.cuh"
 
+// Accumulators of the table-learning eye passes (null when rendering).
+struct LearnAcc {
+    float *conn;        // KT*KS: unweighted connection contribution luminance per (T, S)
+    float *proxy;       // KT*KSp: unweighted proxy contribution luminance per (T, S')
+    float *tile_all;    // per tile: weighted contribution luminance
+    float *tile_proxy;  // per tile: weighted proxy contribution luminance
+};
+
 // Render parameters as the kernels see them.
 struct KParams {
     uint32_t seed;
     int max_depth, M, M_p, repeats, proxy, conn, trial_cap;
     int L;          // light-path vertex slots = max_depth - 1
     int npix;
+    int count;      // 1: count traversal work (node fetches, triangle tests, rays)
+    int handoff;    // estimator nodes walked by a warp before a block continues the chain
+    LearnAcc acc;
+};
+
+// Walk state of a reciprocal estimate handed from a warp to a block: the next
+// pre-order node index, the running sums, the sign of the next node and the
+// stack of pending sibling groups (sign, remaining count).
+#define PB_MAXF 48
+struct ChainState {
+    int slot, k, rep, next;
+    double sum_t;
+    float cur_sign;
+    int sp;
+    float fr_sign[PB_MAXF];
+    int fr_rem[PB_MAXF];
 };
 
 // Device buffers of the iterations in flight ("slots"). Per-light-vertex
@@ -34,12 +58,17 @@ struct Pool {
     int32_t *reptr;
     float *rhat;                                   // per entry: averaged reciprocal estimate
     uint32_t *esig;
-    int32_t *work;                                 // work counter, per-slot work offsets
+    int32_t *work;                                 // work counters, per-slot work offsets
+    struct ChainState *chains;                     // estimates continued by whole blocks
+    int chain_cap;
     int32_t *scratch;                              // 2 * slots * ML ints for the bucket sort
     unsigned long long *counters;                  // stats
 };
 
-enum { CNT_ENTRIES = 0, CNT_TRUNC, CNT_NODES, CNT_CONN, CNT_PROXY, CNT_PROXY_OK, CNT_NFETCH, CNT_TTEST, CNT_N };
+enum {
+    CNT_ENTRIES = 0, CNT_TRUNC, CNT_NODES, CNT_CONN, CNT_PROXY, CNT_PROXY_OK, CNT_NFETCH, CNT_TTEST,
+    CNT_EYE_NODES, CNT_EYE_TRIS, CNT_EYE_RAYS, CNT_REC_NODES, CNT_REC_TRIS, CNT_REC_RAYS, CNT_N
+};
 
 void launch_light_pass(const DScene &S, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                        cudaStream_t st);

@@ -14,31 +14,9 @@
 #include <cstdio>
 
 #include "pb_kernels.h"
+#include "pb_estimator.cuh"
 
 namespace {
-
-__device__ __forceinline__ float3 fwd_cos_over_d2(float3 a, float3 b, float3 nb, float3 &w, float &d2) {
-    float3 d = b - a;
-    d2 = len2(d);
-    w = d * (1.0f / sqrtf(d2));
-    return f3(fabsf(dot(nb, w)), 0, 0);
-}
-
-// light-tracer area density of ys[j] (Eq. tracingPdf)
-__device__ float fwd_density(const DScene &S, const Vtx *ys, int j) {
-    if (j == 0) return light_pdf(S, ys[0].tri);
-    float3 d = ys[j].p - ys[j - 1].p;
-    float d2 = len2(d);
-    float3 w = d * (1.0f / sqrtf(d2));
-    float cn = fabsf(dot(ys[j].n, w));
-    if (j == 1) {
-        float c0 = dot(ys[0].n, w);
-        if (c0 <= 0.0f) return 0.0f;
-        return (c0 / PB_PI) * cn / d2;
-    }
-    const DMat &m = S.mats[ys[j - 1].mat];
-    return bsdf_pdf(m, ys[j - 1].n, dirto(ys[j - 1].p, ys[j - 2].p), w) * cn / d2;
-}
 
 // ---------------------------------------------------------------------------
 __global__ void k_light_pass(DScene S, KParams P, Pool B, uint32_t iter_base) {
@@ -288,128 +266,6 @@ __global__ void k_cdf(DTables T, Pool B) {
     if (threadIdx.x == 0) *Z = Zv;
 }
 
-// ---------------------------------------------------------------------------
-// Supporting distribution of an incomplete sub-path (Sec. 5.3) and the
-// integrand f = p(g | h_c, w_c) p(y_{s-1} | g, h_c) (Sec. 5.2).
-struct Entry {
-    Vtx Y, H;
-    int u, type;
-};
-
-__device__ __forceinline__ float cosY_pdf(const DScene &S, const Vtx &Y, float3 w) {
-    const DMat &m = S.mats[Y.mat];
-    float c = dot(Y.n, w);
-    if (m.kind == MK_DIELECTRIC) return fabsf(c) / (2.0f * PB_PI);
-    return c > 0.0f ? c / PB_PI : 0.0f;
-}
-
-__device__ float q_from_Y(const DScene &S, const Vtx *gs, int u) {
-    float3 d = gs[1].p - gs[0].p;
-    float d2 = len2(d);
-    float3 w = d * (1.0f / sqrtf(d2));
-    float q = cosY_pdf(S, gs[0], w) * fabsf(dot(gs[1].n, w)) / d2;
-    for (int r = 1; r < u; ++r) {
-        const DMat &m = S.mats[gs[r].mat];
-        float3 dd = gs[r + 1].p - gs[r].p;
-        float dd2 = len2(dd);
-        float3 ww = dd * (1.0f / sqrtf(dd2));
-        q *= bsdf_pdf(m, gs[r].n, dirto(gs[r].p, gs[r - 1].p), ww) * fabsf(dot(gs[r + 1].n, ww)) / dd2;
-    }
-    return q;
-}
-
-__device__ void eval_fq(const DScene &S, const Entry &E, const Vtx *gs, bool compA, bool vis, float &f, float &q) {
-    int u = E.u;
-    Vtx ys[8];
-    int n = 0;
-    if (E.type == 1) ys[n++] = E.H;
-    for (int r = u; r >= 1; --r) ys[n++] = gs[r];
-    ys[n++] = E.Y;
-    bool ok = vis;
-    for (int j = 1; j < n && ok; ++j) {
-        const DMat &m = S.mats[ys[j].mat];
-        int want = (j == n - 1) ? 1 : ((E.type == 1 && j == 1) ? 0 : 1);
-        if (m.specular != want) ok = false;
-        if (absorbing(S, ys[j], dirto(ys[j].p, ys[j - 1].p))) ok = false;
-    }
-    if (E.type == 0 && !S.mats[ys[0].mat].emitter) ok = false;
-    float fv = 0.0f;
-    if (ok) {
-        fv = 1.0f;
-        for (int j = (E.type == 1 ? 1 : 0); j < n; ++j) fv *= fwd_density(S, ys, j);
-    }
-    float qB = (vis || !compA) ? q_from_Y(S, gs, u) : 0.0f;
-    float qv = qB;
-    if (u == 1) {
-        float qA;
-        if (E.type == 0) {
-            qA = light_pdf(S, gs[1].tri);
-        } else {
-            float3 d = gs[1].p - E.H.p;
-            float d2 = len2(d);
-            float3 w = d * (1.0f / sqrtf(d2));
-            float c0 = dot(E.H.n, w);
-            bool visHA = compA ? true : vis;
-            qA = (c0 > 0.0f && visHA) ? (c0 / PB_PI) * fabsf(dot(gs[1].n, w)) / d2 : 0.0f;
-        }
-        qv = 0.5f * qA + 0.5f * qB;
-    }
-    f = fv;
-    q = qv;
-}
-
-__device__ __forceinline__ bool trace_vtx(const DScene &S, float3 o, float3 w, int skip, Vtx &out) {
-    Hit h = closest_hit<false>(S, o, w, skip);
-    if (h.tri < 0) return false;
-    out = vertex_at(S, h.tri, h.b1, h.b2);
-    return true;
-}
-
-// one draw from q; returns f/q. Dims: 0 component, 1-3 light sample, 4-5
-// cosine direction, 6+3(r-1) BSDF at the r-th specular vertex, 18 RRS
-// uniform, 19 hemisphere side.
-__device__ float entry_ratio(const DScene &S, const Entry &E, Rng &R) {
-    int u = E.u;
-    Vtx gs[6];
-    gs[0] = E.Y;
-    bool compA = (u == 1) && (R.u(0) < 0.5f);
-    float f, q;
-    if (compA && E.type == 0) {
-        int tri;
-        float b1, b2;
-        if (!sample_light(S, R.u(1), R.u(2), R.u(3), tri, b1, b2)) return 0.0f;
-        gs[1] = vertex_at(S, tri, b1, b2);
-        bool vis = !occluded(S, gs[1].p, E.Y.p, gs[1].tri, E.Y.tri);
-        eval_fq(S, E, gs, true, vis, f, q);
-        return q > 0.0f ? f / q : 0.0f;
-    }
-    if (compA && E.type == 1) {
-        float3 w = cosine_dir(E.H.n, R.u(4), R.u(5));
-        if (!trace_vtx(S, E.H.p, w, E.H.tri, gs[1])) return 0.0f;
-        bool vis = !occluded(S, gs[1].p, E.Y.p, gs[1].tri, E.Y.tri);
-        eval_fq(S, E, gs, true, vis, f, q);
-        return q > 0.0f ? f / q : 0.0f;
-    }
-    const DMat &mY = S.mats[E.Y.mat];
-    float3 nside = E.Y.n;
-    if (mY.kind == MK_DIELECTRIC && !(R.u(19) < 0.5f)) nside = -nside;
-    float3 w = cosine_dir(nside, R.u(4), R.u(5));
-    if (!trace_vtx(S, E.Y.p, w, E.Y.tri, gs[1])) return 0.0f;
-    for (int r = 1; r < u; ++r) {
-        const DMat &m = S.mats[gs[r].mat];
-        float3 wg = dirto(gs[r].p, gs[r - 1].p);
-        if (!m.specular || absorbing(S, gs[r], wg)) return 0.0f;
-        float3 ws;
-        int d0 = 6 + 3 * (r - 1);
-        if (!bsdf_sample(m, gs[r].n, wg, R.u(d0), R.u(d0 + 1), R.u(d0 + 2), ws)) return 0.0f;
-        if (!trace_vtx(S, gs[r].p, ws, gs[r].tri, gs[r + 1])) return 0.0f;
-    }
-    bool vis = true;
-    if (E.type == 1) vis = !occluded(S, gs[u].p, E.H.p, gs[u].tri, E.H.tri);
-    eval_fq(S, E, gs, false, vis, f, q);
-    return q > 0.0f ? f / q : 0.0f;
-}
-
 __device__ __forceinline__ Entry load_entry(const DScene &S, const KParams &P, const Pool &B, int slot, int k,
                                             int &Sp, int &C) {
     size_t o = (size_t)slot * B.ML;
@@ -427,22 +283,27 @@ __device__ __forceinline__ Entry load_entry(const DScene &S, const KParams &P, c
     return E;
 }
 
-#define MAXF 48
+#define MAXF PB_MAXF
+#define MAXF1 8          // walk frames a warp keeps; deeper walks continue in a block
 
-// Warp-parallel evaluation of Alg. I~. The tree's nodes are numbered in
+// Phase 1: one warp per (entry, repeat). The tree's nodes are numbered in
 // pre-order, so node v's sample depends only on v: the 32 lanes draw nodes
-// base..base+31 together, then every lane replays the same sequential scan
-// (children counts and signs), keeping the DFS frames in registers-backed
-// local memory. Speculative nodes past the end are discarded.
+// base..base+31 together, then every lane replays the same sequential walk
+// (children counts and signs, DFS frames in local memory). Speculative nodes
+// past the end are discarded. Chains still running are
+// queued for phase 2 with their walk state (after P.handoff nodes).
+template <bool COUNT>
 __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, Pool B, int slots, uint32_t iter_base) {
     int lane = threadIdx.x & 31;
+    TravCount tc{0, 0, 0};
     int32_t *counter = B.work;
+    int32_t *chain_count = B.work + 2 + slots;
     const int32_t *offs = B.work + 1;   // per slot: first work item, slots+1 entries
     while (true) {
         int item = 0;
         if (lane == 0) item = atomicAdd(counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= offs[slots]) return;
+        if (item >= offs[slots]) break;
         int slot = 0;
         while (item >= offs[slot + 1]) ++slot;
         int local = item - offs[slot];
@@ -451,43 +312,67 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
         Entry E = load_entry(S, P, B, slot, k, Sp, C);
         float Bv = T.Bt[((E.u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
         float invB = 1.0f / Bv;
-        float sum_t = 0.0f;
+        double sum_t = 0.0;   // long chains add thousands of terms
         int nodes = 0;
-        bool done = false, trunc = false;
-        float fr_sign[MAXF];
-        int fr_rem[MAXF];
+        bool done = false, trunc = false, handed = false;
+        float fr_sign[MAXF1];
+        int fr_rem[MAXF1];
         int sp = 0;
         float cur_sign = 1.0f;
+        bool deep = false;   // the walk needs more frames than a warp keeps
         for (int base = 0; !done; base += 32) {
+            if (base >= P.handoff || deep) {
+                int slot_q = 0;
+                if (lane == 0) slot_q = atomicAdd(chain_count, 1);
+                slot_q = __shfl_sync(0xffffffffu, slot_q, 0);
+                if (slot_q < B.chain_cap) {
+                    if (lane == 0) {
+                        ChainState &cs = B.chains[slot_q];
+                        cs.slot = slot; cs.k = k; cs.rep = rep; cs.next = base;
+                        cs.sum_t = sum_t; cs.cur_sign = cur_sign; cs.sp = sp;
+                        for (int i = 0; i < sp; ++i) { cs.fr_sign[i] = fr_sign[i]; cs.fr_rem[i] = fr_rem[i]; }
+                    }
+                    handed = true;
+                    break;
+                }
+                if (deep) {   // no room to hand over a deep walk: stop and report truncation
+                    done = true;
+                    trunc = true;
+                    break;
+                }
+            }
             int v = base + lane;
             float g = 1.0f;
             int nch = 0;
             if (v < P.trial_cap) {
                 Rng R;
                 R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
-                float ratio = entry_ratio(S, E, R);
+                float ratio = entry_ratio<COUNT>(S, E, R, &tc);
                 g = 1.0f - ratio * invB;
                 float r = fabsf(g);
                 nch = (int)floorf(r);
                 if (R.u(18) < r - (float)nch) nch += 1;
             }
+            // the walk stops before a node that would need a frame beyond MAXF1;
+            // the block phase resumes from that node with the full stack
+            int stop = 32;
             for (int j = 0; j < 32; ++j) {
                 float gj = __shfl_sync(0xffffffffu, g, j);
                 int nj = __shfl_sync(0xffffffffu, nch, j);
-                if (done) continue;
+                if (done || j >= stop) continue;
                 if (base + j >= P.trial_cap) {
                     done = true;
                     trunc = true;
                     continue;
                 }
-                sum_t += cur_sign * gj * invB;
+                if (nj >= 1 && sp >= MAXF1) {
+                    stop = j;
+                    deep = true;
+                    continue;
+                }
+                sum_t += (double)(cur_sign * gj * invB);
                 nodes++;
                 if (nj >= 1) {
-                    if (sp >= MAXF) {
-                        done = true;
-                        trunc = true;
-                        continue;
-                    }
                     fr_sign[sp] = cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
                     fr_rem[sp] = nj;
                     ++sp;
@@ -499,19 +384,207 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
                 cur_sign = fr_sign[sp - 1];
                 if (--fr_rem[sp - 1] == 0) --sp;
             }
+            if (deep) base = base + stop - 32;   // resume at node base + stop
         }
-        if (lane == 0) {
+        if (lane == 0 && !handed) {
             size_t o = ((size_t)slot * B.ML + k) * P.repeats + rep;
-            B.rep[o] = invB + sum_t;
+            B.rep[o] = (float)((double)invB + sum_t);
             B.repn[o] = (float)nodes;
             B.reptr[o] = trunc ? 1 : 0;
         }
+    }
+    if (COUNT) {
+        atomicAdd(&B.counters[CNT_REC_NODES], (unsigned long long)tc.nodes);
+        atomicAdd(&B.counters[CNT_REC_TRIS], (unsigned long long)tc.tris);
+        atomicAdd(&B.counters[CNT_REC_RAYS], (unsigned long long)tc.rays);
+    }
+}
+
+#define PH2_THREADS 256
+#define PH2_NPT 8
+#define PH2_BATCH (PH2_THREADS * PH2_NPT)
+
+// Phase 2: a block per long chain. Each batch draws PH2_BATCH consecutive
+// nodes in parallel. While every pending node has sign +1 and the batch has
+// no negative g, the walk reduces to counts: pending_v = pending - 1 + n_v
+// per node, the chain ends at the first node where pending reaches 0, and
+// the estimate adds g_v / B for the nodes up to there -- a block prefix sum.
+// Otherwise one thread replays the exact sequential walk over the batch.
+template <bool COUNT>
+__global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T, KParams P, Pool B, int slots,
+                                                            uint32_t iter_base) {
+    __shared__ float sg[PH2_BATCH];
+    __shared__ int sn[PH2_BATCH];
+    __shared__ int s_item, s_done, s_end, s_neg;
+    __shared__ double s_sum;
+    __shared__ int s_pending[PH2_THREADS];
+    __shared__ double s_part[PH2_THREADS];
+    __shared__ ChainState st;
+    TravCount tc{0, 0, 0};
+    int tid = threadIdx.x;
+    int32_t *next_item = B.work + 2 + slots + 1;
+    int nitems = min(B.work[2 + slots], B.chain_cap);
+    while (true) {
+        if (tid == 0) s_item = atomicAdd(next_item, 1);
+        __syncthreads();
+        int item = s_item;
+        if (item >= nitems) break;
+        if (tid == 0) st = B.chains[item];
+        __syncthreads();
+        int slot = st.slot, k = st.k, rep = st.rep;
+        int Sp, C;
+        Entry E = load_entry(S, P, B, slot, k, Sp, C);
+        float invB = 1.0f / T.Bt[((E.u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
+        bool trunc = false;
+        int done = 0;
+        while (!done) {
+            int base = st.next;
+            // draw the batch
+            for (int j = 0; j < PH2_NPT; ++j) {
+                int idx = tid * PH2_NPT + j;
+                int v = base + idx;
+                float g = 1.0f;
+                int nch = 0;
+                if (v < P.trial_cap) {
+                    Rng R;
+                    R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
+                    float ratio = entry_ratio<COUNT>(S, E, R, &tc);
+                    g = 1.0f - ratio * invB;
+                    float r = fabsf(g);
+                    nch = (int)floorf(r);
+                    if (R.u(18) < r - (float)nch) nch += 1;
+                }
+                sg[idx] = g;
+                sn[idx] = nch;
+            }
+            if (tid == 0) {
+                bool pos = st.cur_sign > 0.0f;
+                for (int i = 0; i < st.sp; ++i) pos = pos && st.fr_sign[i] > 0.0f;
+                s_neg = pos ? 0 : 1;
+            }
+            __syncthreads();
+            // any negative g in the batch?
+            int anyneg = 0;
+            for (int j = 0; j < PH2_NPT; ++j) anyneg |= (sg[tid * PH2_NPT + j] < 0.0f);
+            anyneg = __syncthreads_or(anyneg | s_neg);
+            if (!anyneg && base + PH2_BATCH <= P.trial_cap) {
+                // parallel walk: pending counts by a block prefix sum
+                int pend0 = 1;
+                for (int i = 0; i < st.sp; ++i) pend0 += st.fr_rem[i];
+                int loc[PH2_NPT];
+                int acc = 0;
+                for (int j = 0; j < PH2_NPT; ++j) {
+                    acc += sn[tid * PH2_NPT + j] - 1;
+                    loc[j] = acc;
+                }
+                s_pending[tid] = acc;
+                __syncthreads();
+                for (int off = 1; off < PH2_THREADS; off <<= 1) {
+                    int x = tid >= off ? s_pending[tid - off] : 0;
+                    __syncthreads();
+                    s_pending[tid] += x;
+                    __syncthreads();
+                }
+                int excl = pend0 + s_pending[tid] - acc;
+                int first = PH2_BATCH;
+                for (int j = 0; j < PH2_NPT; ++j)
+                    if (excl + loc[j] <= 0) {
+                        first = tid * PH2_NPT + j;
+                        break;
+                    }
+                if (tid == 0) s_end = PH2_BATCH;
+                __syncthreads();
+                if (first < PH2_BATCH) atomicMin(&s_end, first);
+                __syncthreads();
+                int end = s_end;   // last node processed (inclusive), or PH2_BATCH if none
+                double part = 0.0;
+                for (int j = 0; j < PH2_NPT; ++j) {
+                    int idx = tid * PH2_NPT + j;
+                    if (idx <= end && idx < PH2_BATCH) part += (double)(sg[idx] * invB);
+                }
+                s_part[tid] = part;
+                __syncthreads();
+                for (int off = PH2_THREADS / 2; off > 0; off >>= 1) {
+                    if (tid < off) s_part[tid] += s_part[tid + off];
+                    __syncthreads();
+                }
+                if (tid == 0) {
+                    st.sum_t += s_part[0];
+                    if (end < PH2_BATCH) {
+                        st.next = base + end + 1;
+                        s_done = 1;
+                    } else {
+                        int pend = pend0 + s_pending[PH2_THREADS - 1];
+                        st.next = base + PH2_BATCH;
+                        st.cur_sign = 1.0f;
+                        st.sp = 0;
+                        if (pend - 1 > 0) {
+                            st.fr_sign[0] = 1.0f;
+                            st.fr_rem[0] = pend - 1;
+                            st.sp = 1;
+                        }
+                        s_done = 0;
+                    }
+                }
+            } else if (tid == 0) {
+                // exact sequential walk over the batch
+                s_done = 0;
+                for (int j = 0; j < PH2_BATCH; ++j) {
+                    int v = base + j;
+                    if (v >= P.trial_cap) {
+                        s_done = 1;
+                        trunc = true;
+                        st.next = v;
+                        break;
+                    }
+                    float gj = sg[j];
+                    int nj = sn[j];
+                    st.sum_t += (double)(st.cur_sign * gj * invB);
+                    if (nj >= 1) {
+                        if (st.sp >= MAXF) {
+                            s_done = 1;
+                            trunc = true;
+                            st.next = v + 1;
+                            break;
+                        }
+                        st.fr_sign[st.sp] = st.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                        st.fr_rem[st.sp] = nj;
+                        st.sp++;
+                    }
+                    if (st.sp == 0) {
+                        s_done = 1;
+                        st.next = v + 1;
+                        break;
+                    }
+                    st.cur_sign = st.fr_sign[st.sp - 1];
+                    if (--st.fr_rem[st.sp - 1] == 0) st.sp--;
+                    st.next = v + 1;
+                }
+            }
+            __syncthreads();
+            done = s_done;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            size_t o = ((size_t)slot * B.ML + k) * P.repeats + rep;
+            B.rep[o] = (float)((double)invB + st.sum_t);
+            B.repn[o] = (float)st.next;
+            B.reptr[o] = trunc ? 1 : 0;
+        }
+        __syncthreads();
+    }
+    if (COUNT) {
+        atomicAdd(&B.counters[CNT_REC_NODES], (unsigned long long)tc.nodes);
+        atomicAdd(&B.counters[CNT_REC_TRIS], (unsigned long long)tc.tris);
+        atomicAdd(&B.counters[CNT_REC_RAYS], (unsigned long long)tc.rays);
     }
 }
 
 __global__ void k_recip_offsets(KParams P, Pool B, int slots) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         B.work[0] = 0;
+        B.work[2 + slots] = 0;       // chains handed to phase 2
+        B.work[3 + slots] = 0;       // phase-2 work counter
         int acc = 0;
         for (int s = 0; s < slots; ++s) {
             B.work[1 + s] = acc;
@@ -526,16 +599,17 @@ __global__ void k_recip_finish(KParams P, Pool B) {
     int slot = blockIdx.y;
     if (k >= B.nent[slot]) return;
     size_t o = ((size_t)slot * B.ML + k) * P.repeats;
-    float acc = 0.0f, nn = 0.0f;
+    double acc = 0.0;
+    float nn = 0.0f;
     int tr = 0;
     uint32_t h = 2166136261u;
     for (int r = 0; r < P.repeats; ++r) {
-        acc += B.rep[o + r];
+        acc += (double)B.rep[o + r];
         nn += B.repn[o + r];
         tr |= B.reptr[o + r];
         h = (h ^ (uint32_t)B.repn[o + r]) * 16777619u;
     }
-    B.rhat[(size_t)slot * B.ML + k] = acc / (float)P.repeats;
+    B.rhat[(size_t)slot * B.ML + k] = (float)(acc / (double)P.repeats);
     B.esig[(size_t)slot * B.ML + k] = h;
     atomicAdd(&B.counters[CNT_ENTRIES], 1ull);
     atomicAdd(&B.counters[CNT_TRUNC], (unsigned long long)tr);
@@ -562,7 +636,13 @@ void launch_pool_build(const DScene &S, const DTables &T, const KParams &P, cons
 void launch_recip(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                   int num_sms, cudaStream_t st) {
     k_recip_offsets<<<1, 32, 0, st>>>(P, B, slots);
-    k_recip<<<num_sms * 8, 128, 0, st>>>(S, T, P, B, slots, iter_base);
+    if (P.count) {
+        k_recip<true><<<num_sms * 8, 128, 0, st>>>(S, T, P, B, slots, iter_base);
+        k_recip_long<true><<<num_sms * 4, PH2_THREADS, 0, st>>>(S, T, P, B, slots, iter_base);
+    } else {
+        k_recip<false><<<num_sms * 8, 128, 0, st>>>(S, T, P, B, slots, iter_base);
+        k_recip_long<false><<<num_sms * 4, PH2_THREADS, 0, st>>>(S, T, P, B, slots, iter_base);
+    }
     dim3 g2((B.ML + 127) / 128, slots);
     k_recip_finish<<<g2, 128, 0, st>>>(P, B);
 }

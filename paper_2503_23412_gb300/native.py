@@ -38,24 +38,41 @@ class pb_tables_desc(C.Structure):
 class pb_config(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("spp", C.c_int), ("max_depth", C.c_int), ("M", C.c_int),
                 ("M_p", C.c_int), ("repeats", C.c_int), ("proxy", C.c_int), ("conn", C.c_int),
-                ("trial_cap", C.c_int), ("iter0", C.c_int), ("batch", C.c_int)]
+                ("trial_cap", C.c_int), ("iter0", C.c_int), ("batch", C.c_int), ("count_traversal", C.c_int),
+                ("chain_handoff", C.c_int)]
 
 
 class pb_stats(C.Structure):
     _fields_ = [("ms", C.c_double), ("mpaths_per_s", C.c_double), ("n_entries", C.c_int64),
                 ("n_truncated", C.c_int64), ("n_nodes", C.c_int64), ("n_conn", C.c_int64),
-                ("n_proxy", C.c_int64), ("n_proxy_ok", C.c_int64), ("n_node_fetch", C.c_int64),
-                ("n_tri_test", C.c_int64)]
+                ("n_proxy", C.c_int64), ("n_proxy_ok", C.c_int64), ("ms_light", C.c_double),
+                ("ms_pool", C.c_double), ("ms_recip", C.c_double), ("ms_eye", C.c_double),
+                ("n_launches", C.c_int64), ("n_waves", C.c_int64), ("eye_nodes", C.c_int64),
+                ("eye_tris", C.c_int64), ("eye_rays", C.c_int64), ("rec_nodes", C.c_int64),
+                ("rec_tris", C.c_int64), ("rec_rays", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pb_learn_desc(C.Structure):
+    _fields_ = [("KT", C.c_int), ("KS", C.c_int), ("KSp", C.c_int), ("KC", C.c_int), ("tile", C.c_int),
+                ("n_iter", C.c_int), ("iter0", C.c_uint32), ("n_bsamples", C.c_int), ("lloyd_iters", C.c_int),
+                ("keep_centroids", C.c_int)]
+
+
+class pb_tables_host(C.Structure):
+    _fields_ = [("KT", C.c_int), ("KS", C.c_int), ("KSp", C.c_int), ("KC", C.c_int), ("tile", C.c_int),
+                ("grid_w", C.c_int), ("grid_h", C.c_int)] + [
+        (n, C.c_void_p) for n in ("bbox_lo", "bbox_hi", "cent_T", "cent_S", "cent_Sp", "cent_C", "gamma_conn",
+                                  "gamma_proxy", "B_tab", "mis_tab", "pi_grid")]
 
 
 _lib = None
 
 EXPORTS = ["pb_create", "pb_destroy", "pb_last_error", "pb_scene_upload", "pb_tables_upload", "pb_render",
            "pb_film_clear", "pb_film_readback", "pb_film_device", "pb_trace", "pb_occluded", "pb_light_pass",
-           "pb_iteration"]
+           "pb_iteration", "pb_prepare", "pb_tables_readback"]
 
 
 def lib(path=LIB):
@@ -82,6 +99,8 @@ def lib(path=LIB):
     L.pb_light_pass.argtypes = [vp, C.POINTER(pb_config), i32, vp, vp]
     L.pb_iteration.argtypes = [vp, C.POINTER(pb_config), i32, vp, vp, vp, vp, vp, i32, C.POINTER(i32), vp, vp, vp,
                                C.POINTER(pb_stats)]
+    L.pb_prepare.argtypes = [vp, C.POINTER(pb_config), C.POINTER(pb_learn_desc), C.POINTER(pb_stats)]
+    L.pb_tables_readback.argtypes = [vp, C.POINTER(pb_tables_host)]
     for n in EXPORTS:
         if n not in ("pb_destroy", "pb_last_error"):
             getattr(L, n).restype = i32
@@ -100,8 +119,9 @@ class PBError(RuntimeError):
 
 
 def config(seed=7, spp=1, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, conn=1, trial_cap=1 << 16, iter0=0,
-           batch=0):
-    return pb_config(seed, spp, max_depth, M, M_p, repeats, proxy, conn, trial_cap, iter0, batch)
+           batch=0, count_traversal=0, chain_handoff=0):
+    return pb_config(seed, spp, max_depth, M, M_p, repeats, proxy, conn, trial_cap, iter0, batch, count_traversal,
+                     chain_handoff)
 
 
 def tables_desc(t, W, H):
@@ -149,6 +169,29 @@ class Renderer:
         d = tables_desc(t, self.W, self.H)
         self._check(self.L.pb_tables_upload(self.h, C.byref(d)))
         self.tables = t
+
+    def prepare(self, cfg, n_iter=8, iter0=1 << 20, n_bsamples=32, lloyd_iters=8, keep_centroids=False,
+                KT=300, KS=300, KSp=100, KC=10, tile=10):
+        """Learns the subspace tables on the device (see pb_prepare)."""
+        d = pb_learn_desc(KT, KS, KSp, KC, tile, n_iter, iter0, n_bsamples, lloyd_iters, 1 if keep_centroids else 0)
+        st = pb_stats()
+        self._check(self.L.pb_prepare(self.h, C.byref(cfg), C.byref(d), C.byref(st)))
+        return st.as_dict()
+
+    def tables_readback(self):
+        t = pb_tables_host()
+        self._check(self.L.pb_tables_readback(self.h, C.byref(t)))
+        out = dict(bbox_lo=np.zeros(3, np.float32), bbox_hi=np.zeros(3, np.float32),
+                   cent_T=np.zeros((t.KT, 9), np.float32), cent_S=np.zeros((t.KS, 9), np.float32),
+                   cent_Sp=np.zeros((t.KSp, 6), np.float32), cent_C=np.zeros((t.KC, 3), np.float32),
+                   gamma_conn=np.zeros((t.KT, t.KS), np.float32), gamma_proxy=np.zeros((t.KT, t.KSp), np.float32),
+                   B_tab=np.zeros((4, t.KSp, t.KC + 1), np.float32), mis_tab=np.zeros((4, t.KSp, t.KC + 1), np.float32),
+                   pi_grid=np.zeros((t.grid_h, t.grid_w), np.float32))
+        for k, v in out.items():
+            setattr(t, k, v.ctypes.data)
+        self._check(self.L.pb_tables_readback(self.h, C.byref(t)))
+        out["tile"] = np.int32(t.tile)
+        return out
 
     def render(self, cfg, allow_truncated=False):
         st = pb_stats()

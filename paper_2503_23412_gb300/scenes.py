@@ -213,7 +213,7 @@ def spherical_cap_lens(radius_aperture, R, z_center, rings, segs, center_xy):
     return verts, tris
 
 
-def projector(W=256, H=256, lens_tris_per_cap=10000, lens_rough=0.1, seed=2):
+def projector(W=256, H=256, lens_tris_per_cap=10000, lens_rough=0.1, seed=2, flat=False):
     """Projector-like caustic scene.
 
     A 0.1 x 0.1 emitter textured with seeded 256x256 RGB noise (scale 50)
@@ -264,6 +264,8 @@ def projector(W=256, H=256, lens_tris_per_cap=10000, lens_rough=0.1, seed=2):
     lv, lt = spherical_cap_lens(0.2, 0.4, 3.0, rings, segs, (0.0, 1.2))
     b.add_mesh(lv, lt, glass)
     tex = rng.uniform(0.0, 1.0, size=(256, 256, 3))
+    if flat:   # same scene with a constant texture (isolates geometry from texture gradients)
+        tex = np.full((256, 256, 3), 0.5)
     cam = [1.3, 1.5, 0.2, 0.0, 1.2, 5.0, 0, 1, 0, 45.0, W, H]
     return b.build(tex, cam)
 

@@ -1,0 +1,67 @@
+"""Table learning on the device (pb_prepare) against the oracle's learning.
+
+With the centroids held fixed, both sides draw the same streams: B is a
+maximum of identical f/q draws, the MIS scale a ratio of moments of the same
+reciprocal estimates, Gamma and the tile grid accumulate the same
+contributions; they must agree up to FP32 rounding of sums. Learned
+centroids (k-means) are checked by the properties every Lloyd step keeps.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_23412_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2503_23412_gb300 import build
+    build.build()
+    from paper_2503_23412_gb300 import native
+    native.lib()
+    return native
+
+
+@pytest.mark.parametrize("make", [lambda: scenes.caustic_mini(16, 12), lambda: scenes.cornell(20, 16)])
+def test_learned_statistics_match_oracle(N, make):
+    sc = make()
+    o = O.Oracle(sc)
+    tab = scenes.random_tables(sc, KT=12, KS=12, KSp=6, KC=2, seed=8)
+    p = O.params(M=400, M_p=400, max_depth=5)
+    ref = o.learn(p, tab, 5000, 2, n_bsamples=24)
+    r = N.Renderer(sc, tab)
+    r.prepare(N.config(M=400, M_p=400, max_depth=5), n_iter=2, iter0=5000, n_bsamples=24, keep_centroids=True)
+    got = r.tables_readback()
+    np.testing.assert_allclose(got["cent_T"], tab["cent_T"])
+    np.testing.assert_allclose(got["B_tab"], ref["B_tab"], rtol=2e-4)
+    np.testing.assert_allclose(got["mis_tab"], ref["mis_tab"], rtol=2e-3)
+    np.testing.assert_allclose(got["gamma_conn"], ref["gamma_conn"], rtol=2e-3, atol=1e-5)
+    np.testing.assert_allclose(got["gamma_proxy"], ref["gamma_proxy"], rtol=2e-3, atol=1e-5)
+    assert (got["pi_grid"] == ref["pi_grid"]).mean() >= 0.9
+    r.close()
+
+
+def test_learned_tables_are_valid_and_render(N):
+    sc = scenes.cornell(32, 32)
+    r = N.Renderer(sc)
+    cfg = N.config(M=2000, M_p=2000, max_depth=6, spp=4)
+    st = r.prepare(cfg, n_iter=3, iter0=7000, n_bsamples=16, lloyd_iters=6, KT=24, KS=24, KSp=12, KC=3)
+    t = r.tables_readback()
+    assert st["n_entries"] > 0
+    for k in ("cent_T", "cent_S"):
+        c = t[k]
+        assert np.all(c[:, :3] > -1e-5) and np.all(c[:, :3] < 1 + 1e-5)
+        assert np.all(np.linalg.norm(c[:, 3:6], axis=1) <= 1 + 1e-4)
+        assert np.all(np.linalg.norm(c[:, 6:9], axis=1) <= 1 + 1e-4)
+    assert len(np.unique(t["cent_T"].round(6), axis=0)) > 12
+    assert np.all(t["B_tab"] > 0) and np.all(t["mis_tab"] > 0)
+    np.testing.assert_allclose(t["gamma_conn"].sum(1), 1.0, rtol=1e-4)
+    np.testing.assert_allclose(t["gamma_proxy"].sum(1), 1.0, rtol=1e-4)
+    assert set(np.unique(t["pi_grid"])) <= {np.float32(0.2), np.float32(1.0)}
+    st = r.render(cfg, allow_truncated=True)
+    img = r.film()
+    assert np.isfinite(img).all() and img.mean() > 0
+    r.close()

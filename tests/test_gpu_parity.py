@@ -67,7 +67,7 @@ def test_closest_hit_and_occlusion_parity(N, name):
     og = r.occluded(a, b, -1, -1)
     oc = o.occluded(a.astype(np.float64), b.astype(np.float64), -1, -1)
     assert (og == oc).mean() >= TOPO
-    assert 0.05 < oc.mean() < 0.95
+    assert 0.005 < oc.mean() < 0.995   # the projector room is mostly empty space
     r.close()
 
 
@@ -93,10 +93,19 @@ def test_light_pass_parity(N):
 
 # --- one iteration: pool, reciprocal estimates, eye pass ---------------------------
 
+# share of topology-agreeing paths that must meet REL, and a bound on all.
+# The textured projector is the exception the tolerance model allows: a
+# ~1e-6 FP32 direction error after two alpha = 0.01 refractions moves the
+# emitter hit by ~1e-5 of the 0.1-wide emitter, which the 256x256 noise
+# texture's gradient (~0.5 per texel) turns into up to ~1e-3 in radiance.
+# The same scene with a flat texture isolates geometry and BSDFs.
 CASES = {
-    "cornell": dict(make=lambda: scenes.cornell(24, 20), M=800, M_p=400, max_depth=6),
-    "projector": dict(make=lambda: scenes.projector(24, 24, lens_tris_per_cap=1500), M=1500, M_p=1500, max_depth=8),
-    "caustic": dict(make=lambda: scenes.caustic_mini(16, 12), M=500, M_p=500, max_depth=5),
+    "cornell": dict(make=lambda: scenes.cornell(24, 20), M=800, M_p=400, max_depth=6, share=1.0, bound=REL),
+    "projector_flat": dict(make=lambda: scenes.projector(24, 24, lens_tris_per_cap=1500, flat=True), M=1500,
+                           M_p=1500, max_depth=8, share=0.999, bound=1e-3),
+    "projector": dict(make=lambda: scenes.projector(24, 24, lens_tris_per_cap=1500), M=1500, M_p=1500,
+                      max_depth=8, share=0.99, bound=2e-2),
+    "caustic": dict(make=lambda: scenes.caustic_mini(16, 12), M=500, M_p=500, max_depth=5, share=1.0, bound=REL),
 }
 
 
@@ -122,7 +131,7 @@ def test_iteration_parity(N, case):
         es = ref["entry_sig"] == got["entry_sig"]
         n_ent += len(es)
         n_ent_same += int(es.sum())
-        assert np.all(rel_close(ref["rhat"][es], got["rhat"][es], 1.0 / 1e3))
+        assert np.all(rel_close(ref["rhat"][es], got["rhat"][es], 1e-3))
         assert np.array_equal(ref["entry_nodes"][es], got["entry_nodes"][es])
         # eye pass on the oracle's estimates: isolates the per-path comparison
         got = r.iteration(cfg, it, tri, bary, rhat=ref["rhat"])
@@ -132,13 +141,41 @@ def test_iteration_parity(N, case):
         a, b = ref["rgb"][same], got["rgb"][same]
         floor = max(1e-3 * float(np.abs(ref["rgb"]).mean()), 1e-12)
         ok = rel_close(a, b, floor)
-        assert ok.mean() >= TOPO, (case, ok.mean())
+        assert ok.mean() >= cs["share"], (case, ok.mean())
+        err = np.abs(a - b) / np.maximum(np.abs(a), floor)
+        assert err.max() <= cs["bound"], (case, err.max())
         proxy_live += ref["stats"]["n_proxy_ok"]
     assert n_same / n_items >= TOPO - 0.004, n_same / n_items
     assert n_ent == 0 or n_ent_same / n_ent >= 0.98
     if case != "cornell":
         assert proxy_live > 0
     r.close()
+
+
+@pytest.mark.parametrize("handoff", [32, 96])
+def test_block_phase_of_the_estimator_matches_oracle(N, handoff):
+    """Chains handed from a warp to a block after `handoff` nodes (parallel
+    prefix walk and sequential walk) give the same estimates and node counts
+    as the oracle's recursion; B below max f/q forces negative g (signs)."""
+    sc = scenes.projector(16, 16, lens_tris_per_cap=1500)
+    o = O.Oracle(sc)
+    tab = learned(sc, o, M=1500, M_p=1500, max_depth=8)
+    for scale in (1.0, 0.6):
+        t2 = dict(tab)
+        t2["B_tab"] = (tab["B_tab"] * scale).astype(np.float32)
+        r = N.Renderer(sc, t2)
+        p = O.params(M=1500, M_p=1500, max_depth=8)
+        cfg = N.config(M=1500, M_p=1500, max_depth=8, chain_handoff=handoff)
+        tri, bary = o.light_pass(p, 9)
+        ref = o.iteration(p, o.tables(t2), 9, tri, bary, pix_lo=0, pix_hi=0)
+        got = r.iteration(cfg, 9, tri, bary)
+        assert len(ref["rhat"]) == len(got["rhat"]) > 20
+        es = ref["entry_sig"] == got["entry_sig"]
+        assert es.mean() >= 0.97
+        assert np.array_equal(ref["entry_nodes"][es], got["entry_nodes"][es])
+        assert ref["entry_nodes"].max() > 5 * handoff
+        assert np.all(rel_close(ref["rhat"][es], got["rhat"][es], 1e-3))
+        r.close()
 
 
 # --- edge cases ----------------------------------------------------------------------
