@@ -188,6 +188,36 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
                        float *host_entry_rhat, uint32_t *host_entry_sig, float *host_entry_nodes,
                        pb_stats *stats_or_null);
 
+/* ---- allocation-free reciprocal estimates ---------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory while they run -- an engine that
+ * reserves all of its device memory up front, a process whose allocations
+ * are capped or pooled by another runtime, or a latency-critical path where
+ * cudaMalloc/cudaFree's implicit synchronisation is not acceptable.
+ *
+ * It computes the averaged reciprocal estimate of n incomplete light
+ * sub-paths on the context's scene -- the same values pb_iteration computes
+ * for its pool when given the same entries in (light path, vertex) order,
+ * the same iteration, seed, repeats, trial_cap and B -- and allocates nothing:
+ * its scratch is a file-scope device array of PB_NOALLOC_MAX_ESTIMATES
+ * (entry, repeat) slots that every GPU loading the library keeps until exit.
+ * Calls with n * cfg->repeats above that maximum return PB_ERR_ARG.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture. All calls share the array and it
+ * keeps the last call's contents: calls whose work overlaps on the GPU (two
+ * contexts or streams at once) race on it. The call is synchronous.
+ *
+ * Device inputs (caller-owned): d_tri[2n] (y_{s-1} triangle, h_c triangle),
+ * d_bary[4n] (their barycentrics), d_info[n] (u | type << 3, type 1 = L D S^u),
+ * d_B[n] (bound B > 0 per entry). Device outputs: d_rhat[n], d_nodes[n] (total
+ * estimator nodes over the repeats, may be NULL). *n_truncated (may be NULL)
+ * counts entries with a repeat that hit trial_cap. Only cfg->seed, repeats
+ * and trial_cap are read from cfg. */
+#define PB_NOALLOC_MAX_ESTIMATES 16384
+pb_status pb_recip_estimates_noalloc(pb_ctx *ctx, const pb_config *cfg, int iteration, int n,
+                                     const int32_t *d_tri, const float *d_bary, const int32_t *d_info,
+                                     const float *d_B, float *d_rhat, float *d_nodes, int *n_truncated);
+
 #ifdef __cplusplus
 }
 #endif

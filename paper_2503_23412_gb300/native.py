@@ -72,7 +72,7 @@ _lib = None
 
 EXPORTS = ["pb_create", "pb_destroy", "pb_last_error", "pb_scene_upload", "pb_tables_upload", "pb_render",
            "pb_film_clear", "pb_film_readback", "pb_film_device", "pb_trace", "pb_occluded", "pb_light_pass",
-           "pb_iteration", "pb_prepare", "pb_tables_readback"]
+           "pb_iteration", "pb_prepare", "pb_tables_readback", "pb_recip_estimates_noalloc"]
 
 
 def lib(path=LIB):
@@ -101,6 +101,8 @@ def lib(path=LIB):
                                C.POINTER(pb_stats)]
     L.pb_prepare.argtypes = [vp, C.POINTER(pb_config), C.POINTER(pb_learn_desc), C.POINTER(pb_stats)]
     L.pb_tables_readback.argtypes = [vp, C.POINTER(pb_tables_host)]
+    L.pb_recip_estimates_noalloc.argtypes = [vp, C.POINTER(pb_config), i32, i32, vp, vp, vp, vp, vp, vp,
+                                             C.POINTER(i32)]
     for n in EXPORTS:
         if n not in ("pb_destroy", "pb_last_error"):
             getattr(L, n).restype = i32
@@ -255,6 +257,14 @@ class Renderer:
                                         _p(sig), cap, C.byref(ne), _p(er), _p(es), _p(en), C.byref(st)))
         k = min(ne.value, cap)
         return dict(rgb=rgb, sig=sig, rhat=er[:k], entry_sig=es[:k], entry_nodes=en[:k], stats=st.as_dict())
+
+    def recip_estimates_noalloc(self, cfg, iteration, n, d_tri, d_bary, d_info, d_B, d_rhat, d_nodes=None):
+        """Allocation-free reciprocal estimates on caller device buffers (raw
+        device addresses); returns the number of truncated entries."""
+        ntr = C.c_int(0)
+        self._check(self.L.pb_recip_estimates_noalloc(self.h, C.byref(cfg), iteration, n, d_tri, d_bary, d_info, d_B,
+                                                      d_rhat, d_nodes, C.byref(ntr)))
+        return ntr.value
 
     def close(self):
         if self.h:
