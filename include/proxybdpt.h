@@ -130,8 +130,8 @@ pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *tables);
  *  - k-means centroids of the eye, light, specular and control subspaces
  *    (lloyd_iters Lloyd steps from evenly spaced samples), unless
  *    keep_centroids = 1 keeps those of the uploaded tables;
- *  - B(u,S',C) = 1.5 x the largest f/q of n_bsamples draws per incomplete
- *    sub-path (App. "Optimal value for B": B = max f/q);
+ *  - B(u,S',C) = b_safety (0: 1.0) x the largest f/q of n_bsamples draws per
+ *    incomplete sub-path (App. "Optimal value for B": B = max f/q);
  *  - the MIS scale mean(R)/mean(R^2) per cell (Sec. 5.4, Eq. MIS_1);
  *  - Gamma rows proportional to the accumulated unweighted contribution
  *    (0.9 x normalised + 0.1 uniform) and the 10x10-tile proxy probability
@@ -145,6 +145,7 @@ typedef struct {
     int n_bsamples;
     int lloyd_iters;
     int keep_centroids;
+    float b_safety;
 } pb_learn_desc;
 pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_learn_desc *learn, pb_stats *stats_or_null);
 

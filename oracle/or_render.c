@@ -36,10 +36,10 @@ double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, uint32_t
                      int *trunc, uint32_t *sig);
 
 #define MAXV 40
-/* B is the largest f/q observed during learning times this factor: the
- * observed maximum under-estimates the true one, and B below max f/q turns
- * the estimator's chains into splitting trees (still unbiased, costlier). */
-#define B_SAFETY 1.5
+/* B is the largest f/q observed during learning (App. "Optimal value for B":
+ * B = max f/q) times this factor. Where the observed maximum falls short of
+ * the true one the estimator splits (still unbiased). */
+#define B_SAFETY 1.0
 
 typedef struct { or_vtx v[MAXV]; int n; } or_path;
 

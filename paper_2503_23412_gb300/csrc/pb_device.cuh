@@ -203,7 +203,13 @@ __device__ __forceinline__ float fresnel_dielectric(float cos_i, float eta_i, fl
     return 0.5f * (rs * rs + rp * rp);
 }
 
-__device__ __forceinline__ float3 bsdf_eval(const DMat &m, float3 n, float3 wl, float3 we) {
+#ifdef PB_BSDF_NOINLINE
+#define PB_BSDF_FN static __noinline__
+#else
+#define PB_BSDF_FN __forceinline__
+#endif
+
+__device__ PB_BSDF_FN float3 bsdf_eval(const DMat &m, float3 n, float3 wl, float3 we) {
     float cl = dot(n, wl), ce = dot(n, we);
     if (m.kind == MK_LAMBERT) {
         if (cl * ce <= 0.0f) return f3(0, 0, 0);
@@ -246,7 +252,7 @@ __device__ __forceinline__ float3 bsdf_eval(const DMat &m, float3 n, float3 wl, 
     return f3(f, f, f);
 }
 
-__device__ __forceinline__ float bsdf_pdf(const DMat &m, float3 n, float3 wg, float3 ws) {
+__device__ PB_BSDF_FN float bsdf_pdf(const DMat &m, float3 n, float3 wg, float3 ws) {
     float cg = dot(n, wg), cs = dot(n, ws);
     if (m.kind == MK_LAMBERT) {
         if (cg * cs <= 0.0f) return 0.0f;
@@ -282,8 +288,8 @@ __device__ __forceinline__ float bsdf_pdf(const DMat &m, float3 n, float3 wg, fl
     return (1.0f - F) * ggx_D(a2, n, h) * dot(n, h) * eta_s * eta_s * fabsf(sh) / (den * den);
 }
 
-__device__ __forceinline__ bool bsdf_sample(const DMat &m, float3 n, float3 wg, float u0, float u1, float u2,
-                                            float3 &ws) {
+__device__ PB_BSDF_FN bool bsdf_sample(const DMat &m, float3 n, float3 wg, float u0, float u1, float u2,
+                                       float3 &ws) {
     float cg = dot(n, wg);
     if (m.kind == MK_LAMBERT) {
         if (cg == 0.0f) return false;
@@ -392,7 +398,8 @@ struct TravCount {
     uint32_t nodes, tris, rays;
 };
 
-__device__ __forceinline__ void tri_test(const DScene &S, int slot, float3 o, float3 d, int skip, Hit &h) {
+template <class SV>
+__device__ __forceinline__ void tri_test(const SV &S, int slot, float3 o, float3 d, int skip, Hit &h) {
     const float4 *T = S.itri + 3 * (size_t)slot;
     float4 v0 = __ldg(T), e1 = __ldg(T + 1), e2 = __ldg(T + 2);
     int id = __float_as_int(v0.w);
@@ -418,7 +425,8 @@ __device__ __forceinline__ void tri_test(const DScene &S, int slot, float3 o, fl
     }
 }
 
-__device__ __forceinline__ bool seg_test(const DScene &S, int slot, float3 o, float3 d, int s1, int s2) {
+template <class SV>
+__device__ __forceinline__ bool seg_test(const SV &S, int slot, float3 o, float3 d, int s1, int s2) {
     const float4 *T = S.itri + 3 * (size_t)slot;
     float4 v0 = __ldg(T), e1 = __ldg(T + 1), e2 = __ldg(T + 2);
     int id = __float_as_int(v0.w);
@@ -439,7 +447,8 @@ __device__ __forceinline__ bool seg_test(const DScene &S, int slot, float3 o, fl
 }
 
 // slab test of two child boxes of a node; returns entry distances
-__device__ __forceinline__ void child_boxes(const DScene &S, int node, float3 o, float3 inv, float tmax,
+template <class SV>
+__device__ __forceinline__ void child_boxes(const SV &S, int node, float3 o, float3 inv, float tmax,
                                             bool &hitL, bool &hitR, float &tl, float &tr, int &cl, int &cr) {
     const float4 *N = S.nodes + 4 * (size_t)node;
     float4 a = __ldg(N), b = __ldg(N + 1), c = __ldg(N + 2), d = __ldg(N + 3);
@@ -468,12 +477,48 @@ __device__ __forceinline__ float3 safe_inv(float3 d) {
     return f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
 }
 
+// The traversal cores take a compact by-value view of the scene and are
+// shared out-of-line functions: kernels with many ray queries stay small
+// enough for the instruction cache (measured 1.4-1.9x faster than inlining
+// every query). Define PB_TRAV_INLINE to inline them instead.
+struct TravView {
+    const float4 *nodes;
+    const int *parent, *sibling;
+    const float4 *itri;
+    float eps_t;
+};
+#ifdef PB_TRAV_INLINE
+#define PB_TRAV_FN __forceinline__
+#else
+#define PB_TRAV_FN __noinline__
+#endif
+
+__device__ __forceinline__ TravView trav_view(const DScene &S) {
+    TravView v;
+    v.nodes = S.nodes;
+    v.parent = S.parent;
+    v.sibling = S.sibling;
+    v.itri = S.itri;
+    v.eps_t = S.eps_t;
+    return v;
+}
+
+template <bool COUNT>
+__device__ PB_TRAV_FN Hit trav_closest(TravView S, float3 o, float3 d, int skip, Hit h, TravCount *cnt);
+template <bool COUNT>
+__device__ PB_TRAV_FN bool trav_occluded(TravView S, float3 a, float3 b, int s1, int s2, TravCount *cnt);
+
 // closest hit starting from a known candidate `h` (h.tri = -1, h.t = inf for
 // a plain query): only triangles with a smaller t (or the same t and a lower
 // index) replace it, so the result equals the unrestricted closest hit
 template <bool COUNT>
 __device__ __forceinline__ Hit closest_hit_from(const DScene &S, float3 o, float3 d, int skip, Hit h,
                                                 TravCount *cnt = nullptr) {
+    return trav_closest<COUNT>(trav_view(S), o, d, skip, h, cnt);
+}
+
+template <bool COUNT>
+__device__ PB_TRAV_FN Hit trav_closest(TravView S, float3 o, float3 d, int skip, Hit h, TravCount *cnt) {
     if (COUNT) cnt->rays++;
     float3 inv = safe_inv(d);
     int node = 0;
@@ -578,6 +623,11 @@ __device__ __forceinline__ Hit closest_emitter_hit(const DScene &S, float3 o, fl
 // any hit strictly inside the open segment a -> b (parameter in (1e-4, 1-1e-4))
 template <bool COUNT = false>
 __device__ __forceinline__ bool occluded(const DScene &S, float3 a, float3 b, int s1, int s2, TravCount *cnt = nullptr) {
+    return trav_occluded<COUNT>(trav_view(S), a, b, s1, s2, cnt);
+}
+
+template <bool COUNT>
+__device__ PB_TRAV_FN bool trav_occluded(TravView S, float3 a, float3 b, int s1, int s2, TravCount *cnt) {
     float3 d = b - a;
     float3 inv = safe_inv(d);
     if (COUNT) cnt->rays++;

@@ -8,7 +8,7 @@
 //              valid points in slot order) over: eye vertices of a pretrace
 //              (T, 9-d), connectable light vertices (S, 9-d), ends y_{s-1} of
 //              incomplete sub-paths (S', 6-d) and their control vertices (C, 3-d)
-//   B          B_SAFETY x the largest f/q drawn from the supporting
+//   B          b_safety (default 1) x the largest f/q drawn from the supporting
 //              distribution per (u, S', C) cell (App. "Optimal value for B")
 //   mis        mean(R) / mean(R^2) per cell = 1 / (E[R^2] Pbar), Pbar = 1/E[R]
 //   Gamma      0.9 x normalised unweighted contribution per (T, S) + 0.1 uniform
@@ -23,7 +23,7 @@
 
 namespace {
 
-constexpr float B_SAFETY = 1.5f;
+constexpr float B_SAFETY_DEFAULT = 1.0f;
 enum : uint32_t { K_PRETRACE = 5 };
 
 __device__ __forceinline__ void put9(float *o, const DScene &S, float3 p, float3 n, float3 w) {
@@ -262,6 +262,7 @@ extern "C" pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_lear
     if (ld->keep_centroids && !ctx->has_tables) return pb_fail(ctx, PB_ERR_STATE, "keep_centroids needs uploaded tables");
     CK(cudaSetDevice(ctx->device));
     int W = ctx->S.W, H = ctx->S.H;
+    const float b_safety = ld->b_safety > 0.0f ? ld->b_safety : B_SAFETY_DEFAULT;
     // ---- the tables being learned: sizes, bbox, initial contents
     int KT, KS, KSp, KC, tile;
     std::vector<float> cT, cS, cSp, cC, lo(3), hi(3);
@@ -361,7 +362,7 @@ extern "C" pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_lear
     for (int c = 0; c < ncell; ++c) {
         float v;
         memcpy(&v, &cm[c], 4);
-        Bt[c] = B_SAFETY * (v > 0.0f ? v : gmax);
+        Bt[c] = b_safety * (v > 0.0f ? v : gmax);
     }
     s = upload_tables();
     if (s != PB_OK) return s;

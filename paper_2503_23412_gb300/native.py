@@ -58,7 +58,7 @@ class pb_stats(C.Structure):
 class pb_learn_desc(C.Structure):
     _fields_ = [("KT", C.c_int), ("KS", C.c_int), ("KSp", C.c_int), ("KC", C.c_int), ("tile", C.c_int),
                 ("n_iter", C.c_int), ("iter0", C.c_uint32), ("n_bsamples", C.c_int), ("lloyd_iters", C.c_int),
-                ("keep_centroids", C.c_int)]
+                ("keep_centroids", C.c_int), ("b_safety", C.c_float)]
 
 
 class pb_tables_host(C.Structure):
@@ -173,9 +173,10 @@ class Renderer:
         self.tables = t
 
     def prepare(self, cfg, n_iter=8, iter0=1 << 20, n_bsamples=32, lloyd_iters=8, keep_centroids=False,
-                KT=300, KS=300, KSp=100, KC=10, tile=10):
+                KT=300, KS=300, KSp=100, KC=10, tile=10, b_safety=0.0):
         """Learns the subspace tables on the device (see pb_prepare)."""
-        d = pb_learn_desc(KT, KS, KSp, KC, tile, n_iter, iter0, n_bsamples, lloyd_iters, 1 if keep_centroids else 0)
+        d = pb_learn_desc(KT, KS, KSp, KC, tile, n_iter, iter0, n_bsamples, lloyd_iters, 1 if keep_centroids else 0,
+                          b_safety)
         st = pb_stats()
         self._check(self.L.pb_prepare(self.h, C.byref(cfg), C.byref(d), C.byref(st)))
         return st.as_dict()
