@@ -101,6 +101,15 @@ typedef struct {
     int batch;         /* iterations in flight per launch wave (0: automatic) */
     int count_traversal; /* 1: count BVH node fetches / triangle tests / rays (slower) */
     int chain_handoff;   /* estimator nodes a warp walks before a block takes the chain over (0: 512) */
+    /* Per-entry bound B of the reciprocal estimator (App. "Optimal value for
+     * B": B = max f/q of the integrand being estimated): the largest f/q of
+     * draws from the entry's supporting distribution on its own stream, in
+     * rounds of 32 -- at least pilot_min draws (0: 64), then until one has
+     * f > 0, at most pilot_max (0: 1024; negative: no pilot). An entry whose
+     * draws all had f = 0, or every entry with the pilot off, uses the learned
+     * table value. */
+    int pilot_min;
+    int pilot_max;
 } pb_config;
 
 typedef struct {

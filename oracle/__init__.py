@@ -52,7 +52,8 @@ class TablesDesc(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("max_depth", C.c_int), ("M", C.c_int), ("M_p", C.c_int),
-                ("repeats", C.c_int), ("proxy", C.c_int), ("trial_cap", C.c_int), ("conn", C.c_int)]
+                ("repeats", C.c_int), ("proxy", C.c_int), ("trial_cap", C.c_int), ("conn", C.c_int),
+                ("pilot_min", C.c_int), ("pilot_max", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -93,6 +94,8 @@ def lib():
         L.or_recip_1d.restype = C.c_int
         L.or_recip_1d.argtypes = [C.c_int, C.c_double, C.c_int, C.c_uint32, C.c_int, vp, vp, vp]
         L.or_entry_fq.argtypes = [vp, C.POINTER(Entry), C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, vp, vp]
+        L.or_entry_pilot.restype = C.c_double
+        L.or_entry_pilot.argtypes = [vp, C.POINTER(Entry), C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_int]
         L.or_entry_recip.restype = C.c_int
         L.or_entry_recip.argtypes = [vp, C.POINTER(Entry), C.c_double, C.c_int, C.c_uint32, C.c_int, vp, vp, vp]
         L.or_light_pass.argtypes = [vp, C.POINTER(Params), C.c_int, vp, vp]
@@ -227,6 +230,9 @@ class Oracle:
         self.L.or_entry_fq(self.h, C.byref(entry), n, seed, a, b, _p(f), _p(q))
         return f, q
 
+    def entry_pilot(self, entry, seed=1, a=0, b=0, min_draws=64, max_draws=1024):
+        return self.L.or_entry_pilot(self.h, C.byref(entry), seed, a, b, min_draws, max_draws)
+
     def entry_recip(self, entry, B, n, seed=1, cap=1 << 16):
         t = np.zeros(n, np.float64)
         i = np.zeros(n, np.float64)
@@ -235,8 +241,10 @@ class Oracle:
         return t, i, nn, tr
 
 
-def params(seed=7, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, trial_cap=1 << 16, conn=1):
-    return Params(seed, max_depth, M, M_p, repeats, proxy, trial_cap, conn)
+def params(seed=7, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, trial_cap=1 << 16, conn=1, pilot_min=64,
+           pilot_max=1024):
+    """pilot_max = 0 turns the per-entry pilot off (B from the learned table)."""
+    return Params(seed, max_depth, M, M_p, repeats, proxy, trial_cap, conn, pilot_min, pilot_max)
 
 
 def philox(ctr, key):

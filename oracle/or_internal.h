@@ -45,7 +45,7 @@ void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
  * (seed, kind), counter = (a, b, c, d >> 2), word d & 3. */
 double or_rnd(uint32_t seed, uint32_t kind, uint32_t a, uint32_t b, uint32_t c, uint32_t d);
 
-enum { K_CAMERA = 1, K_LIGHT = 2, K_RECIP = 3, K_TRAIN = 4 };
+enum { K_CAMERA = 1, K_LIGHT = 2, K_RECIP = 3, K_TRAIN = 4, K_PILOT = 6 };
 
 /* ---- scene --------------------------------------------------------------- */
 enum { MK_LAMBERT = 0, MK_CONDUCTOR = 1, MK_DIELECTRIC = 2 };

@@ -338,6 +338,39 @@ double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, uint32_t
     return acc / repeats;
 }
 
+/* B for one entry (App. "Optimal value for B": B = max f/q of the integrand
+ * being estimated). f/q is drawn from the entry's own supporting
+ * distribution on stream (kind PILOT, a = iteration, b = entry, c = draw),
+ * which no estimate uses, in rounds of 32 draws: at least min_draws, then
+ * further rounds until some draw has f > 0, at most max_draws. Returns the
+ * largest f/q seen, or 0 when every draw had f = 0. Because B is fixed
+ * before, and independently of, the draws of the estimate, Alg. I~ stays
+ * unbiased whatever value the pilot returns. */
+double or_pilot_B(const or_scene_t *s, const or_entry *en, uint32_t seed, uint32_t iteration, uint32_t entry,
+                  int min_draws, int max_draws) {
+    entry_ctx e;
+    entry_setup(&e, s, en);
+    e.seed = seed;
+    e.kind = K_PILOT;
+    e.a = iteration;
+    e.b = entry;
+    int lo = ((min_draws + 31) / 32) * 32, hi = ((max_draws + 31) / 32) * 32;
+    if (lo < 32) lo = 32;
+    if (hi < lo) hi = lo;
+    double best = 0.0;
+    for (int i = 0; i < hi; ++i) {
+        if (i % 32 == 0 && i >= lo && best > 0.0) break;
+        double r = entry_ratio(&e, (uint32_t)i);
+        if (r > best) best = r;
+    }
+    return best;
+}
+
+double or_entry_pilot(void *hs, const or_entry *en, uint32_t seed, uint32_t a, uint32_t b, int min_draws,
+                      int max_draws) {
+    return or_pilot_B((const or_scene_t *)hs, en, seed, a, b, min_draws, max_draws);
+}
+
 void or_entry_fq(void *hs, const or_entry *en, int n, uint32_t seed, uint32_t a, uint32_t b,
                  double *f_out, double *q_out) {
     entry_ctx e;

@@ -34,6 +34,8 @@ double or_fwd_density(const or_scene_t *s, const or_vtx *ys, int j);
 double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, uint32_t seed,
                      uint32_t iteration, uint32_t entry, int repeats, int cap, double *nodes,
                      int *trunc, uint32_t *sig);
+double or_pilot_B(const or_scene_t *s, const or_entry *en, uint32_t seed, uint32_t iteration, uint32_t entry,
+                  int min_draws, int max_draws);
 
 #define MAXV 40
 /* B is the largest f/q observed during learning (App. "Optimal value for B":
@@ -278,7 +280,13 @@ static void build_iter(const or_scene_t *s, const or_params *p, const or_tab *T,
             it->rhat[k] = rhat_override[k];
             continue;
         }
+        /* B: the entry's pilot maximum of f/q; the learned cell value when
+         * the pilot is off or saw only f = 0 */
         double B = T->Bt[table_cell(T, it->ent[k].u, it->ent_Sp[k], it->ent_C[k])];
+        if (p->pilot_max > 0) {
+            double Bp = or_pilot_B(s, &it->ent[k], p->seed, iteration, (uint32_t)k, p->pilot_min, p->pilot_max);
+            if (Bp > 0.0) B = Bp;
+        }
         double nodes;
         int trunc;
         uint32_t sg;

@@ -59,6 +59,8 @@ typedef struct {
     int proxy;         /* proxy strategy on/off */
     int trial_cap;     /* maximum estimator nodes per repeat */
     int conn;          /* subspace connection strategy on/off */
+    int pilot_min;     /* pilot draws per entry for its B, at least (rounded up to 32) */
+    int pilot_max;     /* at most; 0 = no pilot (B from the table) */
 } or_params;
 
 typedef struct {
@@ -105,6 +107,11 @@ typedef struct {
  * entry e (Sec. 5.3), using stream (kind TRAIN, a, b, c=sample). */
 void or_entry_fq(void *h, const or_entry *e, int n, uint32_t seed, uint32_t a, uint32_t b,
                  double *f_out, double *q_out);
+/* Pilot B of entry e: the largest f/q of draws on stream (kind PILOT, a, b,
+ * c = draw), at least min_draws and until one is non-zero, at most
+ * max_draws (both rounded up to 32); 0 if every draw had f = 0. */
+double or_entry_pilot(void *h, const or_entry *e, uint32_t seed, uint32_t a, uint32_t b, int min_draws,
+                      int max_draws);
 /* n independent reciprocal estimates (Alg. I~ and I) for entry e with bound B. */
 int or_entry_recip(void *h, const or_entry *e, double B, int n, uint32_t seed, int trial_cap,
                    double *out_t, double *out_i, double *out_n);

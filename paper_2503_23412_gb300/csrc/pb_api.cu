@@ -95,8 +95,9 @@ pb_status ensure_pool(pb_ctx *ctx, int slots, int ML, int repeats, int npix) {
     CK(dalloc(o, &B.repn, n * repeats));
     CK(dalloc(o, &B.reptr, n * repeats));
     CK(dalloc(o, &B.rhat, n));
+    CK(dalloc(o, &B.eB, n));
     CK(dalloc(o, &B.esig, n));
-    CK(dalloc(o, &B.work, (size_t)slots + 4));
+    CK(dalloc(o, &B.work, (size_t)slots + 5));
     B.chain_cap = (int)std::min<size_t>(n * repeats, (size_t)1 << 18);
     CK(dalloc(o, &B.chains, (size_t)B.chain_cap));
     CK(dalloc(o, &B.scratch, 2 * n));
@@ -139,6 +140,15 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
     P.npix = ctx->S.W * ctx->S.H;
     P.count = c->count_traversal ? 1 : 0;
     P.handoff = c->chain_handoff > 0 ? ((c->chain_handoff + 31) / 32) * 32 : 512;
+    if (c->pilot_max < 0) {
+        P.pilot_min = P.pilot_max = 0;
+    } else {
+        int lo = c->pilot_min > 0 ? c->pilot_min : 64, hi = c->pilot_max > 0 ? c->pilot_max : 1024;
+        lo = std::max(32, ((lo + 31) / 32) * 32);
+        hi = std::max(lo, ((hi + 31) / 32) * 32);
+        P.pilot_min = lo;
+        P.pilot_max = hi;
+    }
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     return P;
 }

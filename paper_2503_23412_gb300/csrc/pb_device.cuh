@@ -34,7 +34,7 @@ __device__ __forceinline__ float3 dirto(float3 a, float3 b) { return normalize(b
 
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon et al., SC'11): counter (a, b, c, d>>2), key (seed, kind).
-enum : uint32_t { K_CAMERA = 1, K_LIGHT = 2, K_RECIP = 3, K_TRAIN = 4 };
+enum : uint32_t { K_CAMERA = 1, K_LIGHT = 2, K_RECIP = 3, K_TRAIN = 4, K_PILOT = 6 };
 
 __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll

@@ -21,6 +21,7 @@ struct KParams {
     int npix;
     int count;      // 1: count traversal work (node fetches, triangle tests, rays)
     int handoff;    // estimator nodes walked by a warp before a block continues the chain
+    int pilot_min, pilot_max;   // per-entry B pilot draws (multiples of 32; pilot_max 0 = off)
     LearnAcc acc;
 };
 
@@ -57,6 +58,7 @@ struct Pool {
     float *rep, *repn;                             // per (entry, repeat): estimate, nodes
     int32_t *reptr;
     float *rhat;                                   // per entry: averaged reciprocal estimate
+    float *eB;                                     // per entry: bound B of its estimates
     uint32_t *esig;
     int32_t *work;                                 // work counters, per-slot work offsets
     struct ChainState *chains;                     // estimates continued by whole blocks

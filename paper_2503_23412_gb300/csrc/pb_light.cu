@@ -283,6 +283,50 @@ __device__ __forceinline__ Entry load_entry(const DScene &S, const KParams &P, c
     return E;
 }
 
+// Per-entry bound B (App. "Optimal value for B": B = max f/q of the
+// integrand being estimated). One warp per entry draws from the entry's
+// supporting distribution on stream (kind PILOT, a = iteration, b = entry,
+// c = draw), 32 draws per round: at least pilot_min, then rounds until one
+// has f > 0, at most pilot_max. B is the largest f/q seen, or the learned
+// cell value if every draw had f = 0 or the pilot is off. B depends on none
+// of the estimate's own draws, so the estimate stays unbiased.
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_recip_pilot(DScene S, DTables T, KParams P, Pool B, int slots,
+                                                     uint32_t iter_base) {
+    int lane = threadIdx.x & 31;
+    TravCount tc{0, 0, 0};
+    const int32_t *offs = B.work + 1;   // per slot: first (entry, repeat) item
+    int32_t *counter = B.work + 4 + slots;
+    int total = offs[slots] / P.repeats;
+    while (true) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        int slot = 0;
+        while (item * P.repeats >= offs[slot + 1]) ++slot;
+        int k = item - offs[slot] / P.repeats;
+        int Sp, C;
+        Entry E = load_entry(S, P, B, slot, k, Sp, C);
+        float best = 0.0f;
+        for (int base = 0; base < P.pilot_max; base += 32) {
+            if (base >= P.pilot_min && best > 0.0f) break;   // best is warp-uniform
+            Rng R;
+            R.init(P.seed, K_PILOT, iter_base + slot, (uint32_t)k, (uint32_t)(base + lane));
+            float x = entry_ratio<COUNT>(S, E, R, &tc);
+            for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+            best = fmaxf(best, x);
+        }
+        if (lane == 0)
+            B.eB[(size_t)slot * B.ML + k] = best > 0.0f ? best : T.Bt[((E.u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
+    }
+    if (COUNT) {
+        atomicAdd(&B.counters[CNT_REC_NODES], (unsigned long long)tc.nodes);
+        atomicAdd(&B.counters[CNT_REC_TRIS], (unsigned long long)tc.tris);
+        atomicAdd(&B.counters[CNT_REC_RAYS], (unsigned long long)tc.rays);
+    }
+}
+
 #define MAXF PB_MAXF
 #define MAXF1 8          // walk frames a warp keeps; deeper walks continue in a block
 
@@ -310,8 +354,7 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
         int k = local / P.repeats, rep = local % P.repeats;
         int Sp, C;
         Entry E = load_entry(S, P, B, slot, k, Sp, C);
-        float Bv = T.Bt[((E.u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
-        float invB = 1.0f / Bv;
+        float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
         double sum_t = 0.0;   // long chains add thousands of terms
         int nodes = 0;
         bool done = false, trunc = false, handed = false;
@@ -434,7 +477,7 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
         int slot = st.slot, k = st.k, rep = st.rep;
         int Sp, C;
         Entry E = load_entry(S, P, B, slot, k, Sp, C);
-        float invB = 1.0f / T.Bt[((E.u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
+        float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
         bool trunc = false;
         int done = 0;
         while (!done) {
@@ -585,6 +628,7 @@ __global__ void k_recip_offsets(KParams P, Pool B, int slots) {
         B.work[0] = 0;
         B.work[2 + slots] = 0;       // chains handed to phase 2
         B.work[3 + slots] = 0;       // phase-2 work counter
+        B.work[4 + slots] = 0;       // pilot work counter
         int acc = 0;
         for (int s = 0; s < slots; ++s) {
             B.work[1 + s] = acc;
@@ -637,9 +681,11 @@ void launch_recip(const DScene &S, const DTables &T, const KParams &P, const Poo
                   int num_sms, cudaStream_t st) {
     k_recip_offsets<<<1, 32, 0, st>>>(P, B, slots);
     if (P.count) {
+        k_recip_pilot<true><<<num_sms * 4, 128, 0, st>>>(S, T, P, B, slots, iter_base);
         k_recip<true><<<num_sms * 8, 128, 0, st>>>(S, T, P, B, slots, iter_base);
         k_recip_long<true><<<num_sms * 4, PH2_THREADS, 0, st>>>(S, T, P, B, slots, iter_base);
     } else {
+        k_recip_pilot<false><<<num_sms * 4, 128, 0, st>>>(S, T, P, B, slots, iter_base);
         k_recip<false><<<num_sms * 8, 128, 0, st>>>(S, T, P, B, slots, iter_base);
         k_recip_long<false><<<num_sms * 4, PH2_THREADS, 0, st>>>(S, T, P, B, slots, iter_base);
     }

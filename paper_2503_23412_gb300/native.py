@@ -39,7 +39,7 @@ class pb_config(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("spp", C.c_int), ("max_depth", C.c_int), ("M", C.c_int),
                 ("M_p", C.c_int), ("repeats", C.c_int), ("proxy", C.c_int), ("conn", C.c_int),
                 ("trial_cap", C.c_int), ("iter0", C.c_int), ("batch", C.c_int), ("count_traversal", C.c_int),
-                ("chain_handoff", C.c_int)]
+                ("chain_handoff", C.c_int), ("pilot_min", C.c_int), ("pilot_max", C.c_int)]
 
 
 class pb_stats(C.Structure):
@@ -121,9 +121,9 @@ class PBError(RuntimeError):
 
 
 def config(seed=7, spp=1, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, conn=1, trial_cap=1 << 16, iter0=0,
-           batch=0, count_traversal=0, chain_handoff=0):
+           batch=0, count_traversal=0, chain_handoff=0, pilot_min=0, pilot_max=0):
     return pb_config(seed, spp, max_depth, M, M_p, repeats, proxy, conn, trial_cap, iter0, batch, count_traversal,
-                     chain_handoff)
+                     chain_handoff, pilot_min, pilot_max)
 
 
 def tables_desc(t, W, H):

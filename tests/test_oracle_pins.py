@@ -275,16 +275,11 @@ def test_reciprocal_of_incomplete_pdf_square_light_closed_form():
     assert abs(i.mean() - 1 / P) < 4 * i.std() / math.sqrt(len(i))
 
 
-def test_reciprocal_of_incomplete_pdf_diffuse_control_vertex_quadrature():
-    """L D S, u = 1, h_c on the light: P = int over the floor of the light
-    tracer's densities (cosine emission, then cosine reflection) toward y_2,
-    evaluated here by a midpoint rule over the floor."""
-    sc = scenes.pin_floor_light(a=0.1, h=1.0, floor=1.0, ypos=(0.5, 0.3, 0.0))
-    o = O.Oracle(sc)
+def _floor_light_P(sc, m=600):
+    """P of the floor-light pin entry by a midpoint rule over the floor."""
     v = sc["verts"].astype(np.float64)[sc["tris"][0]]
     H = v[0] + 0.5 * (v[1] - v[0]) + 0.5 * (v[2] - v[0])   # h_c on the light, barycentrics (0.5, 0.5)
     Y = sc["verts"].astype(np.float64)[sc["tris"][4]].mean(0)
-    m = 600
     xs = (np.arange(m) + 0.5) / m * 2 - 1
     X, Z = np.meshgrid(xs, xs, indexing="ij")
     y1 = np.stack([X, np.zeros_like(X), Z], -1)
@@ -296,7 +291,16 @@ def test_reciprocal_of_incomplete_pdf_diffuse_control_vertex_quadrature():
     cos1Y = dY[..., 1] / lY
     cosY = dY[..., 1] / lY          # Y faces -y
     integrand = (cosH / np.pi) * cos1H / lH ** 2 * (cos1Y / np.pi) * cosY / lY ** 2
-    P = integrand.sum() * (2.0 / m) ** 2
+    return integrand.sum() * (2.0 / m) ** 2
+
+
+def test_reciprocal_of_incomplete_pdf_diffuse_control_vertex_quadrature():
+    """L D S, u = 1, h_c on the light: P = int over the floor of the light
+    tracer's densities (cosine emission, then cosine reflection) toward y_2,
+    evaluated here by a midpoint rule over the floor."""
+    sc = scenes.pin_floor_light(a=0.1, h=1.0, floor=1.0, ypos=(0.5, 0.3, 0.0))
+    o = O.Oracle(sc)
+    P = _floor_light_P(sc)
     # entry: y_{s-1} at the tiny triangle's centroid (index 4), h_c as above
     e = O.Entry(4, 1 / 3, 1 / 3, 1, 1, 0, 0.5, 0.5)
     f, q = o.entry_fq(e, 20000)
@@ -305,6 +309,50 @@ def test_reciprocal_of_incomplete_pdf_diffuse_control_vertex_quadrature():
     t, i, nodes, tr = o.entry_recip(e, B=1.2 * ratio.max(), n=20000)
     assert tr == 0
     assert abs(t.mean() - 1 / P) < 4 * t.std() / math.sqrt(len(t)) + 2e-3 / P
+
+
+@pytest.mark.parametrize("scene", ["square", "floor"])
+def test_pilot_bound_keeps_incomplete_pdf_estimate_unbiased(scene):
+    """The per-entry bound B is the largest f/q of a pilot on a stream the
+    estimate never reads (kind PILOT). It usually sits below the supremum, so
+    the estimate meets g < 0 and splits, yet B is fixed before the estimate's
+    draws: the mean must still be 1/P (closed form, resp. quadrature)."""
+    if scene == "square":
+        a, h = 0.1, 0.5
+        sc = scenes.pin_square_light(a=a, h=h)
+        P = (1.0 / (4 * a * a)) * (1 / math.pi) * 4 * _corner(a, a, h)
+        e = O.Entry(2, 1 / 3, 1 / 3, 1, 0, -1, 0.0, 0.0)
+        tol = 0.0
+    else:
+        sc = scenes.pin_floor_light(a=0.1, h=1.0, floor=1.0, ypos=(0.5, 0.3, 0.0))
+        P = _floor_light_P(sc)
+        e = O.Entry(4, 1 / 3, 1 / 3, 1, 1, 0, 0.5, 0.5)
+        tol = 2e-3 / P
+    o = O.Oracle(sc)
+    B = o.entry_pilot(e, seed=1, a=9, b=0, min_draws=64, max_draws=1024)
+    f, q = o.entry_fq(e, 20000)
+    ratio = np.where(q > 0, f / np.where(q > 0, q, 1.0), 0.0)
+    assert 0.0 < B < 1.5 * ratio.max()
+    t, i, nodes, tr = o.entry_recip(e, B=B, n=40000)
+    assert tr == 0
+    assert abs(t.mean() - 1 / P) < 4 * t.std() / math.sqrt(len(t)) + tol
+
+
+def test_pilot_bound_stopping_rule():
+    """The pilot draws a prefix of one stream in rounds of 32: once its
+    minimum is met it stops at the first round boundary with some f > 0, so
+    raising only the maximum changes nothing, and raising the minimum can
+    only raise the maximum seen."""
+    sc = scenes.pin_square_light(a=0.1, h=0.5)
+    o = O.Oracle(sc)
+    e = O.Entry(2, 1 / 3, 1 / 3, 1, 0, -1, 0.0, 0.0)
+    for b in range(6):
+        b32 = o.entry_pilot(e, seed=3, a=1, b=b, min_draws=32, max_draws=32)
+        assert b32 > 0.0
+        assert o.entry_pilot(e, seed=3, a=1, b=b, min_draws=32, max_draws=4096) == b32
+        assert o.entry_pilot(e, seed=3, a=1, b=b, min_draws=1, max_draws=1) == b32   # rounded up to 32
+        b256 = o.entry_pilot(e, seed=3, a=1, b=b, min_draws=256, max_draws=1024)
+        assert b256 >= b32
 
 
 # --- whole estimator ------------------------------------------------------------

@@ -41,7 +41,7 @@ def test_noalloc_estimates_match_pooled_estimator():
         mx = max(mx, float(r.max()))
     tab = scenes.random_tables(sc, KT=8, KS=8, KSp=4, KC=2, B=1.5 * mx, mis=1.0)
     r = N.Renderer(sc, tab)
-    cfg = N.config(M=1500, M_p=600, max_depth=6, repeats=5)
+    cfg = N.config(M=1500, M_p=600, max_depth=6, repeats=5, pilot_max=-1)   # table B, no per-entry pilot
     ref = r.iteration(cfg, 11, tri, bary)
     assert len(ref["rhat"]) == n
 
