@@ -9,6 +9,7 @@ it; the renderer in paper_2503_23412_gb300 never imports it.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -17,7 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
-SOURCES = ["or_philox.c", "or_scene.c", "or_bsdf.c", "or_recip.c", "or_render.c"]
+SOURCES = ["or_philox.c", "or_scene.c", "or_bsdf.c", "or_recip.c", "or_render.c", "or_mlp.c"]
 
 
 def build(force: bool = False) -> str:
@@ -47,7 +48,8 @@ class TablesDesc(C.Structure):
                 ("cent_T", C.c_void_p), ("cent_S", C.c_void_p), ("cent_Sp", C.c_void_p),
                 ("cent_C", C.c_void_p), ("gamma_conn", C.c_void_p), ("gamma_proxy", C.c_void_p),
                 ("B_tab", C.c_void_p), ("mis_tab", C.c_void_p),
-                ("tile", C.c_int), ("grid_w", C.c_int), ("grid_h", C.c_int), ("pi_grid", C.c_void_p)]
+                ("tile", C.c_int), ("grid_w", C.c_int), ("grid_h", C.c_int), ("pi_grid", C.c_void_p),
+                ("mlp_w", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -94,6 +96,16 @@ def lib():
         L.or_recip_1d.restype = C.c_int
         L.or_recip_1d.argtypes = [C.c_int, C.c_double, C.c_int, C.c_uint32, C.c_int, vp, vp, vp]
         L.or_entry_fq.argtypes = [vp, C.POINTER(Entry), C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, vp, vp]
+        L.or_bf16.restype = C.c_double
+        L.or_bf16.argtypes = [C.c_double]
+        L.or_mlp_logits.restype = None
+        L.or_mlp_logits.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, C.c_int, vp]
+        L.or_mlp_select.restype = C.c_int
+        L.or_mlp_select.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp, C.c_double, C.POINTER(C.c_double)]
+        L.or_mlp_loss_grad.restype = C.c_double
+        L.or_mlp_loss_grad.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp]
+        L.or_mlp_adam.restype = None
+        L.or_mlp_adam.argtypes = [C.c_int, vp, vp, vp, vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
         L.or_entry_pilot.restype = C.c_double
         L.or_entry_pilot.argtypes = [vp, C.POINTER(Entry), C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_int]
         L.or_entry_recip.restype = C.c_int
@@ -149,7 +161,10 @@ class Oracle:
                        _p(keep["bbox_lo"]), _p(keep["bbox_hi"]), _p(keep["cent_T"]), _p(keep["cent_S"]),
                        _p(keep["cent_Sp"]), _p(keep["cent_C"]), _p(keep["gamma_conn"]),
                        _p(keep["gamma_proxy"]), _p(keep["B_tab"]), _p(keep["mis_tab"]),
-                       int(t["tile"]), gw, gh, _p(keep["pi_grid"]))
+                       int(t["tile"]), gw, gh, _p(keep["pi_grid"]), None)
+        if t.get("mlp_w") is not None:
+            keep["mlp_w"] = np.ascontiguousarray(t["mlp_w"], np.float64)
+            d.mlp_w = _p(keep["mlp_w"])
         d._keep = keep
         return d
 
@@ -257,6 +272,64 @@ def philox(ctr, key):
 
 def uniform(seed, kind, a, b, c, d):
     return lib().or_uniform(seed, kind, a, b, c, d)
+
+
+# -- learned proposal (or_mlp.c) ------------------------------------------------
+def mlp_nparams(K, KT):
+    return 64 * 16 + 64 * 64 + 64 + 65 * K + 4 * KT
+
+
+def mlp_init(K, KT, seed=0):
+    """Flat weights: He-uniform hidden layers, small output layer, N(0, 0.5) embedding."""
+    rng = np.random.default_rng(seed)
+    w = np.zeros(mlp_nparams(K, KT))
+    o = 0
+    w[o:o + 1024] = rng.uniform(-1, 1, 1024) * math.sqrt(6 / 16); o += 1024
+    w[o:o + 4096] = rng.uniform(-1, 1, 4096) * math.sqrt(6 / 64); o += 4096
+    o += 64
+    w[o:o + 64 * K] = rng.uniform(-1, 1, 64 * K) * 0.05; o += 64 * K
+    o += K
+    w[o:o + 4 * KT] = rng.normal(0, 0.5, 4 * KT)
+    return w
+
+
+def bf16(x):
+    x = np.asarray(x, np.float64)
+    return np.vectorize(lib().or_bf16)(x) if x.ndim else lib().or_bf16(float(x))
+
+
+def mlp_logits(w, K, KT, raw, T, bf16_ops=False):
+    raw = np.ascontiguousarray(raw, np.float64)
+    T = np.ascontiguousarray(T, np.int32)
+    n = len(T)
+    z = np.zeros((n, K))
+    lib().or_mlp_logits(_p(np.ascontiguousarray(w, np.float64)), K, KT, n, _p(raw), _p(T), int(bf16_ops), _p(z))
+    return z
+
+
+def mlp_select(w, K, raw, T, g, start, u):
+    Q = C.c_double(0.0)
+    S = lib().or_mlp_select(_p(np.ascontiguousarray(w, np.float64)), K, _p(np.ascontiguousarray(raw, np.float64)),
+                            int(T), _p(np.ascontiguousarray(g, np.float32)), _p(np.ascontiguousarray(start, np.int32)),
+                            float(u), C.byref(Q))
+    return S, Q.value
+
+
+def mlp_loss_grad(w, K, KT, raw, T, S, wt):
+    w = np.ascontiguousarray(w, np.float64)
+    g = np.zeros_like(w)
+    n = len(T)
+    loss = lib().or_mlp_loss_grad(_p(w), K, KT, n, _p(np.ascontiguousarray(raw, np.float64)),
+                                  _p(np.ascontiguousarray(T, np.int32)), _p(np.ascontiguousarray(S, np.int32)),
+                                  _p(np.ascontiguousarray(wt, np.float64)), _p(g))
+    return loss, g
+
+
+def mlp_adam(w, g, m1, m2, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    w, m1, m2 = (np.array(a, np.float64) for a in (w, m1, m2))
+    lib().or_mlp_adam(len(w), _p(w), _p(np.ascontiguousarray(g, np.float64)), _p(m1), _p(m2), int(t), lr, beta1,
+                      beta2, eps)
+    return w, m1, m2
 
 
 def recip_1d(fn, B, n, seed=1, cap=1 << 20):

@@ -49,6 +49,7 @@ typedef struct {
     int KT, KS, KSp, KC;
     double lo[3], ext[3];
     const float *cT, *cS, *cSp, *cC, *gC, *gP, *Bt, *mis, *pi;
+    const double *mlp;
     int tile, gw, gh;
 } or_tab;
 
@@ -85,6 +86,7 @@ static void tab_init(or_tab *T, const or_tables_desc *t) {
     T->cT = t->cent_T; T->cS = t->cent_S; T->cSp = t->cent_Sp; T->cC = t->cent_C;
     T->gC = t->gamma_conn; T->gP = t->gamma_proxy; T->Bt = t->B_tab; T->mis = t->mis_tab;
     T->pi = t->pi_grid; T->tile = t->tile; T->gw = t->grid_w; T->gh = t->grid_h;
+    T->mlp = t->mlp_w;
 }
 
 static int nearest(const double *f, int dim, int K, const float *cent) {
@@ -123,6 +125,16 @@ static int label_dir(const or_tab *T, const or_vtx *v, v3 w, int K, const float 
     f[3] = n.x; f[4] = n.y; f[5] = n.z;
     f[6] = w.x; f[7] = w.y; f[8] = w.z;
     return nearest(f, 9, K, cent);
+}
+
+/* raw features of an eye vertex for the learned proposal: normalised
+ * position, normal facing w, w, roughness */
+static void feat_raw(const or_scene_t *s, const or_tab *T, const or_vtx *v, v3 w, double *f) {
+    feat_pos(T, v->p, f);
+    v3 n = vdot(v->n, w) >= 0.0 ? v->n : vneg(v->n);
+    f[3] = n.x; f[4] = n.y; f[5] = n.z;
+    f[6] = w.x; f[7] = w.y; f[8] = w.z;
+    f[9] = s->mats[v->mat].rough;
 }
 
 static int label_spec(const or_tab *T, const or_vtx *v) {
@@ -523,9 +535,26 @@ static v3 eye_path(const or_scene_t *s, const or_tab *T, const or_params *p, con
             if (p->conn && i + 2 <= p->max_depth && it->npool > 0) {
                 Tl = label_dir(T, z, we, T->KT, T->cT);
                 double Q;
-                int slot = select_item(T->gC + (size_t)Tl * T->KS, T->KS, it->bstart,
+                int slot;
+                if (T->mlp) {
+                    /* learned proposal: S ~ Q(. | x), then a uniform vertex of S */
+                    double raw[10], QS;
+                    feat_raw(s, T, z, we, raw);
+                    int Sel = or_mlp_select(T->mlp, T->KS, raw, Tl, T->gC + (size_t)Tl * T->KS, it->bstart,
+                                            or_rnd(p->seed, K_CAMERA, iteration, pu, ci, 6), &QS);
+                    slot = -1;
+                    if (Sel >= 0) {
+                        int nS = it->bstart[Sel + 1] - it->bstart[Sel];
+                        int jj = (int)floor(or_rnd(p->seed, K_CAMERA, iteration, pu, ci, 7) * nS);
+                        if (jj > nS - 1) jj = nS - 1;
+                        slot = it->bstart[Sel] + jj;
+                        Q = QS / nS;
+                    }
+                } else {
+                    slot = select_item(T->gC + (size_t)Tl * T->KS, T->KS, it->bstart,
                                        or_rnd(p->seed, K_CAMERA, iteration, pu, ci, 6),
                                        or_rnd(p->seed, K_CAMERA, iteration, pu, ci, 7), &Q);
+                }
                 if (slot >= 0) {
                     int jp = it->bitems[slot];
                     int l = it->pool_l[jp], e = it->pool_e[jp];
@@ -807,6 +836,7 @@ void or_learn(void *hs, const or_params *p, const or_tables_desc *td, int iter0,
     for (int c = 0; c < ncell; ++c) B_out[c] = (float)(B_SAFETY * (Bmax[c] > 0.0 ? Bmax[c] : gmax));
     /* pass 2: reciprocal statistics with the learned B */
     or_tables_desc t2 = *td;
+    t2.mlp_w = NULL;   /* statistics are learned with the table proposal */
     t2.B_tab = B_out;
     or_tab T2;
     tab_init(&T2, &t2);

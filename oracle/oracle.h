@@ -48,6 +48,7 @@ typedef struct {
     const float *mis_tab;             /* 4*KSp*(KC+1): 1/(E[R^2] * Pbar) */
     int tile, grid_w, grid_h;
     const float *pi_grid;             /* grid_h*grid_w proxy probability per tile */
+    const double *mlp_w;              /* learned light-subspace proposal (or_mlp.c layout), NULL: table rows */
 } or_tables_desc;
 
 typedef struct {
@@ -143,6 +144,19 @@ void or_render(void *h, const or_params *p, const or_tables_desc *t, int iter0, 
 
 /* Subspace labels of a vertex (nearest centroid, ties to the lowest index). */
 int or_label_9(const or_tables_desc *t, const double *feat9, int K, const float *cent);
+
+/* Learned light-subspace proposal (or_mlp.c): weights are a flat vector of
+ * or_mlp_nparams(K, KT) doubles; raw features are 10 per row (normalised
+ * position, facing normal, incident direction, roughness). */
+size_t or_mlp_nparams(int K, int KT);
+double or_bf16(double x);
+void or_mlp_logits(const double *w, int K, int KT, int n, const double *raw, const int *T, int bf16, double *z);
+int or_mlp_select(const double *w, int K, const double *raw, int T, const float *g, const int *start, double u,
+                  double *Q);
+double or_mlp_loss_grad(const double *w, int K, int KT, int n, const double *raw, const int *T, const int *S,
+                        const double *wt, double *grad);
+void or_mlp_adam(int np, double *w, const double *g, double *m1, double *m2, int t, double lr, double beta1,
+                 double beta2, double eps);
 
 /* Statistics / selection learning (Sec. 5.4-5.5 as read in the design notes).
  * Inputs: centroids in t (gamma/B/mis/pi entries are ignored and rebuilt).
