@@ -110,6 +110,11 @@ typedef struct {
      * table value. */
     int pilot_min;
     int pilot_max;
+    /* Light-subspace proposal of the subspace connection (Sec. 3.2): 0 = the
+     * table row Gamma[T, .]; 1 = the learned network mixed with the table,
+     * Q(S | x) = 0.9 softmax(MLP(x))_S + 0.1 Gamma[T, S] / Z_T over occupied
+     * subspaces (needs a network: pb_mlp_upload or pb_train_proposal). */
+    int proposal;
 } pb_config;
 
 typedef struct {
@@ -124,6 +129,7 @@ typedef struct {
     int64_t n_waves;                              /* launch waves (iterations in flight per wave) */
     /* traversal work when count_traversal = 1: eye kernel and estimator kernel */
     int64_t eye_nodes, eye_tris, eye_rays, rec_nodes, rec_tris, rec_rays;
+    double ms_mlp;             /* device time of the proposal's feature pass and network (proposal = 1) */
 } pb_stats;
 
 pb_status pb_create(pb_ctx **out, int device, void *cuda_stream /* NULL: own stream */);
@@ -227,6 +233,68 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
 pb_status pb_recip_estimates_noalloc(pb_ctx *ctx, const pb_config *cfg, int iteration, int n,
                                      const int32_t *d_tri, const float *d_bary, const int32_t *d_info,
                                      const float *d_B, float *d_rhat, float *d_nodes, int *n_truncated);
+
+/* ---- learned light-subspace proposal --------------------------------------
+ * Not in the paper, which selects the light subspace of a connection from the
+ * learned table Gamma[T, .] (Sec. 3.2, Sec. 5.5). The network maps features
+ * of the eye vertex x = (position normalised to the table box, normal facing
+ * the incident direction, incident direction, roughness, a 4-d embedding of
+ * T, 1, 0) through 16 -> 64 ReLU -> 64 ReLU -> KS logits. Weights are a flat
+ * fp32 vector, row-major with the output index first:
+ *   W1[64][16] | W2[64][64] | b2[64] | W3[KS][64] | b3[KS] | E[KT][4]
+ * with KS, KT those of the uploaded tables (KS <= 384). Inference runs with
+ * bf16 operands and fp32 accumulation on the tensor cores; training in fp32.
+ * The loss of a batch is -(1/n) sum_b w_b log softmax(z_b)[S_b]. All calls
+ * are synchronous. */
+size_t pb_mlp_nparams(int KS, int KT);
+/* copies the n = pb_mlp_nparams weights (host) and resets Adam's moments */
+pb_status pb_mlp_upload(pb_ctx *ctx, const float *w, size_t n);
+pb_status pb_mlp_readback(pb_ctx *ctx, float *w, size_t n);
+/* logits of n rows: raw features n x 10 (host), eye subspaces T (host); z is
+ * n x KS (host). Runs the tensor-core kernel of the render path. */
+pb_status pb_mlp_logits(pb_ctx *ctx, int n, const float *raw, const int32_t *T, float *z);
+/* gradient of the batch loss (host arrays: raw n x 10, T, S, w; grad has
+ * pb_mlp_nparams entries); loss may be NULL */
+pb_status pb_mlp_grad(pb_ctx *ctx, int n, const float *raw, const int32_t *T, const int32_t *S, const float *w,
+                      float *grad, float *loss);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on the gradient of the batch */
+pb_status pb_mlp_train_batch(pb_ctx *ctx, int n, const float *raw, const int32_t *T, const int32_t *S,
+                             const float *w, float lr, float *loss);
+
+typedef struct {
+    int samples;               /* training samples collected per round (buffer size) */
+    int rounds;                /* collect-then-train rounds */
+    int steps;                 /* Adam steps per round */
+    int batch;                 /* samples per step, drawn with replacement from the round's samples */
+    float lr;                  /* Adam step size (0: 1e-3) */
+    uint32_t seed;             /* initialisation and mini-batch draws */
+    int iter0;                 /* first iteration number of the collection renders */
+    int max_iters_per_round;   /* collection iterations per round at most (0: 256) */
+    int iters_per_wave;        /* iterations in flight while collecting (0: 8) */
+    int reinit;                /* 1: start from a fresh initialisation even if a network is loaded */
+    int learned_first;         /* 1: the first round already collects with the network */
+} pb_train_desc;
+
+typedef struct {
+    int64_t iterations, samples, steps;
+    double loss_first, loss_last;
+} pb_train_stats;
+
+/* Online training: each round renders collection iterations (never added to
+ * the film) with the current proposal -- the table in the first round unless
+ * learned_first -- and records one sample per connection with a non-zero
+ * contribution (features, T, the chosen S, the unweighted contribution
+ * luminance, which already carries the 1/Q(S) of the proposal that drew it),
+ * then takes `steps` Adam steps on mini-batches of those samples. */
+pb_status pb_train_proposal(pb_ctx *ctx, const pb_config *cfg, const pb_train_desc *td, pb_train_stats *out);
+
+/* Moments of the subspace-connection estimate under cfg->proposal: renders
+ * iterations [iter0, iter0 + spp) without touching the film and returns
+ * out[0] = connections made, out[1] = sum of their unweighted contribution
+ * luminance, out[2] = sum of its squares. Both proposals are unbiased, so
+ * out[1] / out[0] agrees between them up to noise, and the proposal with the
+ * smaller out[2] / out[0] is the better one. */
+pb_status pb_connection_moments(pb_ctx *ctx, const pb_config *cfg, double *out);
 
 #ifdef __cplusplus
 }

@@ -123,6 +123,7 @@ pb_status check_cfg(pb_ctx *ctx, const pb_config *c) {
     if (c->repeats < 1 || c->repeats > 8) return fail(ctx, PB_ERR_ARG, "repeats must be in [1, 8]");
     if (c->trial_cap < 1) return fail(ctx, PB_ERR_ARG, "trial_cap must be positive");
     if (c->spp < 0) return fail(ctx, PB_ERR_ARG, "spp must be >= 0");
+    if (c->proposal < 0 || c->proposal > 1) return fail(ctx, PB_ERR_ARG, "proposal must be 0 (table) or 1 (learned)");
     return PB_OK;
 }
 
@@ -150,6 +151,8 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
         P.pilot_max = hi;
     }
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
+    P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    P.smp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
     return P;
 }
 
@@ -301,6 +304,7 @@ void pb_destroy(pb_ctx *ctx) {
     free_all(ctx->scene_mem);
     free_all(ctx->table_mem);
     free_all(ctx->pool_mem);
+    mlp_free(ctx);
     if (ctx->film) cudaFree(ctx->film);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -409,6 +413,7 @@ pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *d) {
         M.kind = (int)m[0];
         M.cr = m[1]; M.cg = m[2]; M.cb = m[3];
         M.alpha = m[4] * m[4];
+        M.rough = m[4];
         M.ior = m[5];
         M.ler = m[6]; M.leg = m[7]; M.leb = m[8];
         M.textured = m[9] != 0.0f;
@@ -532,6 +537,28 @@ pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *t) {
     return PB_OK;
 }
 
+}  // extern "C"
+
+pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t iter_base, const SampleSink &sink) {
+    KParams P = kparams(ctx, cfg);
+    pb_status s = ensure_pool(ctx, slots, P.M * P.L, P.repeats, P.npix);
+    if (s != PB_OK) return s;
+    launch_light_pass(ctx->S, P, ctx->B, slots, iter_base, ctx->stream);
+    launch_pool_build(ctx->S, ctx->T, P, ctx->B, slots, ctx->stream);
+    launch_recip(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->num_sms, ctx->stream);
+    if (cfg->proposal) {
+        s = mlp_wave(ctx, P, slots, iter_base);
+        if (s != PB_OK) return s;
+    }
+    P.smp = sink;
+    launch_eye(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->Lbuf, nullptr, ctx->stream);
+    CK(cudaGetLastError());
+    if (cfg->proposal) return mlp_check_err(ctx);
+    return PB_OK;
+}
+
+extern "C" {
+
 pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
     if (!ctx) return PB_ERR_ARG;
     pb_status s = check_cfg(ctx, cfg);
@@ -544,14 +571,15 @@ pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
     if (s != PB_OK) return s;
     CK(cudaMemsetAsync(ctx->B.counters, 0, sizeof(unsigned long long) * CNT_N, ctx->stream));
     int waves = (cfg->spp + slots - 1) / slots;
-    std::vector<cudaEvent_t> ev(5 * (size_t)std::max(waves, 0));
+    constexpr int NEV = 6;
+    std::vector<cudaEvent_t> ev(NEV * (size_t)std::max(waves, 0));
     for (auto &e : ev) CK(cudaEventCreate(&e));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     int w = 0;
     for (int done = 0; done < cfg->spp; ++w) {
         int ns = std::min(slots, cfg->spp - done);
         uint32_t base = (uint32_t)(cfg->iter0 + done);
-        cudaEvent_t *e = &ev[5 * (size_t)w];
+        cudaEvent_t *e = &ev[NEV * (size_t)w];
         CK(cudaEventRecord(e[0], ctx->stream));
         launch_light_pass(ctx->S, P, ctx->B, ns, base, ctx->stream);
         CK(cudaEventRecord(e[1], ctx->stream));
@@ -559,8 +587,14 @@ pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
         CK(cudaEventRecord(e[2], ctx->stream));
         launch_recip(ctx->S, ctx->T, P, ctx->B, ns, base, ctx->num_sms, ctx->stream);
         CK(cudaEventRecord(e[3], ctx->stream));
-        launch_eye(ctx->S, ctx->T, P, ctx->B, ns, base, ctx->Lbuf, nullptr, ctx->stream);
+        KParams Pw = P;
+        if (cfg->proposal) {
+            s = mlp_wave(ctx, Pw, ns, base);
+            if (s != PB_OK) return s;
+        }
         CK(cudaEventRecord(e[4], ctx->stream));
+        launch_eye(ctx->S, ctx->T, Pw, ctx->B, ns, base, ctx->Lbuf, nullptr, ctx->stream);
+        CK(cudaEventRecord(e[5], ctx->stream));
         launch_film_add(P, ns, ctx->Lbuf, ctx->film, ctx->stream);
         CK(cudaGetLastError());
         done += ns;
@@ -575,20 +609,27 @@ pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
     st.ms = ms;
     st.mpaths_per_s = ms > 0 ? (double)P.npix * cfg->spp / (ms * 1e-3) / 1e6 : 0.0;
     for (int i = 0; i < waves; ++i) {
-        float a = 0, b = 0, c = 0, d = 0;
-        cudaEvent_t *e = &ev[5 * (size_t)i];
+        float a = 0, b = 0, c = 0, d = 0, m = 0;
+        cudaEvent_t *e = &ev[NEV * (size_t)i];
         cudaEventElapsedTime(&a, e[0], e[1]);
         cudaEventElapsedTime(&b, e[1], e[2]);
         cudaEventElapsedTime(&c, e[2], e[3]);
-        cudaEventElapsedTime(&d, e[3], e[4]);
+        cudaEventElapsedTime(&m, e[3], e[4]);
+        cudaEventElapsedTime(&d, e[4], e[5]);
         st.ms_light += a;
         st.ms_pool += b;
         st.ms_recip += c;
+        st.ms_mlp += m;
         st.ms_eye += d;
     }
     for (auto &e : ev) cudaEventDestroy(e);
     st.n_waves = waves;
-    st.n_launches = 10 * (int64_t)waves;  // light, pool, bucket, cdf, offsets, recip x2, finish, eye, film
+    // light, pool, bucket, cdf, offsets, pilot, recip x2, finish, eye, film; proposal: feature pass, network
+    st.n_launches = (11 + (cfg->proposal ? 2 : 0)) * (int64_t)waves;
+    if (cfg->proposal) {
+        s = mlp_check_err(ctx);
+        if (s != PB_OK) return s;
+    }
     read_counters(ctx, &st);
     if (stats) *stats = st;
     if (st.n_truncated > 0) return fail(ctx, PB_ERR_TRUNCATED, "reciprocal estimate hit the trial cap");
@@ -713,9 +754,17 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
     } else {
         launch_recip(ctx->S, ctx->T, P, ctx->B, 1, (uint32_t)iteration, ctx->num_sms, ctx->stream);
     }
+    if (cfg->proposal) {
+        s = mlp_wave(ctx, P, 1, (uint32_t)iteration);
+        if (s != PB_OK) return s;
+    }
     launch_eye(ctx->S, ctx->T, P, ctx->B, 1, (uint32_t)iteration, ctx->Lbuf, ctx->sigbuf, ctx->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
+    if (cfg->proposal) {
+        s = mlp_check_err(ctx);
+        if (s != PB_OK) return s;
+    }
     if (n_entries) *n_entries = ne;
     int k = std::min(ne, std::max(cap, 0));
     if (host_pix_rgb) {

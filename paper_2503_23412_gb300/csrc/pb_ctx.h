@@ -7,6 +7,31 @@
 #include "../../include/proxybdpt.h"
 #include "pb_kernels.h"
 
+// learned proposal: network, Adam state, eye-pass rows, training buffers
+struct MlpState {
+    int K = 0, KT = 0, Kpad = 0;
+    size_t np = 0;
+    float *w = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;   // fp32 master weights, gradient, moments
+    int step = 0;
+    bool ready = false;                 // bf16 images are current
+    uint8_t *img = nullptr;             // bf16 operand images of W1, W2, W3
+    float *bias = nullptr;              // b2 | b3 (padded)
+    uint16_t *emb = nullptr;            // bf16 E[KT][4]
+    int *err = nullptr;                 // set by the tensor-core kernel when a wait times out
+    uint16_t *rows = nullptr;
+    int32_t *rowT = nullptr, *sel = nullptr;
+    float *selq = nullptr;
+    size_t cap_rows16 = 0, cap_rowT = 0, cap_sel = 0, cap_selq = 0;
+    float *s_raw = nullptr, *s_w = nullptr;
+    int32_t *s_T = nullptr, *s_S = nullptr;
+    unsigned int *s_count = nullptr;
+    size_t s_cap = 0;
+    int b_cap = 0;
+    float *b_X = nullptr, *b_a = nullptr, *b_H1 = nullptr, *b_H2 = nullptr, *b_DH1 = nullptr, *b_DH2 = nullptr,
+          *b_DZ = nullptr, *b_DE = nullptr, *b_loss = nullptr;
+    int32_t *b_T = nullptr, *b_S = nullptr;
+};
+
 struct pb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -27,6 +52,7 @@ struct pb_ctx {
     float *film = nullptr;
     int64_t film_iters = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    MlpState mlp;
 };
 
 // shared by the host translation units
@@ -36,3 +62,9 @@ pb_status pb_run_wave(pb_ctx *ctx, const KParams &P, int slots, uint32_t iter_ba
                       bool with_recip, uint32_t *sig);
 KParams pb_kparams(const pb_ctx *ctx, const pb_config *c);
 pb_status pb_check_cfg(pb_ctx *ctx, const pb_config *c);
+// learned proposal (pb_mlp.cu)
+void mlp_free(pb_ctx *ctx);
+pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base);
+pb_status mlp_check_err(pb_ctx *ctx);
+// one wave of iterations that records proposal training samples and leaves the film alone (pb_api.cu)
+pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t iter_base, const SampleSink &sink);

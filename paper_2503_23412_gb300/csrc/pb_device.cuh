@@ -83,7 +83,8 @@ struct DMat {
     float alpha, ior;
     float ler, leg, leb;
     int textured, specular, emitter, black;
-    float pad[3];
+    float rough;             // roughness (alpha = rough^2)
+    float pad[2];
 };
 
 struct DScene {

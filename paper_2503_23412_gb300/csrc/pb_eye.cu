@@ -22,6 +22,7 @@
 // and NEE weights of paths with the proxy shape; connections (s >= 2) can
 // never produce such paths (both joined vertices must be non-specular).
 #include "pb_kernels.h"
+#include "pb_mlp.cuh"
 
 namespace {
 
@@ -192,16 +193,26 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
             // ---- (s >= 2) subspace probabilistic connection
             if (P.conn && a + 2 <= P.max_depth && npool > 0) {
                 Tl = label_dir(S, z, we, T.KT, T.cT);
-                const float *cdf = B.cdfC + (size_t)slot * T.KT * T.KS + (size_t)Tl * T.KS;
-                int Ssel = select_cdf(cdf, T.KS, R.u(6));
+                int Ssel;
+                float QS;   // probability of the subspace
+                if (P.mlp.sel) {
+                    // learned proposal: drawn by the network kernel from this vertex's row
+                    size_t row = ((size_t)slot * P.mlp.A + (a - 1)) * P.npix + pix;
+                    Ssel = P.mlp.sel[row];
+                    QS = P.mlp.selq[row];
+                } else {
+                    const float *cdf = B.cdfC + (size_t)slot * T.KT * T.KS + (size_t)Tl * T.KS;
+                    Ssel = select_cdf(cdf, T.KS, R.u(6));
+                    QS = T.gC[(size_t)Tl * T.KS + Ssel] / B.ZC[(size_t)slot * T.KT + Tl];
+                }
                 const int32_t *bst = B.bstart + (size_t)slot * (T.KS + 1);
-                int nS = bst[Ssel + 1] - bst[Ssel];
+                int nS = Ssel >= 0 ? bst[Ssel + 1] - bst[Ssel] : 0;
                 if (nS > 0) {
                     int jj = min((int)(R.u(7) * (float)nS), nS - 1);
                     int jp = B.bitems[so + bst[Ssel] + jj];
                     int fixed = B.pool_idx[so + jp];
                     int e = fixed % P.L;
-                    float Q = (T.gC[(size_t)Tl * T.KS + Ssel] / B.ZC[(size_t)slot * T.KT + Tl]) / (float)nS;
+                    float Q = QS / (float)nS;
                     sig = sig_upd(sig, 0xB0000000u | (uint32_t)jp);
                     n_conn++;
                     int sl = e + 1;
@@ -244,6 +255,15 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                                 }
                                 float w = 1.0f / (1.0f + Ls + Ea);
                                 L = L + c * w;
+                                if (P.smp.raw) {
+                                    unsigned int idx = atomicAdd(P.smp.count, 1u);
+                                    if (idx < (unsigned int)P.smp.cap) {
+                                        mlp_raw(S, z, we, P.smp.raw + (size_t)MLP_NRAW * idx);
+                                        P.smp.T[idx] = Tl;
+                                        P.smp.S[idx] = Ssel;
+                                        P.smp.w[idx] = lum(c);
+                                    }
+                                }
                                 if (P.acc.conn) {
                                     atomicAdd(&P.acc.tile_all[tile], lum(c) * w);
                                     atomicAdd(&P.acc.conn[(size_t)Tl * T.KS + Ssel], lum(c));
@@ -430,6 +450,51 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
     }
 }
 
+// Feature pass of the learned proposal: the same camera sub-paths as k_eye
+// (the walk uses only the BSDF dimensions 0-2, never a connection's
+// choice), writing the network's input row and eye subspace at every vertex
+// where k_eye makes a subspace connection. Rows of other vertices keep
+// rowT = -1.
+__global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base) {
+    int pix = blockIdx.x * blockDim.x + threadIdx.x;
+    int slot = blockIdx.y;
+    if (pix >= P.npix) return;
+    if (!P.conn || B.npool[slot] <= 0) return;
+    uint32_t it = iter_base + (uint32_t)slot;
+    int px = pix % S.W, py = pix / S.W;
+    Rng r0;
+    r0.init(P.seed, K_CAMERA, it, (uint32_t)pix, 0);
+    float j0 = r0.u(0), j1 = r0.u(1);
+    float sx = 2.0f * ((float)px + j0) / (float)S.W - 1.0f, sy = 1.0f - 2.0f * ((float)py + j1) / (float)S.H;
+    float3 d = normalize(S.cfwd + (S.cright * (sx * S.tanh_ * S.aspect) + S.cup * (sy * S.tanh_)));
+    Hit h = closest_hit<false>(S, S.cpos, d, -1, nullptr);
+    int a = 1;
+    while (h.tri >= 0) {
+        Vtx z = vertex_at(S, h.tri, h.b1, h.b2);
+        const DMat &mz = S.mats[z.mat];
+        float3 we = -d;
+        if (absorbing(S, z, we)) break;
+        if (!mz.specular && a + 2 <= P.max_depth) {
+            int Tl = label_dir(S, z, we, T.KT, T.cT);
+            size_t row = ((size_t)slot * P.mlp.A + (a - 1)) * P.npix + pix;
+            float raw[MLP_NRAW];
+            mlp_raw(S, z, we, raw);
+            mlp_pack_row(raw, Tl, P.mlp.emb, P.mlp.rows + (size_t)MLP_NX * row);
+            P.mlp.rowT[row] = Tl;
+        }
+        if (a + 1 > P.max_depth) break;
+        Rng R;
+        R.init(P.seed, K_CAMERA, it, (uint32_t)pix, (uint32_t)a);
+        float3 wl;
+        if (!bsdf_sample(mz, z.n, we, R.u(0), R.u(1), R.u(2), wl)) break;
+        float pw = bsdf_pdf(mz, z.n, we, wl);
+        if (!(pw > 0.0f)) break;
+        d = wl;
+        h = closest_hit<false>(S, z.p, d, z.tri, nullptr);
+        ++a;
+    }
+}
+
 __global__ void k_film_add(KParams P, int slots, const float4 *Lbuf, float *film) {
     int pix = blockIdx.x * blockDim.x + threadIdx.x;
     if (pix >= P.npix) return;
@@ -452,6 +517,12 @@ void launch_eye(const DScene &S, const DTables &T, const KParams &P, const Pool 
     dim3 grid((P.npix + 127) / 128, slots);
     if (P.count) k_eye<true><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
     else k_eye<false><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
+}
+
+void launch_eye_feat(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
+                     cudaStream_t st) {
+    dim3 grid((P.npix + 127) / 128, slots);
+    k_eye_feat<<<grid, 128, 0, st>>>(S, T, P, B, iter_base);
 }
 
 void launch_film_add(const KParams &P, int slots, const float4 *Lbuf, float *film, cudaStream_t st) {

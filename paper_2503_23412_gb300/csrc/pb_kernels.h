@@ -14,6 +14,28 @@ struct LearnAcc {
 };
 
 // Render parameters as the kernels see them.
+// Learned light-subspace proposal: per (slot, eye vertex a, pixel) input
+// rows of the network and the subspace it selected. Row index
+// ((slot * A) + a - 1) * npix + pix for eye vertices a = 1..A.
+struct MlpRows {
+    uint16_t *rows;         // bf16[16] network input per row
+    int32_t *rowT;          // eye subspace T of the row, -1: no connection there
+    const int32_t *sel;     // selected light subspace (-1: none)
+    const float *selq;      // its proposal probability Q(S | x)
+    const uint16_t *emb;    // bf16[KT][4] embedding of T
+    int A;                  // eye vertices with a row per pixel (max_depth - 2)
+};
+
+// Training samples of the proposal: one per connection with a non-zero
+// contribution (raw features, T, S, unweighted contribution luminance).
+struct SampleSink {
+    float *raw;             // [cap][10]
+    int32_t *T, *S;
+    float *w;
+    unsigned int *count;
+    int cap;
+};
+
 struct KParams {
     uint32_t seed;
     int max_depth, M, M_p, repeats, proxy, conn, trial_cap;
@@ -23,6 +45,8 @@ struct KParams {
     int handoff;    // estimator nodes walked by a warp before a block continues the chain
     int pilot_min, pilot_max;   // per-entry B pilot draws (multiples of 32; pilot_max 0 = off)
     LearnAcc acc;
+    MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
+    SampleSink smp;         // raw != nullptr: record proposal training samples
 };
 
 // Walk state of a reciprocal estimate handed from a warp to a block: the next
@@ -80,6 +104,8 @@ void launch_recip(const DScene &S, const DTables &T, const KParams &P, const Poo
                   uint32_t iter_base, int num_sms, cudaStream_t st);
 void launch_eye(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                 float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st);
+void launch_eye_feat(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
+                     cudaStream_t st);
 void launch_film_add(const KParams &P, int slots, const float4 *Lbuf, float *film, cudaStream_t st);
 void launch_trace(const DScene &S, const float *rays, int n, float *hits, int count, unsigned long long *counters,
                   cudaStream_t st);

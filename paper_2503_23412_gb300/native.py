@@ -39,7 +39,7 @@ class pb_config(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("spp", C.c_int), ("max_depth", C.c_int), ("M", C.c_int),
                 ("M_p", C.c_int), ("repeats", C.c_int), ("proxy", C.c_int), ("conn", C.c_int),
                 ("trial_cap", C.c_int), ("iter0", C.c_int), ("batch", C.c_int), ("count_traversal", C.c_int),
-                ("chain_handoff", C.c_int), ("pilot_min", C.c_int), ("pilot_max", C.c_int)]
+                ("chain_handoff", C.c_int), ("pilot_min", C.c_int), ("pilot_max", C.c_int), ("proposal", C.c_int)]
 
 
 class pb_stats(C.Structure):
@@ -49,7 +49,21 @@ class pb_stats(C.Structure):
                 ("ms_pool", C.c_double), ("ms_recip", C.c_double), ("ms_eye", C.c_double),
                 ("n_launches", C.c_int64), ("n_waves", C.c_int64), ("eye_nodes", C.c_int64),
                 ("eye_tris", C.c_int64), ("eye_rays", C.c_int64), ("rec_nodes", C.c_int64),
-                ("rec_tris", C.c_int64), ("rec_rays", C.c_int64)]
+                ("rec_tris", C.c_int64), ("rec_rays", C.c_int64), ("ms_mlp", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pb_train_desc(C.Structure):
+    _fields_ = [("samples", C.c_int), ("rounds", C.c_int), ("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_float),
+                ("seed", C.c_uint32), ("iter0", C.c_int), ("max_iters_per_round", C.c_int),
+                ("iters_per_wave", C.c_int), ("reinit", C.c_int), ("learned_first", C.c_int)]
+
+
+class pb_train_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("samples", C.c_int64), ("steps", C.c_int64), ("loss_first", C.c_double),
+                ("loss_last", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -72,7 +86,9 @@ _lib = None
 
 EXPORTS = ["pb_create", "pb_destroy", "pb_last_error", "pb_scene_upload", "pb_tables_upload", "pb_render",
            "pb_film_clear", "pb_film_readback", "pb_film_device", "pb_trace", "pb_occluded", "pb_light_pass",
-           "pb_iteration", "pb_prepare", "pb_tables_readback", "pb_recip_estimates_noalloc"]
+           "pb_iteration", "pb_prepare", "pb_tables_readback", "pb_recip_estimates_noalloc", "pb_mlp_nparams",
+           "pb_mlp_upload", "pb_mlp_readback", "pb_mlp_logits", "pb_mlp_grad", "pb_mlp_train_batch",
+           "pb_train_proposal", "pb_connection_moments"]
 
 
 def lib(path=LIB):
@@ -103,9 +119,18 @@ def lib(path=LIB):
     L.pb_tables_readback.argtypes = [vp, C.POINTER(pb_tables_host)]
     L.pb_recip_estimates_noalloc.argtypes = [vp, C.POINTER(pb_config), i32, i32, vp, vp, vp, vp, vp, vp,
                                              C.POINTER(i32)]
+    L.pb_mlp_upload.argtypes = [vp, vp, C.c_size_t]
+    L.pb_mlp_readback.argtypes = [vp, vp, C.c_size_t]
+    L.pb_mlp_logits.argtypes = [vp, i32, vp, vp, vp]
+    L.pb_mlp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, C.POINTER(C.c_float)]
+    L.pb_mlp_train_batch.argtypes = [vp, i32, vp, vp, vp, vp, C.c_float, C.POINTER(C.c_float)]
+    L.pb_train_proposal.argtypes = [vp, C.POINTER(pb_config), C.POINTER(pb_train_desc), C.POINTER(pb_train_stats)]
+    L.pb_connection_moments.argtypes = [vp, C.POINTER(pb_config), vp]
     for n in EXPORTS:
         if n not in ("pb_destroy", "pb_last_error"):
             getattr(L, n).restype = i32
+    L.pb_mlp_nparams.argtypes = [i32, i32]
+    L.pb_mlp_nparams.restype = C.c_size_t
     _lib = L
     return L
 
@@ -121,9 +146,15 @@ class PBError(RuntimeError):
 
 
 def config(seed=7, spp=1, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, conn=1, trial_cap=1 << 16, iter0=0,
-           batch=0, count_traversal=0, chain_handoff=0, pilot_min=0, pilot_max=0):
+           batch=0, count_traversal=0, chain_handoff=0, pilot_min=0, pilot_max=0, proposal=0):
     return pb_config(seed, spp, max_depth, M, M_p, repeats, proxy, conn, trial_cap, iter0, batch, count_traversal,
-                     chain_handoff, pilot_min, pilot_max)
+                     chain_handoff, pilot_min, pilot_max, proposal)
+
+
+def train_desc(samples=1 << 20, rounds=2, steps=400, batch=4096, lr=1e-3, seed=1, iter0=1 << 23, max_iters_per_round=0,
+               iters_per_wave=0, reinit=0, learned_first=0):
+    return pb_train_desc(samples, rounds, steps, batch, lr, seed, iter0, max_iters_per_round, iters_per_wave, reinit,
+                         learned_first)
 
 
 def tables_desc(t, W, H):
@@ -266,6 +297,65 @@ class Renderer:
         self._check(self.L.pb_recip_estimates_noalloc(self.h, C.byref(cfg), iteration, n, d_tri, d_bary, d_info, d_B,
                                                       d_rhat, d_nodes, C.byref(ntr)))
         return ntr.value
+
+    # -- learned proposal ---------------------------------------------------------
+    def _table_dims(self):
+        t = pb_tables_host()
+        self._check(self.L.pb_tables_readback(self.h, C.byref(t)))   # null arrays: sizes only
+        return t.KS, t.KT
+
+    @property
+    def KS(self):
+        return self._table_dims()[0]
+
+    @property
+    def KT(self):
+        return self._table_dims()[1]
+
+    def mlp_nparams(self):
+        return int(self.L.pb_mlp_nparams(self.KS, self.KT))
+
+    def mlp_upload(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        self._check(self.L.pb_mlp_upload(self.h, _p(w), w.size))
+
+    def mlp_readback(self):
+        w = np.zeros(self.mlp_nparams(), np.float32)
+        self._check(self.L.pb_mlp_readback(self.h, _p(w), w.size))
+        return w
+
+    def mlp_logits(self, raw, T):
+        raw = np.ascontiguousarray(raw, np.float32)
+        T = np.ascontiguousarray(T, np.int32)
+        z = np.zeros((len(T), self.KS), np.float32)
+        self._check(self.L.pb_mlp_logits(self.h, len(T), _p(raw), _p(T), _p(z)))
+        return z
+
+    def mlp_grad(self, raw, T, S, w):
+        raw, w = (np.ascontiguousarray(a, np.float32) for a in (raw, w))
+        T, S = (np.ascontiguousarray(a, np.int32) for a in (T, S))
+        g = np.zeros(self.mlp_nparams(), np.float32)
+        loss = C.c_float(0.0)
+        self._check(self.L.pb_mlp_grad(self.h, len(T), _p(raw), _p(T), _p(S), _p(w), _p(g), C.byref(loss)))
+        return loss.value, g
+
+    def mlp_train_batch(self, raw, T, S, w, lr):
+        raw, w = (np.ascontiguousarray(a, np.float32) for a in (raw, w))
+        T, S = (np.ascontiguousarray(a, np.int32) for a in (T, S))
+        loss = C.c_float(0.0)
+        self._check(self.L.pb_mlp_train_batch(self.h, len(T), _p(raw), _p(T), _p(S), _p(w), lr, C.byref(loss)))
+        return loss.value
+
+    def connection_moments(self, cfg):
+        out = np.zeros(3)
+        self._check(self.L.pb_connection_moments(self.h, C.byref(cfg), _p(out)))
+        n, s1, s2 = out
+        return dict(n=n, mean=s1 / max(n, 1), m2=s2 / max(n, 1), relvar=(s2 / max(n, 1)) / max((s1 / max(n, 1)) ** 2, 1e-300) - 1)
+
+    def train_proposal(self, cfg, td):
+        st = pb_train_stats()
+        self._check(self.L.pb_train_proposal(self.h, C.byref(cfg), C.byref(td), C.byref(st)))
+        return st.as_dict()
 
     def close(self):
         if self.h:
