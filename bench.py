@@ -145,7 +145,7 @@ def oracle_tables(scene):
     return o, o.tables(tab)
 
 
-def oracle_iteration_rate(o, td, M_p, it, npx):
+def oracle_iteration_rate(o, td, M_p, it, npx, keep=False):
     """CPU oracle, one iteration of the workload measured in two parts: the
     light side (light pass, pool, all reciprocal estimates) and the eye paths
     of the first `npx` pixels (reusing those estimates). Returns the
@@ -161,18 +161,29 @@ def oracle_iteration_rate(o, td, M_p, it, npx):
     o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0, rhat=r["rhat"])
     t_pool = time.perf_counter() - t0
     t0 = time.perf_counter()
-    o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=npx, rhat=r["rhat"])
+    px = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=npx, rhat=r["rhat"])
     t_eye = max(time.perf_counter() - t0 - t_pool, 1e-9)
     rate = W * H / (t_light + W * H * t_eye / npx) / 1e6
+    if keep:
+        return rate, t_light + t_pool + t_eye, np.asarray(px["rgb"], np.float64)
     return rate, t_light + t_pool + t_eye
 
 
 def oracle_sample(scene, M_p, npx=2048):
+    """Returns the extrapolated rate, its description and the sampled
+    pixels' 1-spp radiance (first `npx` pixels)."""
     o, td = oracle_tables(scene)
-    rate, secs = oracle_iteration_rate(o, td, M_p, 0, npx)
+    rate, secs, rgb = oracle_iteration_rate(o, td, M_p, 0, npx, keep=True)
     desc = ("1 iteration, 1 thread: light pass (M=%d), reciprocal estimates (M_p=%d) and eye paths of %d of %d "
-            "pixels (%.1f s); extrapolated to the full 256x256 iteration" % (M, M_p, npx, W * H, secs))
-    return rate, desc
+            "pixels (%.1f s); extrapolated to the full %dx%d iteration" % (M, M_p, npx, W * H, secs, W, H))
+    return rate, desc, rgb
+
+
+def mape(x, ref):
+    """mean over pixels and channels of |x - r| / (r + eps), eps = 1e-2 mean(r)"""
+    x, ref = np.asarray(x, np.float64), np.asarray(ref, np.float64)
+    eps = 1e-2 * float(ref.mean())
+    return float(np.mean(np.abs(x - ref) / (ref + eps)))
 
 
 def run_reference(args):
@@ -200,6 +211,55 @@ def run_reference(args):
            "cpu_baseline": {"value": v, "unit": "Mpaths/s", "cores": 1, "kind": "oracle", "sample": desc},
            "e2e": {"value": v, "unit": "Mpaths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+REF_SPP = 1024
+
+
+def equal_time_study(N, r, M_p, base_iter, table_ms):
+    """Learned vs plain proposal on the bench workload: trains the network on
+    the renderer's connections, times a learned-proposal step, renders a
+    REF_SPP reference (table proposal, disjoint iterations) and compares image
+    MAPE at equal wall time (one table step). Untimed with respect to the
+    headline number."""
+    base = dict(M=M, M_p=M_p, max_depth=DEPTH, seed=7)
+    t0 = time.perf_counter()
+    tr = r.train_proposal(N.config(**base), N.train_desc(samples=1 << 20, rounds=3, steps=500, batch=8192, lr=3e-3,
+                                                         seed=5, iter0=(1 << 23) + base_iter))
+    train_s = time.perf_counter() - t0
+    # learned-proposal step (same workload)
+    r.clear()
+    r.render(N.config(spp=SPP, iter0=base_iter + (1 << 20), proposal=1, **base), allow_truncated=True)
+    r.clear()
+    sl = r.render(N.config(spp=SPP, iter0=base_iter + (1 << 20) + SPP, proposal=1, **base), allow_truncated=True)
+    learned_ms = sl["ms"]
+    # connection-estimate moments under both proposals (8 iterations each)
+    mt = r.connection_moments(N.config(spp=8, iter0=base_iter + (5 << 20), **base))
+    ml = r.connection_moments(N.config(spp=8, iter0=base_iter + (5 << 20), proposal=1, **base))
+    # reference
+    r.clear()
+    r.render(N.config(spp=REF_SPP, iter0=base_iter + (2 << 20), **base), allow_truncated=True)
+    ref = r.film().astype(np.float64)
+    # equal wall time: one table step (SPP iterations) vs as many learned iterations as fit
+    spp_l = max(1, int(round(SPP * table_ms / learned_ms)))
+    r.clear()
+    r.render(N.config(spp=SPP, iter0=base_iter + (3 << 20), **base), allow_truncated=True)
+    img_t = r.film().astype(np.float64)
+    r.clear()
+    r.render(N.config(spp=spp_l, iter0=base_iter + (4 << 20), proposal=1, **base), allow_truncated=True)
+    img_l = r.film().astype(np.float64)
+    r.clear()
+    return {
+        "seconds": table_ms * 1e-3,
+        "reference": "%d spp, table proposal, disjoint iterations" % REF_SPP,
+        "mape": {"table": mape(img_t, ref), "learned": mape(img_l, ref)},
+        "spp": {"table": SPP, "learned": spp_l},
+        "learned": {"value": W * H * SPP / (learned_ms * 1e-3) / 1e6, "unit": "Mpaths/s", "ms_per_step": learned_ms,
+                    "ms_mlp_per_step": sl["ms_mlp"], "train_s": train_s, "train": tr},
+        "connection_second_moment": {"table": mt["m2"], "learned": ml["m2"], "gain": mt["m2"] / ml["m2"],
+                                     "mean_table": mt["mean"], "mean_learned": ml["mean"]},
+        "_ref": ref,
+    }
 
 
 # ---------------------------------------------------------------------------
@@ -292,7 +352,14 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
-    cpu_v, cpu_desc = oracle_sample(sc, M_p)
+    study = equal_time_study(N, r, M_p, base_iter, total_ms / args.steps) if args.workload != "small" else None
+    cpu_v, cpu_desc, cpu_px = oracle_sample(sc, M_p)
+    if study is not None:
+        ref = study.pop("_ref")
+        npx = len(cpu_px)
+        study["mape"]["cpu_oracle_1spp"] = mape(cpu_px, ref[:npx])
+        study["cpu_oracle"] = {"spp": 1, "pixels": npx, "seconds_per_spp_full_image": W * H / (cpu_v * 1e6),
+                               "note": "oracle's own learned tables; MAPE over its first %d pixels" % npx}
     out = {
         "metric": METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -311,6 +378,8 @@ def run_ours(args):
         "clocks": clk.summary(),
         "gpu_launches": int(sum(s["n_launches"] for s in stats)),
     }
+    if study is not None:
+        out["equal_time"] = study
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
