@@ -289,6 +289,13 @@ def run_ours(args):
     tables = r.tables_readback()
     base_iter = rank * (1 << 24)
     cfg = N.config(M=M, M_p=M_p, max_depth=DEPTH, spp=SPP, seed=7)
+    trained = None
+    if args.proposal == "learned":
+        # the network is trained before timing, like the tables
+        trained = r.train_proposal(N.config(M=M, M_p=M_p, max_depth=DEPTH, seed=7),
+                                   N.train_desc(samples=1 << 20, rounds=3, steps=500, batch=8192, lr=3e-3, seed=5,
+                                                iter0=(1 << 23) + base_iter))
+        cfg.proposal = 1
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step(i, count=False):
@@ -323,7 +330,7 @@ def run_ours(args):
     value = paths / (total_ms * 1e-3) / 1e6
     # traversal work of one step (untimed counting run) -> algorithmic bytes
     cst = step(args.warmup + args.steps, count=True)
-    mean = {k: float(np.mean([s[k] for s in stats])) for k in ("ms_light", "ms_pool", "ms_recip", "ms_eye")}
+    mean = {k: float(np.mean([s[k] for s in stats])) for k in ("ms_light", "ms_pool", "ms_recip", "ms_mlp", "ms_eye")}
     waves = stats[-1]["n_waves"]
     eye_ms, rec_ms = mean["ms_eye"] / waves, mean["ms_recip"] / waves
     eye_bytes = (64.0 * cst["eye_nodes"] + 48.0 * cst["eye_tris"]) / waves
@@ -352,7 +359,9 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
-    study = equal_time_study(N, r, M_p, base_iter, total_ms / args.steps) if args.workload != "small" else None
+    study = None
+    if args.workload != "small" and args.proposal == "table":
+        study = equal_time_study(N, r, M_p, base_iter, total_ms / args.steps)
     cpu_v, cpu_desc, cpu_px = oracle_sample(sc, M_p)
     if study is not None:
         ref = study.pop("_ref")
@@ -369,7 +378,8 @@ def run_ours(args):
                    "tables": "learned on the device before timing (%.1f s, %d learning iterations)" % (learn_s, n_learn),
                    "stage_ms_per_step": mean, "entries_per_iteration": stats[-1]["n_entries"] / SPP,
                    "truncated_estimates_per_step": stats[-1]["n_truncated"],
-                   "estimator_nodes_per_step": stats[-1]["n_nodes"], "parallelism": "replicas" if ws > 1 else "1 GPU"},
+                   "estimator_nodes_per_step": stats[-1]["n_nodes"], "parallelism": "replicas" if ws > 1 else "1 GPU",
+                   "proposal": args.proposal},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom, sha),
                      "algorithmic_bytes_per_launch": b, "launch_ms": ms, "src_sha": sha},
@@ -380,6 +390,8 @@ def run_ours(args):
     }
     if study is not None:
         out["equal_time"] = study
+    if trained is not None:
+        out["config"]["proposal_training"] = trained
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
@@ -392,6 +404,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--proposal", default="table", choices=["table", "learned"],
+                    help="light-subspace proposal of the timed steps (learned: trained before timing)")
     ap.add_argument("--workload", default="projector", choices=["projector", "small"],
                     help="small: the same scene and pipeline at 64x64, 4 spp, M=2000 (profiling captures)")
     args = ap.parse_args()

@@ -151,7 +151,7 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
         P.pilot_max = hi;
     }
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
-    P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
     P.smp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
     return P;
 }

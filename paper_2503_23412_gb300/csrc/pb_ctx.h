@@ -19,9 +19,11 @@ struct MlpState {
     uint16_t *emb = nullptr;            // bf16 E[KT][4]
     int *err = nullptr;                 // set by the tensor-core kernel when a wait times out
     uint16_t *rows = nullptr;
-    int32_t *rowT = nullptr, *sel = nullptr;
+    int32_t *rowT = nullptr, *rowPos = nullptr, *sel = nullptr;
     float *selq = nullptr;
-    size_t cap_rows16 = 0, cap_rowT = 0, cap_sel = 0, cap_selq = 0;
+    int4 *hits = nullptr;
+    unsigned int *rcount = nullptr;
+    size_t cap_rows16 = 0, cap_rowT = 0, cap_rowPos = 0, cap_sel = 0, cap_selq = 0, cap_hits = 0;
     float *s_raw = nullptr, *s_w = nullptr;
     int32_t *s_T = nullptr, *s_S = nullptr;
     unsigned int *s_count = nullptr;

@@ -21,8 +21,12 @@
 // connection and are finished at connection time. The proxy term enters PT
 // and NEE weights of paths with the proxy shape; connections (s >= 2) can
 // never produce such paths (both joined vertices must be non-specular).
+#include <cooperative_groups.h>
+
 #include "pb_kernels.h"
 #include "pb_mlp.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -47,6 +51,17 @@ __device__ __forceinline__ int select_cdf(const float *cdf, int K, float u) {
 }
 
 __device__ __forceinline__ float lum(float3 c) { return (c.x + c.y + c.z) * (1.0f / 3.0f); }
+
+// hit of eye vertex a stored by the feature pass
+__device__ __forceinline__ Hit stored_hit(const KParams &P, int slot, int a, int pix) {
+    int4 v = P.mlp.hits[((size_t)slot * P.max_depth + (a - 1)) * P.npix + pix];
+    Hit h;
+    h.tri = v.x;
+    h.t = __int_as_float(v.y);
+    h.b1 = __int_as_float(v.z);
+    h.b2 = __int_as_float(v.w);
+    return h;
+}
 
 __device__ __forceinline__ float mis_cell(const DTables &T, int u, int Sp, int C) {
     return T.mis[((u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
@@ -82,7 +97,8 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
     int pstate = 0, f_idx = 0, Sp_f1 = 0;
     float rev_f1 = 1.0f;
     unsigned long long n_conn = 0, n_proxy = 0, n_proxy_ok = 0;
-    Hit h = closest_hit<COUNT>(S, S.cpos, d, -1, &tc);
+    const bool replay = P.mlp.hits != nullptr;   // eye rays were traced by the feature pass
+    Hit h = replay ? stored_hit(P, slot, 1, pix) : closest_hit<COUNT>(S, S.cpos, d, -1, &tc);
     int a = 1;
     while (h.tri >= 0) {
         Vtx z = vertex_at(S, h.tri, h.b1, h.b2);
@@ -434,7 +450,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
         zp.nonS = nonS;
         zp.rev = rev_a;
         d = wl;
-        h = closest_hit<COUNT>(S, z.p, d, z.tri, &tc);
+        h = replay ? stored_hit(P, slot, a + 1, pix) : closest_hit<COUNT>(S, z.p, d, z.tri, &tc);
         ++a;
     }
     size_t o = (size_t)slot * P.npix + pix;
@@ -452,14 +468,14 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
 
 // Feature pass of the learned proposal: the same camera sub-paths as k_eye
 // (the walk uses only the BSDF dimensions 0-2, never a connection's
-// choice), writing the network's input row and eye subspace at every vertex
-// where k_eye makes a subspace connection. Rows of other vertices keep
-// rowT = -1.
+// choice). Stores every vertex's hit for k_eye to replay, and appends the
+// network's input row, eye subspace and dense index of every vertex where
+// k_eye makes a subspace connection (row order is arbitrary; each row's
+// result depends on its own content only).
 __global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base) {
     int pix = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = blockIdx.y;
     if (pix >= P.npix) return;
-    if (!P.conn || B.npool[slot] <= 0) return;
     uint32_t it = iter_base + (uint32_t)slot;
     int px = pix % S.W, py = pix / S.W;
     Rng r0;
@@ -469,18 +485,28 @@ __global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P
     float3 d = normalize(S.cfwd + (S.cright * (sx * S.tanh_ * S.aspect) + S.cup * (sy * S.tanh_)));
     Hit h = closest_hit<false>(S, S.cpos, d, -1, nullptr);
     int a = 1;
-    while (h.tri >= 0) {
+    bool conn = P.conn && B.npool[slot] > 0;
+    while (true) {
+        P.mlp.hits[((size_t)slot * P.max_depth + (a - 1)) * P.npix + pix] =
+            make_int4(h.tri, __float_as_int(h.t), __float_as_int(h.b1), __float_as_int(h.b2));
+        if (h.tri < 0) break;
         Vtx z = vertex_at(S, h.tri, h.b1, h.b2);
         const DMat &mz = S.mats[z.mat];
         float3 we = -d;
         if (absorbing(S, z, we)) break;
-        if (!mz.specular && a + 2 <= P.max_depth) {
+        if (conn && !mz.specular && a + 2 <= P.max_depth) {
             int Tl = label_dir(S, z, we, T.KT, T.cT);
-            size_t row = ((size_t)slot * P.mlp.A + (a - 1)) * P.npix + pix;
-            float raw[MLP_NRAW];
-            mlp_raw(S, z, we, raw);
-            mlp_pack_row(raw, Tl, P.mlp.emb, P.mlp.rows + (size_t)MLP_NX * row);
-            P.mlp.rowT[row] = Tl;
+            cg::coalesced_group g = cg::coalesced_threads();
+            unsigned int base = 0;
+            if (g.thread_rank() == 0) base = atomicAdd(P.mlp.count, (unsigned int)g.size());
+            unsigned int idx = g.shfl(base, 0) + g.thread_rank();
+            if (idx < (unsigned int)P.mlp.cap) {
+                float raw[MLP_NRAW];
+                mlp_raw(S, z, we, raw);
+                mlp_pack_row(raw, Tl, P.mlp.emb, P.mlp.rows + (size_t)MLP_NX * idx);
+                P.mlp.rowT[idx] = Tl;
+                P.mlp.rowPos[idx] = (int32_t)(((size_t)slot * P.mlp.A + (a - 1)) * P.npix + pix);
+            }
         }
         if (a + 1 > P.max_depth) break;
         Rng R;

@@ -14,14 +14,21 @@ struct LearnAcc {
 };
 
 // Render parameters as the kernels see them.
-// Learned light-subspace proposal: per (slot, eye vertex a, pixel) input
-// rows of the network and the subspace it selected. Row index
-// ((slot * A) + a - 1) * npix + pix for eye vertices a = 1..A.
+// Learned light-subspace proposal. The feature pass traces the camera
+// sub-paths once, stores every eye vertex's hit (replayed by the eye pass
+// instead of tracing again) and appends one network input row per vertex
+// that makes a subspace connection. Dense index of a connecting vertex:
+// ((slot * A) + a - 1) * npix + pix for a = 1..A; of a hit:
+// ((slot * max_depth) + a - 1) * npix + pix for a = 1..max_depth.
 struct MlpRows {
-    uint16_t *rows;         // bf16[16] network input per row
-    int32_t *rowT;          // eye subspace T of the row, -1: no connection there
-    const int32_t *sel;     // selected light subspace (-1: none)
-    const float *selq;      // its proposal probability Q(S | x)
+    uint16_t *rows;         // compact: bf16[16] network input per row
+    int32_t *rowT;          // compact: eye subspace T of the row
+    int32_t *rowPos;        // compact: dense index of the row's vertex
+    unsigned int *count;    // rows appended
+    int cap;                // rows the compact arrays hold
+    int4 *hits;             // dense: the eye vertex's hit (tri, t, b1, b2), tri = -1: the path left the scene
+    const int32_t *sel;     // dense: selected light subspace (-1: none)
+    const float *selq;      // dense: its proposal probability Q(S | x)
     const uint16_t *emb;    // bf16[KT][4] embedding of T
     int A;                  // eye vertices with a row per pixel (max_depth - 2)
 };

@@ -153,7 +153,9 @@ struct SelArgs {
     int K, Kpad;
     const uint16_t *rows;
     const int32_t *rowT;
-    long long nrows;
+    const int32_t *rowPos;       // dense index of each row (selection mode)
+    const unsigned int *count;   // selection mode: rows to process (read on the device)
+    long long nrows;             // logits mode: rows to process; selection mode: capacity
     // selection mode
     int A, npix, slots, KT;
     uint32_t seed, iter_base;
@@ -178,12 +180,14 @@ __device__ __forceinline__ int select_cdf_row(const float *cdf, int K, float u) 
     return lo;
 }
 
-constexpr int SEL_THREADS = 128;
+// 8 warps: warp w reads TMEM lanes 32 (w % 4) .. (the rows of its quarter)
+// and handles half h = w / 4 of each accumulator's columns
+constexpr int SEL_THREADS = 256;
 constexpr int MASK_WORDS = MLP_KMAX / 32;
 constexpr int MAX_SLOTS = 64;
 
 struct SelSmem {
-    uint32_t a1, a23, bias, mask, bar, tslot, abort_, bytes;
+    uint32_t a1, a23, bias, mask, part, bar, tslot, abort_, bytes;
 };
 __host__ __device__ inline SelSmem sel_smem(int Kpad) {
     SelSmem s;
@@ -196,6 +200,8 @@ __host__ __device__ inline SelSmem sel_smem(int Kpad) {
     o += (MLP_H + MLP_KMAX) * 4;
     s.mask = o;
     o += MAX_SLOTS * MASK_WORDS * 4;
+    s.part = o;                     // per half and row: max, sum, last occupied S, its logit, pick, its weight
+    o += 2 * TILE_M * 6 * 4;
     s.bar = o;
     o += 8;
     s.tslot = o;
@@ -206,29 +212,26 @@ __host__ __device__ inline SelSmem sel_smem(int Kpad) {
     return s;
 }
 
-// epilogue of layers 1 and 2: this thread's row of the accumulator (columns
-// col0..col0+63) plus bias, ReLU, bf16, into the next layer's A operand
-__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, int col0, const float *bias, uint8_t *a23,
+// hidden-layer epilogue: 32 columns (col0 + 32 h) of this thread's row plus
+// bias, ReLU, bf16 into the next layer's A operand
+__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, int col0, int h, const float *bias, uint8_t *a23,
                                                 int r) {
     float v[32];
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        tmem_ld32(tmem_row + (uint32_t)(col0 + 32 * h), v);
+    tmem_ld32(tmem_row + (uint32_t)(col0 + 32 * h), v);
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            uint4 q;
-            float x[8];
+    for (int g = 0; g < 4; ++g) {
+        uint4 q;
+        float x[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                float t = v[8 * g + e] + (bias ? bias[32 * h + 8 * g + e] : 0.0f);
-                x[e] = t > 0.0f ? t : 0.0f;
-            }
-            q.x = bf16_pair(x[0], x[1]);
-            q.y = bf16_pair(x[2], x[3]);
-            q.z = bf16_pair(x[4], x[5]);
-            q.w = bf16_pair(x[6], x[7]);
-            *reinterpret_cast<uint4 *>(a23 + canon_off(r, 32 * h + 8 * g, MLP_H)) = q;
+        for (int e = 0; e < 8; ++e) {
+            float t = v[8 * g + e] + (bias ? bias[32 * h + 8 * g + e] : 0.0f);
+            x[e] = t > 0.0f ? t : 0.0f;
         }
+        q.x = bf16_pair(x[0], x[1]);
+        q.y = bf16_pair(x[2], x[3]);
+        q.z = bf16_pair(x[4], x[5]);
+        q.w = bf16_pair(x[6], x[7]);
+        *reinterpret_cast<uint4 *>(a23 + canon_off(r, 32 * h + 8 * g, MLP_H)) = q;
     }
 }
 
@@ -236,11 +239,14 @@ template <bool LOGITS>
 __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = 32 * quarter + lane;   // this thread's row within the tile
     const SelSmem SL = sel_smem(a.Kpad);
     const ImgLayout IL = img_layout(a.Kpad);
     uint8_t *a1 = sm + SL.a1, *a23 = sm + SL.a23;
     float *sbias = reinterpret_cast<float *>(sm + SL.bias);
     uint32_t *smask = reinterpret_cast<uint32_t *>(sm + SL.mask);
+    float *part = reinterpret_cast<float *>(sm + SL.part);   // [half][field][row]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + SL.tslot);
     volatile int *abort_ = reinterpret_cast<int *>(sm + SL.abort_);
     const uint32_t bar = smem_u32(sm + SL.bar);
@@ -249,11 +255,11 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
     for (uint32_t o = 16 * tid; o < IL.bytes; o += 16 * SEL_THREADS)
         *reinterpret_cast<uint4 *>(sm + o) = *reinterpret_cast<const uint4 *>(a.img + o);
     for (int i = tid; i < MLP_H + a.Kpad; i += SEL_THREADS) sbias[i] = a.bias[i];
-    // occupied light subspaces of every slot
+    const int nchunk = (a.Kpad + 31) / 32;
     if (!LOGITS) {
-        int nw = a.Kpad / 32 + ((a.Kpad & 31) ? 1 : 0);
-        for (int i = tid; i < a.slots * nw; i += SEL_THREADS) {
-            int s = i / nw, wd = i % nw;
+        // occupied light subspaces of every slot
+        for (int i = tid; i < a.slots * nchunk; i += SEL_THREADS) {
+            int s = i / nchunk, wd = i % nchunk;
             uint32_t m = 0;
             const int32_t *st = a.bstart + (size_t)s * (a.K + 1);
             for (int b = 0; b < 32; ++b) {
@@ -279,26 +285,29 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tslot;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);   // this warp's TMEM lanes
+    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's TMEM lanes
     const uint32_t d1 = tmem, d2 = tmem + 64, d3 = tmem + 128;
     const uint32_t sa1 = smem_u32(a1), sa23 = smem_u32(a23);
     const uint32_t sw1 = smem_u32(sm + IL.w1), sw2 = smem_u32(sm + IL.w2), sw3 = smem_u32(sm + IL.w3);
     const uint64_t TIMEOUT = 1000000000ull;   // 1 s per wait
     uint32_t phase = 0;
-    const long long ntiles = (a.nrows + TILE_M - 1) / TILE_M;
+    long long nrows = a.nrows;
+    if (!LOGITS) nrows = min((long long)*a.count, a.nrows);
+    const long long ntiles = (nrows + TILE_M - 1) / TILE_M;
     bool pending = false;   // an MMA group was committed and not yet waited for
+    // column chunks of this half: [c0, c1)
+    const int cmid = (nchunk + 1) / 2;
+    const int c0 = half ? cmid : 0, c1 = half ? nchunk : cmid;
 
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long row = tile * TILE_M + tid;
-        // A tile of layer 1: one 32-byte input row per thread
-        uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
-        if (row < a.nrows) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(a.rows + (size_t)MLP_NX * row);
-            q0 = src[0];
-            q1 = src[1];
+        // A tile of layer 1: each of the 128 rows is 32 bytes, one 16-byte half per thread
+        {
+            const int rr = tid >> 1, hh = tid & 1;
+            const long long row = tile * TILE_M + rr;
+            uint4 q = make_uint4(0, 0, 0, 0);
+            if (row < nrows) q = reinterpret_cast<const uint4 *>(a.rows + (size_t)MLP_NX * row)[hh];
+            *reinterpret_cast<uint4 *>(a1 + canon_off(rr, 8 * hh, MLP_NX)) = q;
         }
-        *reinterpret_cast<uint4 *>(a1 + canon_off(tid, 0, MLP_NX)) = q0;
-        *reinterpret_cast<uint4 *>(a1 + canon_off(tid, 8, MLP_NX)) = q1;
         async_smem_fence();
         __syncthreads();
         // layer 1: D1 = A1 (128 x 16) W1^T
@@ -317,7 +326,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
         __syncthreads();
         if (*abort_) break;
         tc_after();
-        hidden_epilogue(trow, 0, nullptr, a23, tid);
+        hidden_epilogue(trow, 0, half, nullptr, a23, r);
         async_smem_fence();
         tc_before();
         __syncthreads();
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
         __syncthreads();
         if (*abort_) break;
         tc_after();
-        hidden_epilogue(trow, 64, sbias, a23, tid);
+        hidden_epilogue(trow, 64, half, sbias, a23, r);
         async_smem_fence();
         tc_before();
         __syncthreads();
@@ -366,71 +375,98 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
         if (*abort_) break;
         tc_after();
         const float *b3 = sbias + MLP_H;
-        const int nchunk = (a.Kpad + 31) / 32;
+        const long long row = tile * TILE_M + r;
         float v[32];
         if (LOGITS) {
-            for (int c = 0; c < nchunk; ++c) {
-                tmem_ld32(d3 + ((uint32_t)(32 * warp) << 16) + 32 * c, v);
-                if (row < a.nrows)
+            for (int c = c0; c < c1; ++c) {
+                tmem_ld32(trow + 128 + 32 * c, v);
+                if (row < nrows)
+#pragma unroll
                     for (int k = 0; k < 32; ++k) {
                         int S = 32 * c + k;
                         if (S < a.K) a.logits[(size_t)row * a.K + S] = v[k] + b3[S];
                     }
             }
         } else {
-            int T = row < a.nrows ? a.rowT[row] : -1;
-            long long per_slot = (long long)a.A * a.npix;
-            int slot = row < a.nrows ? (int)(row / per_slot) : 0;
-            long long rem = row - (long long)slot * per_slot;
-            int av = (int)(rem / a.npix) + 1, pix = (int)(rem % a.npix);
+            const bool inrow = row < nrows;
+            const int T = inrow ? a.rowT[row] : -1;
+            const int pos = inrow ? a.rowPos[row] : 0;
+            const long long per_slot = (long long)a.A * a.npix;
+            const int slot = (int)(pos / per_slot);
+            const long long rem = pos - (long long)slot * per_slot;
+            const int av = (int)(rem / a.npix) + 1, pix = (int)(rem % a.npix);
             const uint32_t *mk = smask + slot * MASK_WORDS;
-            // pass 1: max over occupied subspaces; pass 2: normaliser
-            float m = -INFINITY;
-            for (int c = 0; c < nchunk; ++c) {
-                tmem_ld32(d3 + ((uint32_t)(32 * warp) << 16) + 32 * c, v);
-                uint32_t bits = mk[c];
+            // pass A over this half: online max and normaliser, last occupied subspace
+            float m = -INFINITY, Z = 0.0f, vlast = 0.0f;
+            int last = -1;
+            for (int c = c0; c < c1; ++c) {
+                tmem_ld32(trow + 128 + 32 * c, v);
+                const uint32_t bits = mk[c];
+                float cm = -INFINITY;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    v[k] += b3[32 * c + k];
+                    if ((bits >> k) & 1u) cm = fmaxf(cm, v[k]);
+                }
+                if (cm == -INFINITY) continue;
+                float nm = fmaxf(m, cm);
+                float s = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) s += ((bits >> k) & 1u) ? __expf(v[k] - nm) : 0.0f;
+                Z = Z * __expf(m - nm) + s;
+                m = nm;
+                const int hb = 31 - __clz(bits);
+#pragma unroll
                 for (int k = 0; k < 32; ++k)
-                    if ((bits >> k) & 1u) m = fmaxf(m, v[k] + b3[32 * c + k]);
+                    if (k == hb) vlast = v[k];
+                last = 32 * c + hb;
             }
-            float Z = 0.0f;
-            for (int c = 0; c < nchunk; ++c) {
-                tmem_ld32(d3 + ((uint32_t)(32 * warp) << 16) + 32 * c, v);
-                uint32_t bits = mk[c];
-                for (int k = 0; k < 32; ++k)
-                    if ((bits >> k) & 1u) Z += expf(v[k] + b3[32 * c + k] - m);
-            }
+            float *P0 = part + (size_t)(half * 6) * TILE_M;
+            P0[0 * TILE_M + r] = m;
+            P0[1 * TILE_M + r] = Z;
+            P0[2 * TILE_M + r] = __int_as_float(last);
+            P0[3 * TILE_M + r] = vlast;
+            __syncthreads();
+            const float *Q0 = part, *Q1 = part + 6 * TILE_M;
+            const float m0 = Q0[r], m1 = Q1[r];
+            const float mg = fmaxf(m0, m1);
+            const float Zh0 = m0 == -INFINITY ? 0.0f : Q0[TILE_M + r] * __expf(m0 - mg);
+            const float Zh1 = m1 == -INFINITY ? 0.0f : Q1[TILE_M + r] * __expf(m1 - mg);
+            const float Zg = Zh0 + Zh1;
+            const bool valid = T >= 0 && mg > -INFINITY;
             // one uniform picks the mixture component and the subspace
-            float u = 0.0f;
             int gpick = -1;
             float target = 0.0f;
-            bool valid = T >= 0 && m > -INFINITY;
             if (valid) {
                 Rng R;
                 R.init(a.seed, K_CAMERA, a.iter_base + (uint32_t)slot, (uint32_t)pix, (uint32_t)av);
-                u = R.u(6);
-                if (u < MLP_EPS) {
-                    const float *cdf = a.cdfC + ((size_t)slot * a.KT + T) * a.K;
-                    gpick = select_cdf_row(cdf, a.K, u / MLP_EPS);
-                } else {
-                    target = (u - MLP_EPS) / (1.0f - MLP_EPS) * Z;
-                }
+                const float u = R.u(6);
+                if (u < MLP_EPS) gpick = select_cdf_row(a.cdfC + ((size_t)slot * a.KT + T) * a.K, a.K, u / MLP_EPS);
+                else target = (u - MLP_EPS) / (1.0f - MLP_EPS) * Zg;
             }
-            // pass 3: cumulative search (softmax branch) or the chosen subspace's weight
-            int pick = -1, last = -1;
-            float e_pick = 0.0f, e_last = 0.0f, cum = 0.0f;
-            for (int c = 0; c < nchunk; ++c) {
-                tmem_ld32(d3 + ((uint32_t)(32 * warp) << 16) + 32 * c, v);
-                uint32_t bits = mk[c];
-                if (!valid) continue;
+            // pass B over this half: the cumulative search (softmax branch, the
+            // half that holds the target) or the drawn subspace's weight
+            int pick = -1;
+            float e_pick = 0.0f;
+            const bool mine = valid && (gpick >= 0 ? (gpick >= 32 * c0 && gpick < 32 * c1)
+                                                   : (half == 0 ? target < Zh0 : target >= Zh0));
+            float cum = half ? Zh0 : 0.0f;
+            for (int c = c0; c < c1; ++c) {
+                if (__all_sync(0xffffffffu, !mine || pick >= 0)) break;
+                tmem_ld32(trow + 128 + 32 * c, v);
+                if (!mine || pick >= 0) continue;
+                const uint32_t bits = mk[c];
+#pragma unroll
                 for (int k = 0; k < 32; ++k) {
-                    if (!((bits >> k) & 1u)) continue;
-                    int S = 32 * c + k;
-                    float e = expf(v[k] + b3[S] - m);
-                    last = S;
-                    e_last = e;
+                    const int S = 32 * c + k;
+                    const bool occ = (bits >> k) & 1u;
+                    const float e = occ ? __expf(v[k] + b3[S] - mg) : 0.0f;
                     if (gpick >= 0) {
-                        if (S == gpick) e_pick = e;
-                    } else if (pick < 0) {
+                        if (pick < 0 && S == gpick) {
+                            pick = S;
+                            e_pick = e;
+                        }
+                    } else if (pick < 0 && occ) {
                         cum += e;
                         if (target < cum) {
                             pick = S;
@@ -439,18 +475,30 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
                     }
                 }
             }
-            if (valid) {
-                if (gpick >= 0) pick = gpick;
-                if (pick < 0) {
-                    pick = last;
-                    e_pick = e_last;
+            P0[4 * TILE_M + r] = __int_as_float(pick);
+            P0[5 * TILE_M + r] = e_pick;
+            __syncthreads();
+            if (half == 0 && inrow) {
+                int pk = __float_as_int(Q0[4 * TILE_M + r]);
+                float ep = Q0[5 * TILE_M + r];
+                if (pk < 0) {
+                    pk = __float_as_int(Q1[4 * TILE_M + r]);
+                    ep = Q1[5 * TILE_M + r];
                 }
-                float gam = a.gC[(size_t)T * a.K + pick] / a.ZC[(size_t)slot * a.KT + T];
-                a.sel[row] = pick;
-                a.selq[row] = (1.0f - MLP_EPS) * e_pick / Z + MLP_EPS * gam;
-            } else if (row < a.nrows) {
-                a.sel[row] = -1;
-                a.selq[row] = 0.0f;
+                if (valid && pk < 0) {
+                    // rounding left the target past the last occupied subspace
+                    int l1 = __float_as_int(Q1[2 * TILE_M + r]);
+                    pk = l1 >= 0 ? l1 : __float_as_int(Q0[2 * TILE_M + r]);
+                    ep = __expf((l1 >= 0 ? Q1[3 * TILE_M + r] : Q0[3 * TILE_M + r]) - mg);
+                }
+                if (valid) {
+                    const float gam = a.gC[(size_t)T * a.K + pk] / a.ZC[(size_t)slot * a.KT + T];
+                    a.sel[pos] = pk;
+                    a.selq[pos] = (1.0f - MLP_EPS) * ep / Zg + MLP_EPS * gam;
+                } else {
+                    a.sel[pos] = -1;
+                    a.selq[pos] = 0.0f;
+                }
             }
         }
         tc_before();
@@ -464,7 +512,6 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
     tc_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
-    (void)lane;
 }
 
 // ---- training (fp32, CUDA cores) -------------------------------------------
@@ -692,7 +739,8 @@ static pb_status mlp_shape(pb_ctx *ctx) {
 
 void mlp_free(pb_ctx *ctx) {
     MlpState &M = ctx->mlp;
-    void *ps[] = {M.w, M.g, M.m1, M.m2, M.img, M.bias, M.emb, M.err, M.rows, M.rowT, M.sel, M.selq, M.s_raw,
+    void *ps[] = {M.w, M.g, M.m1, M.m2, M.img, M.bias, M.emb, M.err, M.rows, M.rowT, M.rowPos, M.hits, M.rcount,
+                  M.sel, M.selq, M.s_raw,
                   M.s_T, M.s_S, M.s_w, M.s_count, M.b_X, M.b_T, M.b_S, M.b_a, M.b_H1, M.b_H2, M.b_DH1, M.b_DH2,
                   M.b_DZ, M.b_DE, M.b_loss};
     for (void *p : ps)
@@ -709,7 +757,7 @@ static pb_status mlp_pack(pb_ctx *ctx) {
     return PB_OK;
 }
 
-static pb_status run_select(pb_ctx *ctx, SelArgs &a) {
+static pb_status run_select(pb_ctx *ctx, SelArgs &a, bool device_count) {
     int smem = (int)sel_smem(a.Kpad).bytes;
     // one CTA per SM: the kernel holds all 512 TMEM columns
     int smem_req = smem < 120 * 1024 ? 120 * 1024 : smem;
@@ -720,7 +768,8 @@ static pb_status run_select(pb_ctx *ctx, SelArgs &a) {
         attr_set[a.logits ? 1 : 0] = true;
     }
     long long ntiles = (a.nrows + TILE_M - 1) / TILE_M;
-    int grid = (int)std::min<long long>(ntiles, (long long)ctx->num_sms);
+    // with the row count on the device every SM gets a CTA; idle ones exit at once
+    int grid = device_count ? ctx->num_sms : (int)std::min<long long>(ntiles, (long long)ctx->num_sms);
     if (grid < 1) return PB_OK;
     if (a.logits) k_mlp_select<true><<<grid, SEL_THREADS, smem_req, ctx->stream>>>(a);
     else k_mlp_select<false><<<grid, SEL_THREADS, smem_req, ctx->stream>>>(a);
@@ -740,14 +789,18 @@ static SelArgs sel_base(pb_ctx *ctx) {
     return a;
 }
 
-// rows / selections of `slots` iterations of the eye pass
-pb_status mlp_ensure_rows(pb_ctx *ctx, int slots, int A) {
+// rows, hits and selections of `slots` iterations of the eye pass
+pb_status mlp_ensure_rows(pb_ctx *ctx, int slots, int A, int depth) {
     MlpState &M = ctx->mlp;
-    size_t n = (size_t)slots * A * ctx->S.W * ctx->S.H;
+    size_t npix = (size_t)ctx->S.W * ctx->S.H;
+    size_t n = (size_t)slots * A * npix;
     CK(grow(&M.rows, M.cap_rows16, MLP_NX * n));
     CK(grow(&M.rowT, M.cap_rowT, n));
+    CK(grow(&M.rowPos, M.cap_rowPos, n));
     CK(grow(&M.sel, M.cap_sel, n));
     CK(grow(&M.selq, M.cap_selq, n));
+    CK(grow(&M.hits, M.cap_hits, (size_t)slots * depth * npix));
+    if (!M.rcount) CK(cudaMalloc(&M.rcount, sizeof(unsigned int)));
     return PB_OK;
 }
 
@@ -758,16 +811,18 @@ pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base) {
     if (slots > MAX_SLOTS) return pb_fail(ctx, PB_ERR_ARG, "mlp: too many iterations in flight");
     int A = P.max_depth - 2;
     if (A < 1) return PB_OK;
-    pb_status s = mlp_ensure_rows(ctx, slots, A);
+    pb_status s = mlp_ensure_rows(ctx, slots, A, P.max_depth);
     if (s != PB_OK) return s;
     size_t n = (size_t)slots * A * P.npix;
-    CK(cudaMemsetAsync(M.rowT, 0xFF, 4 * n, ctx->stream));
-    P.mlp = MlpRows{M.rows, M.rowT, nullptr, nullptr, M.emb, A};
+    CK(cudaMemsetAsync(M.rcount, 0, sizeof(unsigned int), ctx->stream));
+    P.mlp = MlpRows{M.rows, M.rowT, M.rowPos, M.rcount, (int)n, M.hits, nullptr, nullptr, M.emb, A};
     launch_eye_feat(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->stream);
     CK(cudaGetLastError());
     SelArgs a = sel_base(ctx);
     a.rows = M.rows;
     a.rowT = M.rowT;
+    a.rowPos = M.rowPos;
+    a.count = M.rcount;
     a.nrows = (long long)n;
     a.A = A;
     a.npix = P.npix;
@@ -780,7 +835,7 @@ pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base) {
     a.cdfC = ctx->B.cdfC;
     a.sel = M.sel;
     a.selq = M.selq;
-    s = run_select(ctx, a);
+    s = run_select(ctx, a, true);
     if (s != PB_OK) return s;
     P.mlp.rows = nullptr;
     P.mlp.sel = M.sel;
@@ -966,7 +1021,7 @@ pb_status pb_mlp_logits(pb_ctx *ctx, int n, const float *raw, const int32_t *T, 
     a.rows = drows;
     a.nrows = n;
     a.logits = dz;
-    pb_status s = run_select(ctx, a);
+    pb_status s = run_select(ctx, a, false);
     if (s != PB_OK) return s;
     CK(cudaMemcpyAsync(z, dz, 4 * (size_t)n * M.K, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaFreeAsync(draw, ctx->stream));
