@@ -115,6 +115,12 @@ typedef struct {
      * Q(S | x) = 0.9 softmax(MLP(x))_S + 0.1 Gamma[T, S] / Z_T over occupied
      * subspaces (needs a network: pb_mlp_upload or pb_train_proposal). */
     int proposal;
+    /* 1: capture the render's waves as a CUDA graph the first time this
+     * configuration is seen on the context, then replay it (iter0 becomes a
+     * device scalar set before each replay). Results are identical to the
+     * eager path. The cache is dropped when the scene, the tables or the
+     * buffers it points to change. */
+    int graph;
 } pb_config;
 
 typedef struct {
@@ -130,6 +136,7 @@ typedef struct {
     /* traversal work when count_traversal = 1: eye kernel and estimator kernel */
     int64_t eye_nodes, eye_tris, eye_rays, rec_nodes, rec_tris, rec_rays;
     double ms_mlp;             /* device time of the proposal's feature pass and network (proposal = 1) */
+    double batch_ms;           /* pb_render_batch: device time of the whole batch (first entry only) */
 } pb_stats;
 
 pb_status pb_create(pb_ctx **out, int device, void *cuda_stream /* NULL: own stream */);
@@ -139,6 +146,29 @@ const char *pb_last_error(const pb_ctx *ctx);
 /* Builds the BVH on the host (binned SAH) and uploads scene and BVH. */
 pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *scene);
 pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *tables);
+
+/* Renders n scenes (one context each, same device, each context at most
+ * once) with their own configurations as ONE graph launch: each scene's
+ * render graph (captured as with cfg.graph = 1) becomes a child of a parent
+ * graph, so the scenes run concurrently and fill the GPU however uneven
+ * their sizes. Each film receives exactly what pb_render would add;
+ * stats[i] (may be NULL) is scene i's, stats[0].batch_ms the whole batch's.
+ * Errors are reported on ctxs[0]. Returns PB_ERR_TRUNCATED if any scene's
+ * estimator hit its cap. */
+pb_status pb_render_batch(pb_ctx *const *ctxs, const pb_config *cfgs, int n, pb_stats *stats);
+
+/* Autotuner: times trial renders of trial_iters iterations (0: 32; never
+ * added to the film) over iterations in flight {4, 8, 16, 32} x estimator
+ * hand-off {256, 512, 1024} and writes cfg with the fastest pair into
+ * *best. Results are cached per size bucket (log2 of the triangle and
+ * pixel counts, depth, M, M_p, repeats, proposal, proxy) for the process;
+ * *from_cache (may be NULL) tells whether the cache answered. Neither
+ * parameter changes an image beyond the estimator's summation order. */
+pb_status pb_autotune(pb_ctx *ctx, const pb_config *cfg, int trial_iters, pb_config *best, int *from_cache);
+/* the cache as text lines "bucket batch handoff ms_per_iteration" */
+pb_status pb_autotune_cache_save(const char *path);
+pb_status pb_autotune_cache_load(const char *path);
+void pb_autotune_cache_clear(void);
 
 /* Table learning (Sec. 5.4-5.5): n_iter learning iterations, numbered from
  * iter0 and never added to the film, build on the device

@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -62,6 +64,7 @@ pb_status ensure_pool(pb_ctx *ctx, int slots, int ML, int repeats, int npix) {
         return PB_OK;
     }
     CK(cudaStreamSynchronize(ctx->stream));
+    free_graphs(ctx);   // captured renders point into the old buffers
     free_all(ctx->pool_mem);
     Pool &B = ctx->B;
     B = Pool{};
@@ -153,6 +156,7 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
     P.smp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    P.iter_dev = nullptr;
     return P;
 }
 
@@ -303,8 +307,10 @@ void pb_destroy(pb_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_all(ctx->scene_mem);
     free_all(ctx->table_mem);
+    free_graphs(ctx);
     free_all(ctx->pool_mem);
     mlp_free(ctx);
+    if (ctx->d_iter0) cudaFree(ctx->d_iter0);
     if (ctx->film) cudaFree(ctx->film);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -327,6 +333,7 @@ pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *d) {
     if (d->tex_w > 0 && (!d->tex || d->tex_h <= 0)) return fail(ctx, PB_ERR_ARG, "scene: texture size without data");
     CK(cudaSetDevice(ctx->device));
     CK(cudaStreamSynchronize(ctx->stream));
+    free_graphs(ctx);   // captured renders point into the buffers replaced here
     free_all(ctx->scene_mem);
     free_all(ctx->pool_mem);
     ctx->cap_slots = ctx->cap_ML = 0;
@@ -509,6 +516,7 @@ pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *t) {
     for (int i = 0; i < ncell; ++i)
         if (!(t->B_tab[i] > 0.0f)) return fail(ctx, PB_ERR_ARG, "tables: B must be positive");
     CK(cudaStreamSynchronize(ctx->stream));
+    free_graphs(ctx);   // captured renders point into the buffers replaced here
     free_all(ctx->table_mem);
     DTables T{};
     T.KT = t->KT; T.KS = t->KS; T.KSp = t->KSp; T.KC = t->KC;
@@ -559,58 +567,91 @@ pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t
 
 extern "C" {
 
-pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
-    if (!ctx) return PB_ERR_ARG;
+}  // extern "C"
+
+// ---- render: prepare, enqueue (eager or captured), finish ---------------------
+constexpr int NEV = 6;   // per wave: light | pool | estimator | proposal | eye | end
+
+static int render_slots(const pb_config *cfg, const KParams &P) {
+    int slots = cfg->batch > 0 ? cfg->batch : std::max(1, std::min(32, (1 << 20) / std::max(1, P.npix)));
+    return std::max(1, std::min(slots, std::max(1, cfg->spp)));
+}
+
+static pb_status prepare_render(pb_ctx *ctx, const pb_config *cfg, KParams &P, int &slots) {
     pb_status s = check_cfg(ctx, cfg);
     if (s != PB_OK) return s;
     CK(cudaSetDevice(ctx->device));
-    KParams P = kparams(ctx, cfg);
-    int slots = cfg->batch > 0 ? cfg->batch : std::max(1, std::min(32, (1 << 20) / std::max(1, P.npix)));
-    slots = std::max(1, std::min(slots, std::max(1, cfg->spp)));
+    P = kparams(ctx, cfg);
+    slots = render_slots(cfg, P);
     s = ensure_pool(ctx, slots, P.M * P.L, P.repeats, P.npix);
     if (s != PB_OK) return s;
-    CK(cudaMemsetAsync(ctx->B.counters, 0, sizeof(unsigned long long) * CNT_N, ctx->stream));
-    int waves = (cfg->spp + slots - 1) / slots;
-    constexpr int NEV = 6;
-    std::vector<cudaEvent_t> ev(NEV * (size_t)std::max(waves, 0));
-    for (auto &e : ev) CK(cudaEventCreate(&e));
-    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    if (cfg->proposal) {
+        s = mlp_prepare(ctx, slots, P.max_depth);
+        if (s != PB_OK) return s;
+    }
+    if (!ctx->d_iter0) CK(cudaMalloc(&ctx->d_iter0, sizeof(uint32_t)));
+    return PB_OK;
+}
+
+// Enqueues the waves of a render on ctx->stream. Iteration numbers are
+// iter_off + (iterations already enqueued), plus *P.iter_dev when set
+// (graph replay). `ev` holds NEV events per wave; film == false leaves the
+// film alone (autotuning trials).
+static pb_status enqueue_render(pb_ctx *ctx, const pb_config *cfg, const KParams &P, int slots, uint32_t iter_off,
+                                cudaEvent_t *ev, bool film, bool capturing = false) {
+    cudaStream_t st = ctx->stream;
+    // inside a capture the stage events become event-record nodes of the graph
+    const unsigned int evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CK(cudaMemsetAsync(ctx->B.counters, 0, sizeof(unsigned long long) * CNT_N, st));
     int w = 0;
     for (int done = 0; done < cfg->spp; ++w) {
         int ns = std::min(slots, cfg->spp - done);
-        uint32_t base = (uint32_t)(cfg->iter0 + done);
-        cudaEvent_t *e = &ev[NEV * (size_t)w];
-        CK(cudaEventRecord(e[0], ctx->stream));
-        launch_light_pass(ctx->S, P, ctx->B, ns, base, ctx->stream);
-        CK(cudaEventRecord(e[1], ctx->stream));
-        launch_pool_build(ctx->S, ctx->T, P, ctx->B, ns, ctx->stream);
-        CK(cudaEventRecord(e[2], ctx->stream));
-        launch_recip(ctx->S, ctx->T, P, ctx->B, ns, base, ctx->num_sms, ctx->stream);
-        CK(cudaEventRecord(e[3], ctx->stream));
+        uint32_t base = iter_off + (uint32_t)done;
+        cudaEvent_t *e = ev + NEV * (size_t)w;
+        CK(cudaEventRecordWithFlags(e[0], st, evf));
+        launch_light_pass(ctx->S, P, ctx->B, ns, base, st);
+        CK(cudaEventRecordWithFlags(e[1], st, evf));
+        launch_pool_build(ctx->S, ctx->T, P, ctx->B, ns, st);
+        CK(cudaEventRecordWithFlags(e[2], st, evf));
+        launch_recip(ctx->S, ctx->T, P, ctx->B, ns, base, ctx->num_sms, st);
+        CK(cudaEventRecordWithFlags(e[3], st, evf));
         KParams Pw = P;
         if (cfg->proposal) {
-            s = mlp_wave(ctx, Pw, ns, base);
+            pb_status s = mlp_wave(ctx, Pw, ns, base);
             if (s != PB_OK) return s;
         }
-        CK(cudaEventRecord(e[4], ctx->stream));
-        launch_eye(ctx->S, ctx->T, Pw, ctx->B, ns, base, ctx->Lbuf, nullptr, ctx->stream);
-        CK(cudaEventRecord(e[5], ctx->stream));
-        launch_film_add(P, ns, ctx->Lbuf, ctx->film, ctx->stream);
+        CK(cudaEventRecordWithFlags(e[4], st, evf));
+        launch_eye(ctx->S, ctx->T, Pw, ctx->B, ns, base, ctx->Lbuf, nullptr, st);
+        CK(cudaEventRecordWithFlags(e[5], st, evf));
+        if (film) launch_film_add(P, ns, ctx->Lbuf, ctx->film, st);
         CK(cudaGetLastError());
         done += ns;
     }
-    CK(cudaEventRecord(ctx->ev1, ctx->stream));
-    CK(cudaEventSynchronize(ctx->ev1));
+    return PB_OK;
+}
+
+static pb_status make_events(pb_ctx *ctx, std::vector<cudaEvent_t> &ev, size_t n) {
+    ev.resize(n, nullptr);
+    for (auto &e : ev)
+        if (!e) CK(cudaEventCreate(&e));
+    return PB_OK;
+}
+
+// stats of a finished render (the caller synchronised)
+static pb_status finish_render(pb_ctx *ctx, const pb_config *cfg, const KParams &P, int slots,
+                               const std::vector<cudaEvent_t> &ev, cudaEvent_t e0, cudaEvent_t e1, bool film,
+                               pb_stats *stats) {
     CK(cudaGetLastError());
-    ctx->film_iters += cfg->spp;
+    int waves = (cfg->spp + slots - 1) / slots;
+    if (film) ctx->film_iters += cfg->spp;
     pb_stats st{};
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    cudaEventElapsedTime(&ms, e0, e1);
     st.ms = ms;
     st.mpaths_per_s = ms > 0 ? (double)P.npix * cfg->spp / (ms * 1e-3) / 1e6 : 0.0;
     for (int i = 0; i < waves; ++i) {
         float a = 0, b = 0, c = 0, d = 0, m = 0;
-        cudaEvent_t *e = &ev[NEV * (size_t)i];
+        const cudaEvent_t *e = ev.data() + NEV * (size_t)i;
         cudaEventElapsedTime(&a, e[0], e[1]);
         cudaEventElapsedTime(&b, e[1], e[2]);
         cudaEventElapsedTime(&c, e[2], e[3]);
@@ -622,18 +663,295 @@ pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
         st.ms_mlp += m;
         st.ms_eye += d;
     }
-    for (auto &e : ev) cudaEventDestroy(e);
     st.n_waves = waves;
     // light, pool, bucket, cdf, offsets, pilot, recip x2, finish, eye, film; proposal: feature pass, network
     st.n_launches = (11 + (cfg->proposal ? 2 : 0)) * (int64_t)waves;
     if (cfg->proposal) {
-        s = mlp_check_err(ctx);
+        pb_status s = mlp_check_err(ctx);
         if (s != PB_OK) return s;
     }
     read_counters(ctx, &st);
     if (stats) *stats = st;
     if (st.n_truncated > 0) return fail(ctx, PB_ERR_TRUNCATED, "reciprocal estimate hit the trial cap");
     return PB_OK;
+}
+
+static bool same_graph_cfg(const pb_config &a, const pb_config &b) {
+    pb_config x = a, y = b;
+    x.iter0 = y.iter0 = 0;
+    return std::memcmp(&x, &y, sizeof(pb_config)) == 0;
+}
+
+// the captured render of `cfg` (any iter0): one graph per configuration,
+// iteration numbers offset by *ctx->d_iter0 at replay
+static pb_status get_graph(pb_ctx *ctx, const pb_config *cfg, KParams P, int slots, RenderGraph **out) {
+    for (RenderGraph *g : ctx->graphs)
+        if (same_graph_cfg(g->cfg, *cfg)) {
+            *out = g;
+            return PB_OK;
+        }
+    RenderGraph *g = new RenderGraph();
+    g->cfg = *cfg;
+    g->slots = slots;
+    int waves = (cfg->spp + slots - 1) / slots;
+    pb_status s = make_events(ctx, g->ev, NEV * (size_t)std::max(waves, 1));
+    if (s == PB_OK) s = make_events(ctx, g->ends, 2);
+    if (s != PB_OK) {
+        delete g;
+        return s;
+    }
+    P.iter_dev = ctx->d_iter0;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecordWithFlags(g->ends[0], ctx->stream, cudaEventRecordExternal);
+    s = enqueue_render(ctx, cfg, P, slots, 0, g->ev.data(), true, true);
+    cudaEventRecordWithFlags(g->ends[1], ctx->stream, cudaEventRecordExternal);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (s != PB_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        delete g;
+        if (s != PB_OK) return s;
+        return fail(ctx, PB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    g->graph = graph;
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        delete g;
+        return fail(ctx, PB_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    ctx->graphs.push_back(g);
+    *out = g;
+    return PB_OK;
+}
+
+void free_graphs(pb_ctx *ctx) {
+    for (RenderGraph *g : ctx->graphs) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        for (auto e : g->ev) cudaEventDestroy(e);
+        for (auto e : g->ends) cudaEventDestroy(e);
+        delete g;
+    }
+    ctx->graphs.clear();
+}
+
+// ---- autotuning: iterations in flight x estimator hand-off per size bucket ----
+struct TuneEntry {
+    int batch, handoff;
+    double ms_per_iter;
+};
+static std::mutex g_tune_mutex;
+static std::map<std::string, TuneEntry> g_tune;
+
+static std::string tune_key(const pb_ctx *ctx, const pb_config *cfg) {
+    auto lg = [](long long v) {
+        int b = 0;
+        while ((1ll << (b + 1)) <= v) ++b;
+        return b;
+    };
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "tris2^%d|pix2^%d|depth%d|M%d|Mp%d|rep%d|prop%d|proxy%d", lg(ctx->S.nt),
+                  lg((long long)ctx->S.W * ctx->S.H), cfg->max_depth, cfg->M, cfg->M_p, cfg->repeats, cfg->proposal,
+                  cfg->proxy);
+    return std::string(buf);
+}
+
+extern "C" {
+
+pb_status pb_render(pb_ctx *ctx, const pb_config *cfg, pb_stats *stats) {
+    if (!ctx) return PB_ERR_ARG;
+    KParams P;
+    int slots;
+    pb_status s = prepare_render(ctx, cfg, P, slots);
+    if (s != PB_OK) return s;
+    if (cfg->graph) {
+        RenderGraph *g;
+        s = get_graph(ctx, cfg, P, slots, &g);
+        if (s != PB_OK) return s;
+        uint32_t it0 = (uint32_t)cfg->iter0;   // pageable source: staged before the call returns
+        CK(cudaMemcpyAsync(ctx->d_iter0, &it0, sizeof(it0), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaGraphLaunch(g->exec, ctx->stream));
+        CK(cudaEventSynchronize(g->ends[1]));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return finish_render(ctx, cfg, P, slots, g->ev, g->ends[0], g->ends[1], true, stats);
+    }
+    int waves = (cfg->spp + slots - 1) / slots;
+    std::vector<cudaEvent_t> ev;
+    if ((s = make_events(ctx, ev, NEV * (size_t)std::max(waves, 1))) != PB_OK) return s;
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    s = enqueue_render(ctx, cfg, P, slots, (uint32_t)cfg->iter0, ev.data(), true);
+    if (s == PB_OK) {
+        CK(cudaEventRecord(ctx->ev1, ctx->stream));
+        CK(cudaEventSynchronize(ctx->ev1));
+        s = finish_render(ctx, cfg, P, slots, ev, ctx->ev0, ctx->ev1, true, stats);
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return s;
+}
+
+pb_status pb_render_batch(pb_ctx *const *ctxs, const pb_config *cfgs, int n, pb_stats *stats) {
+    if (!ctxs || !cfgs || n < 1) return PB_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return PB_ERR_ARG;
+    pb_ctx *c0 = ctxs[0];
+    for (int i = 0; i < n; ++i) {
+        if (ctxs[i]->device != c0->device) return fail(c0, PB_ERR_ARG, "batch: contexts on different devices");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(c0, PB_ERR_ARG, "batch: a context appears twice");
+    }
+    std::vector<KParams> Ps(n);
+    std::vector<int> slots(n);
+    std::vector<RenderGraph *> gs(n);
+    for (int i = 0; i < n; ++i) {
+        pb_config c = cfgs[i];
+        c.graph = 1;
+        pb_status s = prepare_render(ctxs[i], &c, Ps[i], slots[i]);
+        if (s == PB_OK) s = get_graph(ctxs[i], &c, Ps[i], slots[i], &gs[i]);
+        if (s != PB_OK) {
+            if (ctxs[i] != c0) c0->err = "batch item " + std::to_string(i) + ": " + ctxs[i]->err;
+            return s;
+        }
+    }
+    // one graph: per scene, set its iteration base, then its render
+    pb_ctx *ctx = c0;
+    cudaGraph_t parent = nullptr;
+    CK(cudaGraphCreate(&parent, 0));
+    pb_status s = PB_OK;
+    for (int i = 0; i < n && s == PB_OK; ++i) {
+        cudaMemsetParams mp{};
+        mp.dst = ctxs[i]->d_iter0;
+        mp.value = (unsigned int)cfgs[i].iter0;
+        mp.elementSize = 4;
+        mp.width = 1;
+        mp.height = 1;
+        cudaGraphNode_t ms, child;
+        cudaError_t e = cudaGraphAddMemsetNode(&ms, parent, nullptr, 0, &mp);
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, parent, &ms, 1, gs[i]->graph);
+        if (e != cudaSuccess) s = fail(ctx, PB_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (s == PB_OK) {
+        cudaError_t e = cudaGraphInstantiate(&exec, parent, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev0, ctx->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) s = fail(ctx, PB_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(parent);
+    if (s != PB_OK) return s;
+    pb_status worst = PB_OK;
+    for (int i = 0; i < n; ++i) {
+        pb_config c = cfgs[i];
+        c.graph = 1;
+        pb_status si = finish_render(ctxs[i], &c, Ps[i], slots[i], gs[i]->ev, gs[i]->ends[0], gs[i]->ends[1], true,
+                                     stats ? &stats[i] : nullptr);
+        if (si != PB_OK && si != PB_ERR_TRUNCATED) return si;
+        if (si == PB_ERR_TRUNCATED) worst = si;
+    }
+    if (stats) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        stats[0].batch_ms = ms;
+    }
+    return worst;
+}
+
+pb_status pb_autotune(pb_ctx *ctx, const pb_config *cfg, int trial_iters, pb_config *best, int *from_cache) {
+    if (!ctx) return PB_ERR_ARG;
+    if (!cfg || !best) return fail(ctx, PB_ERR_ARG, "autotune: null config");
+    pb_status s = check_cfg(ctx, cfg);
+    if (s != PB_OK) return s;
+    std::string key = tune_key(ctx, cfg);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            *best = *cfg;
+            best->batch = it->second.batch;
+            best->chain_handoff = it->second.handoff;
+            if (from_cache) *from_cache = 1;
+            return PB_OK;
+        }
+    }
+    if (from_cache) *from_cache = 0;
+    int n = trial_iters > 0 ? trial_iters : 32;
+    const int batches[] = {4, 8, 16, 32};
+    const int handoffs[] = {256, 512, 1024};
+    TuneEntry bestE{0, 0, 1e300};
+    std::vector<cudaEvent_t> ev;
+    bool warmed = false;
+    for (int b : batches) {
+        if (b > n) continue;
+        for (int h : handoffs) {
+            pb_config c = *cfg;
+            c.batch = b;
+            c.chain_handoff = h;
+            c.spp = n;
+            c.iter0 = (1 << 28) + 7919;   // iterations no render uses
+            c.graph = 0;
+            KParams P;
+            int slots;
+            if ((s = prepare_render(ctx, &c, P, slots)) != PB_OK) return s;
+            int waves = (n + slots - 1) / slots;
+            if ((s = make_events(ctx, ev, NEV * (size_t)waves)) != PB_OK) return s;
+            for (int rep = warmed ? 0 : 1; rep >= 0; --rep) {   // the first trial runs twice (warm-up)
+                CK(cudaEventRecord(ctx->ev0, ctx->stream));
+                if ((s = enqueue_render(ctx, &c, P, slots, (uint32_t)c.iter0, ev.data(), false)) != PB_OK) return s;
+                CK(cudaEventRecord(ctx->ev1, ctx->stream));
+                CK(cudaEventSynchronize(ctx->ev1));
+            }
+            warmed = true;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            if (cfg->proposal) {
+                if ((s = mlp_check_err(ctx)) != PB_OK) return s;
+            }
+            double per = ms / n;
+            if (per < bestE.ms_per_iter) bestE = TuneEntry{b, h, per};
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (bestE.batch == 0) return fail(ctx, PB_ERR_ARG, "autotune: no candidate fits trial_iters");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune[key] = bestE;
+    }
+    *best = *cfg;
+    best->batch = bestE.batch;
+    best->chain_handoff = bestE.handoff;
+    return PB_OK;
+}
+
+pb_status pb_autotune_cache_save(const char *path) {
+    if (!path) return PB_ERR_ARG;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return PB_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (auto &kv : g_tune)
+        std::fprintf(f, "%s %d %d %.9g\n", kv.first.c_str(), kv.second.batch, kv.second.handoff, kv.second.ms_per_iter);
+    std::fclose(f);
+    return PB_OK;
+}
+
+pb_status pb_autotune_cache_load(const char *path) {
+    if (!path) return PB_ERR_ARG;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return PB_ERR_ARG;
+    char key[256];
+    TuneEntry e;
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    while (std::fscanf(f, "%255s %d %d %lf", key, &e.batch, &e.handoff, &e.ms_per_iter) == 4)
+        if (e.batch > 0 && e.batch <= 64 && e.handoff > 0) g_tune[key] = e;
+    std::fclose(f);
+    return PB_OK;
+}
+
+void pb_autotune_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_tune.clear();
 }
 
 pb_status pb_film_clear(pb_ctx *ctx) {

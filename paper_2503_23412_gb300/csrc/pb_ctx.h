@@ -34,6 +34,16 @@ struct MlpState {
     int32_t *b_T = nullptr, *b_S = nullptr;
 };
 
+// a render captured as a CUDA graph (one per configuration; iter0 is a device scalar)
+struct RenderGraph {
+    pb_config cfg;
+    int slots = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;     // per wave stage events
+    std::vector<cudaEvent_t> ends;   // start and end of the render
+};
+
 struct pb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -55,6 +65,8 @@ struct pb_ctx {
     int64_t film_iters = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     MlpState mlp;
+    std::vector<RenderGraph *> graphs;
+    uint32_t *d_iter0 = nullptr;     // iteration base of graph replays
 };
 
 // shared by the host translation units
@@ -66,6 +78,8 @@ KParams pb_kparams(const pb_ctx *ctx, const pb_config *c);
 pb_status pb_check_cfg(pb_ctx *ctx, const pb_config *c);
 // learned proposal (pb_mlp.cu)
 void mlp_free(pb_ctx *ctx);
+pb_status mlp_prepare(pb_ctx *ctx, int slots, int depth);
+void free_graphs(pb_ctx *ctx);
 pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base);
 pb_status mlp_check_err(pb_ctx *ctx);
 // one wave of iterations that records proposal training samples and leaves the film alone (pb_api.cu)

@@ -70,6 +70,7 @@ __device__ __forceinline__ float mis_cell(const DTables &T, int u, int Sp, int C
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base,
                                              float4 *Lbuf, uint32_t *sigbuf) {
+    iter_base = eff_iter(P, iter_base);
     TravCount tc{0, 0, 0};
     int pix = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = blockIdx.y;
@@ -473,6 +474,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
 // k_eye makes a subspace connection (row order is arbitrary; each row's
 // result depends on its own content only).
 __global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
     int pix = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = blockIdx.y;
     if (pix >= P.npix) return;

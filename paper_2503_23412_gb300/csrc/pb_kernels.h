@@ -54,7 +54,12 @@ struct KParams {
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
     SampleSink smp;         // raw != nullptr: record proposal training samples
+    const uint32_t *iter_dev;   // non-null (graph replay): iteration numbers are *iter_dev + the launch's base
 };
+
+__device__ __forceinline__ uint32_t eff_iter(const KParams &P, uint32_t iter_base) {
+    return P.iter_dev ? iter_base + *P.iter_dev : iter_base;
+}
 
 // Walk state of a reciprocal estimate handed from a warp to a block: the next
 // pre-order node index, the running sums, the sign of the next node and the

@@ -20,6 +20,7 @@ namespace {
 
 // ---------------------------------------------------------------------------
 __global__ void k_light_pass(DScene S, KParams P, Pool B, uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = blockIdx.y;
     if (l >= P.M) return;
@@ -293,6 +294,7 @@ __device__ __forceinline__ Entry load_entry(const DScene &S, const KParams &P, c
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_recip_pilot(DScene S, DTables T, KParams P, Pool B, int slots,
                                                      uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
     int lane = threadIdx.x & 31;
     TravCount tc{0, 0, 0};
     const int32_t *offs = B.work + 1;   // per slot: first (entry, repeat) item
@@ -338,6 +340,7 @@ __global__ void __launch_bounds__(128) k_recip_pilot(DScene S, DTables T, KParam
 // queued for phase 2 with their walk state (after P.handoff nodes).
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, Pool B, int slots, uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
     int lane = threadIdx.x & 31;
     TravCount tc{0, 0, 0};
     int32_t *counter = B.work;
@@ -456,6 +459,7 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
 template <bool COUNT>
 __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T, KParams P, Pool B, int slots,
                                                             uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
     __shared__ float sg[PH2_BATCH];
     __shared__ int sn[PH2_BATCH];
     __shared__ int s_item, s_done, s_end, s_neg;

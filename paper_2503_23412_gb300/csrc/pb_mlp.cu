@@ -159,6 +159,7 @@ struct SelArgs {
     // selection mode
     int A, npix, slots, KT;
     uint32_t seed, iter_base;
+    const uint32_t *iter_dev;    // graph replay: iteration numbers are *iter_dev + iter_base
     const int32_t *bstart;   // slots x (K + 1)
     const float *gC;         // KT x K
     const float *ZC;         // slots x KT
@@ -439,7 +440,8 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
             float target = 0.0f;
             if (valid) {
                 Rng R;
-                R.init(a.seed, K_CAMERA, a.iter_base + (uint32_t)slot, (uint32_t)pix, (uint32_t)av);
+                const uint32_t ib = a.iter_dev ? a.iter_base + *a.iter_dev : a.iter_base;
+                R.init(a.seed, K_CAMERA, ib + (uint32_t)slot, (uint32_t)pix, (uint32_t)av);
                 const float u = R.u(6);
                 if (u < MLP_EPS) gpick = select_cdf_row(a.cdfC + ((size_t)slot * a.KT + T) * a.K, a.K, u / MLP_EPS);
                 else target = (u - MLP_EPS) / (1.0f - MLP_EPS) * Zg;
@@ -716,6 +718,7 @@ static pb_status mlp_shape(pb_ctx *ctx) {
     MlpState &M = ctx->mlp;
     int K = ctx->T.KS, KT = ctx->T.KT;
     if (M.K == K && M.KT == KT && M.w) return PB_OK;
+    free_graphs(ctx);
     mlp_free(ctx);
     M.K = K;
     M.KT = KT;
@@ -757,16 +760,23 @@ static pb_status mlp_pack(pb_ctx *ctx) {
     return PB_OK;
 }
 
+static pb_status set_select_attr(pb_ctx *ctx) {
+    static bool done = false;
+    if (done) return PB_OK;
+    int smem = 120 * 1024;
+    CK(cudaFuncSetAttribute(k_mlp_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    CK(cudaFuncSetAttribute(k_mlp_select<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    done = true;
+    return PB_OK;
+}
+
 static pb_status run_select(pb_ctx *ctx, SelArgs &a, bool device_count) {
-    int smem = (int)sel_smem(a.Kpad).bytes;
-    // one CTA per SM: the kernel holds all 512 TMEM columns
-    int smem_req = smem < 120 * 1024 ? 120 * 1024 : smem;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[a.logits ? 1 : 0]) {
-        if (a.logits) CK(cudaFuncSetAttribute(k_mlp_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_req));
-        else CK(cudaFuncSetAttribute(k_mlp_select<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_req));
-        attr_set[a.logits ? 1 : 0] = true;
-    }
+    // one CTA per SM: the kernel holds all 512 TMEM columns, and 120 KB of
+    // shared memory keeps a second CTA off the SM (the layout needs < 100 KB)
+    const int smem_req = 120 * 1024;
+    if ((int)sel_smem(a.Kpad).bytes > smem_req) return pb_fail(ctx, PB_ERR_ARG, "mlp: shared memory layout too large");
+    pb_status s0 = set_select_attr(ctx);
+    if (s0 != PB_OK) return s0;
     long long ntiles = (a.nrows + TILE_M - 1) / TILE_M;
     // with the row count on the device every SM gets a CTA; idle ones exit at once
     int grid = device_count ? ctx->num_sms : (int)std::min<long long>(ntiles, (long long)ctx->num_sms);
@@ -794,6 +804,7 @@ pb_status mlp_ensure_rows(pb_ctx *ctx, int slots, int A, int depth) {
     MlpState &M = ctx->mlp;
     size_t npix = (size_t)ctx->S.W * ctx->S.H;
     size_t n = (size_t)slots * A * npix;
+    if (M.cap_rowT < n || M.cap_hits < (size_t)slots * depth * npix) free_graphs(ctx);
     CK(grow(&M.rows, M.cap_rows16, MLP_NX * n));
     CK(grow(&M.rowT, M.cap_rowT, n));
     CK(grow(&M.rowPos, M.cap_rowPos, n));
@@ -802,6 +813,16 @@ pb_status mlp_ensure_rows(pb_ctx *ctx, int slots, int A, int depth) {
     CK(grow(&M.hits, M.cap_hits, (size_t)slots * depth * npix));
     if (!M.rcount) CK(cudaMalloc(&M.rcount, sizeof(unsigned int)));
     return PB_OK;
+}
+
+// everything a wave of the learned proposal allocates or configures, done
+// before a render is enqueued (and possibly captured)
+pb_status mlp_prepare(pb_ctx *ctx, int slots, int depth) {
+    if (!ctx->mlp.ready) return pb_fail(ctx, PB_ERR_STATE, "learned proposal requested but no network is loaded");
+    if (depth - 2 < 1) return PB_OK;
+    pb_status s = mlp_ensure_rows(ctx, slots, depth - 2, depth);
+    if (s != PB_OK) return s;
+    return set_select_attr(ctx);
 }
 
 // feature pass, network and selection for one wave of iterations; sets P.mlp
@@ -829,6 +850,7 @@ pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base) {
     a.slots = slots;
     a.seed = P.seed;
     a.iter_base = iter_base;
+    a.iter_dev = P.iter_dev;
     a.bstart = ctx->B.bstart;
     a.gC = ctx->T.gC;
     a.ZC = ctx->B.ZC;

@@ -39,7 +39,8 @@ class pb_config(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("spp", C.c_int), ("max_depth", C.c_int), ("M", C.c_int),
                 ("M_p", C.c_int), ("repeats", C.c_int), ("proxy", C.c_int), ("conn", C.c_int),
                 ("trial_cap", C.c_int), ("iter0", C.c_int), ("batch", C.c_int), ("count_traversal", C.c_int),
-                ("chain_handoff", C.c_int), ("pilot_min", C.c_int), ("pilot_max", C.c_int), ("proposal", C.c_int)]
+                ("chain_handoff", C.c_int), ("pilot_min", C.c_int), ("pilot_max", C.c_int), ("proposal", C.c_int),
+                ("graph", C.c_int)]
 
 
 class pb_stats(C.Structure):
@@ -49,7 +50,7 @@ class pb_stats(C.Structure):
                 ("ms_pool", C.c_double), ("ms_recip", C.c_double), ("ms_eye", C.c_double),
                 ("n_launches", C.c_int64), ("n_waves", C.c_int64), ("eye_nodes", C.c_int64),
                 ("eye_tris", C.c_int64), ("eye_rays", C.c_int64), ("rec_nodes", C.c_int64),
-                ("rec_tris", C.c_int64), ("rec_rays", C.c_int64), ("ms_mlp", C.c_double)]
+                ("rec_tris", C.c_int64), ("rec_rays", C.c_int64), ("ms_mlp", C.c_double), ("batch_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -88,7 +89,8 @@ EXPORTS = ["pb_create", "pb_destroy", "pb_last_error", "pb_scene_upload", "pb_ta
            "pb_film_clear", "pb_film_readback", "pb_film_device", "pb_trace", "pb_occluded", "pb_light_pass",
            "pb_iteration", "pb_prepare", "pb_tables_readback", "pb_recip_estimates_noalloc", "pb_mlp_nparams",
            "pb_mlp_upload", "pb_mlp_readback", "pb_mlp_logits", "pb_mlp_grad", "pb_mlp_train_batch",
-           "pb_train_proposal", "pb_connection_moments"]
+           "pb_train_proposal", "pb_connection_moments", "pb_render_batch", "pb_autotune", "pb_autotune_cache_save",
+           "pb_autotune_cache_load", "pb_autotune_cache_clear"]
 
 
 def lib(path=LIB):
@@ -126,9 +128,15 @@ def lib(path=LIB):
     L.pb_mlp_train_batch.argtypes = [vp, i32, vp, vp, vp, vp, C.c_float, C.POINTER(C.c_float)]
     L.pb_train_proposal.argtypes = [vp, C.POINTER(pb_config), C.POINTER(pb_train_desc), C.POINTER(pb_train_stats)]
     L.pb_connection_moments.argtypes = [vp, C.POINTER(pb_config), vp]
+    L.pb_render_batch.argtypes = [vp, vp, i32, vp]
+    L.pb_autotune.argtypes = [vp, C.POINTER(pb_config), i32, C.POINTER(pb_config), C.POINTER(i32)]
+    L.pb_autotune_cache_save.argtypes = [C.c_char_p]
+    L.pb_autotune_cache_load.argtypes = [C.c_char_p]
+    L.pb_autotune_cache_clear.argtypes = []
     for n in EXPORTS:
-        if n not in ("pb_destroy", "pb_last_error"):
+        if n not in ("pb_destroy", "pb_last_error", "pb_autotune_cache_clear"):
             getattr(L, n).restype = i32
+    L.pb_autotune_cache_clear.restype = None
     L.pb_mlp_nparams.argtypes = [i32, i32]
     L.pb_mlp_nparams.restype = C.c_size_t
     _lib = L
@@ -146,9 +154,37 @@ class PBError(RuntimeError):
 
 
 def config(seed=7, spp=1, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, conn=1, trial_cap=1 << 16, iter0=0,
-           batch=0, count_traversal=0, chain_handoff=0, pilot_min=0, pilot_max=0, proposal=0):
+           batch=0, count_traversal=0, chain_handoff=0, pilot_min=0, pilot_max=0, proposal=0, graph=0):
     return pb_config(seed, spp, max_depth, M, M_p, repeats, proxy, conn, trial_cap, iter0, batch, count_traversal,
-                     chain_handoff, pilot_min, pilot_max, proposal)
+                     chain_handoff, pilot_min, pilot_max, proposal, graph)
+
+
+def render_batch(renderers, cfgs, allow_truncated=False):
+    """One graph launch rendering every scene (see pb_render_batch); returns per-scene stats."""
+    L = lib()
+    n = len(renderers)
+    hs = (C.c_void_p * n)(*[r.h for r in renderers])
+    cs = (pb_config * n)(*cfgs)
+    st = (pb_stats * n)()
+    rc = L.pb_render_batch(hs, cs, n, st)
+    ok = (PB_OK, PB_ERR_TRUNCATED) if allow_truncated else (PB_OK,)
+    if rc not in ok:
+        raise PBError(rc, L.pb_last_error(renderers[0].h).decode())
+    return [s.as_dict() for s in st]
+
+
+def autotune_cache_save(path):
+    if lib().pb_autotune_cache_save(path.encode()) != PB_OK:
+        raise PBError(PB_ERR_ARG, "cannot write " + path)
+
+
+def autotune_cache_load(path):
+    if lib().pb_autotune_cache_load(path.encode()) != PB_OK:
+        raise PBError(PB_ERR_ARG, "cannot read " + path)
+
+
+def autotune_cache_clear():
+    lib().pb_autotune_cache_clear()
 
 
 def train_desc(samples=1 << 20, rounds=2, steps=400, batch=4096, lr=1e-3, seed=1, iter0=1 << 23, max_iters_per_round=0,
@@ -345,6 +381,12 @@ class Renderer:
         loss = C.c_float(0.0)
         self._check(self.L.pb_mlp_train_batch(self.h, len(T), _p(raw), _p(T), _p(S), _p(w), lr, C.byref(loss)))
         return loss.value
+
+    def autotune(self, cfg, trial_iters=32):
+        best = pb_config()
+        fc = C.c_int(0)
+        self._check(self.L.pb_autotune(self.h, C.byref(cfg), trial_iters, C.byref(best), C.byref(fc)))
+        return best, bool(fc.value)
 
     def connection_moments(self, cfg):
         out = np.zeros(3)

@@ -1,0 +1,121 @@
+"""Graph replay, batched multi-scene rendering and the autotuner.
+
+Iterations are independent and the film adds them in iteration order, so
+how iterations are grouped into waves, whether the waves are replayed from a
+captured CUDA graph, and whether several scenes share one graph launch must
+not change a single bit of any film. The estimator's hand-off point only
+changes its summation order, so a tuned configuration matches the default
+up to rounding.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2503_23412_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2503_23412_gb300 import build
+    build.build()
+    from paper_2503_23412_gb300 import native
+    native.lib()
+    return native
+
+
+def _prepared(N, sc, KT=24, KS=24, **base):
+    r = N.Renderer(sc)
+    r.prepare(N.config(**base), n_iter=2, iter0=7000, n_bsamples=16, lloyd_iters=4, KT=KT, KS=KS, KSp=8, KC=2)
+    return r
+
+
+def _film(N, r, cfg):
+    r.clear()
+    st = r.render(cfg, allow_truncated=True)
+    return r.film(), st
+
+
+def test_graph_replay_is_bit_identical(N):
+    base = dict(M=1500, M_p=1500, max_depth=6)
+    r = _prepared(N, scenes.cornell(24, 24), **base)
+    for it0 in (100, 900):   # the second replay reuses the captured graph with a new iter0
+        a, _ = _film(N, r, N.config(spp=12, iter0=it0, batch=5, **base))
+        b, st = _film(N, r, N.config(spp=12, iter0=it0, batch=5, graph=1, **base))
+        np.testing.assert_array_equal(a, b)
+        assert st["n_waves"] == 3 and st["ms"] > 0
+    # wave grouping does not matter either
+    c, _ = _film(N, r, N.config(spp=12, iter0=900, batch=4, **base))
+    np.testing.assert_array_equal(b, c)
+    r.close()
+
+
+def test_graph_replay_with_learned_proposal(N):
+    base = dict(M=1500, M_p=1500, max_depth=6)
+    r = _prepared(N, scenes.cornell(24, 24), **base)
+    r.train_proposal(N.config(**base), N.train_desc(samples=1 << 16, rounds=1, steps=50, batch=2048, seed=3))
+    a, _ = _film(N, r, N.config(spp=8, iter0=300, proposal=1, **base))
+    b, st = _film(N, r, N.config(spp=8, iter0=300, proposal=1, graph=1, **base))
+    np.testing.assert_array_equal(a, b)
+    assert st["ms_mlp"] > 0
+    r.close()
+
+
+def test_batch_of_uneven_scenes_matches_solo_renders(N):
+    """Three scenes of different size, depth and spp in one graph launch:
+    every film equals the scene's solo render, bit for bit."""
+    items = [
+        (scenes.cornell(32, 24), dict(M=1500, M_p=1500, max_depth=6), 10),
+        (scenes.caustic_mini(16, 12), dict(M=800, M_p=800, max_depth=5), 24),
+        (scenes.projector(24, 24, lens_tris_per_cap=800), dict(M=1200, M_p=1200, max_depth=8), 6),
+    ]
+    rs, cfgs, solo = [], [], []
+    for sc, base, spp in items:
+        r = _prepared(N, sc, **base)
+        cfg = N.config(spp=spp, iter0=40, **base)
+        solo.append(_film(N, r, cfg)[0])
+        r.clear()
+        rs.append(r)
+        cfgs.append(cfg)
+    st = N.render_batch(rs, cfgs, allow_truncated=True)
+    assert st[0]["batch_ms"] > 0
+    for r, ref, s, (sc, base, spp) in zip(rs, solo, st, items):
+        np.testing.assert_array_equal(r.film(), ref)
+        assert s["n_waves"] >= 1 and s["ms"] > 0
+    # a second batch reuses the captured graphs (new iteration numbers)
+    for r in rs:
+        r.clear()
+    cfgs2 = [N.config(spp=c.spp, iter0=500, **b) for c, (_, b, _) in zip(cfgs, items)]
+    N.render_batch(rs, cfgs2, allow_truncated=True)
+    for r, c in zip(rs, cfgs2):
+        got = r.film()
+        ref, _ = _film(N, r, c)
+        np.testing.assert_array_equal(got, ref)
+    for r in rs:
+        r.close()
+
+
+def test_autotune_chooses_cached_valid_configuration(N, tmp_path):
+    base = dict(M=1500, M_p=1500, max_depth=6)
+    r = _prepared(N, scenes.cornell(32, 32), **base)
+    N.autotune_cache_clear()
+    cfg = N.config(spp=16, iter0=50, **base)
+    best, cached = r.autotune(cfg, trial_iters=16)
+    assert not cached
+    assert best.batch in (4, 8, 16) and best.chain_handoff in (256, 512, 1024)
+    assert (best.spp, best.iter0, best.M, best.max_depth) == (16, 50, 1500, 6)
+    best2, cached2 = r.autotune(cfg, trial_iters=16)
+    assert cached2 and (best2.batch, best2.chain_handoff) == (best.batch, best.chain_handoff)
+    # the cache survives a save / clear / load round trip
+    path = str(tmp_path / "tune.txt")
+    N.autotune_cache_save(path)
+    N.autotune_cache_clear()
+    N.autotune_cache_load(path)
+    best3, cached3 = r.autotune(cfg, trial_iters=16)
+    assert cached3 and (best3.batch, best3.chain_handoff) == (best.batch, best.chain_handoff)
+    # tuned and default renders agree (the hand-off changes only the estimator's summation order)
+    a, _ = _film(N, r, cfg)
+    b, _ = _film(N, r, best)
+    np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6 * float(np.abs(a).max()))
+    r.close()
