@@ -262,6 +262,68 @@ def equal_time_study(N, r, M_p, base_iter, table_ms):
     }
 
 
+def run_batch(args):
+    """Batched workload: procedural glass / GGX / diffuse scenes of uneven
+    size rendered by one graph launch (pb_render_batch), each with its
+    autotuned configuration, against the same scenes rendered one after
+    another. 1 GPU, rank 0 only."""
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_2503_23412_gb300 import native as N
+    from paper_2503_23412_gb300 import scenes
+    specs = scenes.batch_specs(args.scenes, seed=1)
+    depth, Mb = 10, 10000
+    rs, cfgs, tuned = [], [], 0
+    t0 = time.perf_counter()
+    for (w_, h_, spp, nt, sd) in specs:
+        sc = scenes.glossy_mix(w_, h_, nt, seed=sd)
+        r = N.Renderer(sc)
+        st = r.prepare(N.config(M=Mb, M_p=Mb, max_depth=depth), n_iter=2, iter0=1 << 22, n_bsamples=16,
+                       lloyd_iters=6, KT=64, KS=64, KSp=32, KC=4)
+        frac = st["n_entries"] / float(2 * Mb)
+        mp = int(min(Mb, max(1, round(ENTRY_TARGET / max(frac, 1e-9)))))
+        cfg = N.config(M=Mb, M_p=mp, max_depth=depth, spp=spp, seed=7)
+        best, cached = r.autotune(cfg, trial_iters=16)
+        tuned += 0 if cached else 1
+        rs.append(r)
+        cfgs.append(best)
+    setup_s = time.perf_counter() - t0
+    paths = sum(w_ * h_ * spp for (w_, h_, spp, _, _) in specs)
+    # one after another, eager
+    seq_ms = 0.0
+    for r, c in zip(rs, cfgs):
+        r.clear()
+        seq_ms += r.render(c, allow_truncated=True)["ms"]
+    # one graph launch per batch: the first captures every scene's graph
+    for k in range(args.warmup + args.steps):
+        for r in rs:
+            r.clear()
+        for c in cfgs:
+            c.iter0 = (k + 1) * 4096
+        st = N.render_batch(rs, cfgs, allow_truncated=True)
+        if k == args.warmup:
+            times = []
+        if k >= args.warmup:
+            times.append(st[0]["batch_ms"])
+    batch_ms = float(np.mean(times))
+    out = {"metric": "Mpaths/s, batched render of procedural scenes in one graph launch", "value": paths / (batch_ms * 1e-3) / 1e6,
+           "unit": "Mpaths/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch of %d glass/GGX/diffuse scenes (20/40/40), 1k-500k triangles log-uniform, "
+                                  "{128,256,512}^2, spp 16-256 log-uniform, depth %d, M=%d" % (len(specs), depth, Mb),
+                      "scenes": [{"W": w_, "spp": s_, "tris": t_} for (w_, _, s_, t_, _) in specs],
+                      "paths_per_step": paths, "sequential_eager_ms": seq_ms,
+                      "sequential_eager_mpaths": paths / (seq_ms * 1e-3) / 1e6,
+                      "speedup_vs_sequential": seq_ms / batch_ms, "setup_s": setup_s, "autotuned_buckets": tuned,
+                      "tuned": [{"batch": c.batch, "handoff": c.chain_handoff} for c in cfgs]}}
+    print(json.dumps(out))
+    for r in rs:
+        r.close()
+
+
 # ---------------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -406,14 +468,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--proposal", default="table", choices=["table", "learned"],
                     help="light-subspace proposal of the timed steps (learned: trained before timing)")
-    ap.add_argument("--workload", default="projector", choices=["projector", "small"],
-                    help="small: the same scene and pipeline at 64x64, 4 spp, M=2000 (profiling captures)")
+    ap.add_argument("--workload", default="projector", choices=["projector", "small", "batch"],
+                    help="small: the same scene and pipeline at 64x64, 4 spp, M=2000 (profiling captures); "
+                         "batch: procedural scenes of uneven size in one graph launch")
+    ap.add_argument("--scenes", type=int, default=16, help="scenes of the batch workload")
     args = ap.parse_args()
     if args.workload == "small":
         W, H, SPP, M = 64, 64, 4, 2000
         WORKLOAD = WORKLOAD.replace("256x256, 64 spp", "64x64, 4 spp").replace("M=10000", "M=2000")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

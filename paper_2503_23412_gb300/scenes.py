@@ -321,6 +321,64 @@ def glossy(W=512, H=512, n_inst=2000, seed=1, n_lights=3):
     return b.build(np.zeros((1, 1, 3)), cam)
 
 
+def glossy_mix(W=256, H=256, n_tris=20000, seed=1, n_lights=3, glass=0.2, ggx=0.4):
+    """A scene of the batched workload: seeded instances (icospheres of
+    80..1280 triangles and boxes) in a 20^3 volume until about `n_tris`
+    triangles, materials glass / GGX conductor / Lambert in the ratio
+    glass : ggx : rest (roughness log-uniform in [0.005, 0.1], IOR 1.5),
+    `n_lights` quad lights of radiance log-uniform in [1, 50], inside a
+    diffuse enclosure."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = _Builder()
+    encl = b.add_material(material(LAMBERT, (0.5, 0.5, 0.5)))
+    b.add_box((-1, -1, -1), (21, 21, 21), encl, inward=True)
+    spheres = {s: icosphere(s) for s in (1, 2, 3)}
+    tris, i = 12, 0
+    while tris < n_tris:
+        x = rng.uniform()
+        rough = float(math.exp(rng.uniform(math.log(0.005), math.log(0.1))))
+        if x < glass:
+            m = material(DIELECTRIC, (1, 1, 1), rough=rough, ior=1.5)
+        elif x < glass + ggx:
+            m = material(CONDUCTOR, tuple(rng.uniform(0.6, 0.95, 3)), rough=rough)
+        else:
+            m = material(LAMBERT, tuple(rng.uniform(0.3, 0.8, 3)))
+        mi = b.add_material(m)
+        c = rng.uniform(0, 20, 3)
+        size = rng.uniform(0.2, 0.8)
+        if i % 2 == 0:
+            sub = int(rng.choice([1, 2, 3, 3, 3]))
+            sv, st = spheres[sub]
+            b.add_mesh(sv * size + c, st, mi)
+            tris += len(st)
+        else:
+            b.add_box(c - size, c + size, mi, inward=False)
+            tris += 12
+        i += 1
+    for _ in range(n_lights):
+        L = float(math.exp(rng.uniform(0.0, math.log(50.0))))
+        li = b.add_material(material(LAMBERT, (0, 0, 0), Le=(L, L, L)))
+        c = rng.uniform(2, 18, 3)
+        c[1] = 20.9
+        b.add_quad(c, (0.8, 0, 0), (0, 0, 0.8), (0, -1, 0), li)
+    cam = [10.0, 10.0, -0.9, 10.0, 10.0, 10.0, 0, 1, 0, 70.0, W, H]
+    return b.build(np.zeros((1, 1, 3)), cam)
+
+
+def batch_specs(n=64, seed=1, tris=(1000, 500000), res=(128, 256, 512), spp=(16, 256)):
+    """Per-scene (W, H, spp, triangles, seed) of the batched workload:
+    triangle counts and spp log-uniform in the given ranges, square
+    resolutions uniform over `res`."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(n):
+        t = int(math.exp(rng.uniform(math.log(tris[0]), math.log(tris[1]))))
+        r = int(rng.choice(res))
+        s = int(round(math.exp(rng.uniform(math.log(spp[0]), math.log(spp[1])))))
+        out.append((r, r, s, t, 1000 + k))
+    return out
+
+
 SCENES = {"cornell": cornell, "projector": projector, "furnace": furnace, "glossy": glossy}
 
 
