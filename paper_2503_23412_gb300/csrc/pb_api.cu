@@ -99,6 +99,7 @@ pb_status ensure_pool(pb_ctx *ctx, int slots, int ML, int repeats, int npix) {
     CK(dalloc(o, &B.reptr, n * repeats));
     CK(dalloc(o, &B.rhat, n));
     CK(dalloc(o, &B.eB, n));
+    CK(dalloc(o, &B.eMu, n));
     CK(dalloc(o, &B.esig, n));
     CK(dalloc(o, &B.work, (size_t)slots + 5));
     B.chain_cap = (int)std::min<size_t>(n * repeats, (size_t)1 << 18);

@@ -95,6 +95,7 @@ struct Pool {
     int32_t *reptr;
     float *rhat;                                   // per entry: averaged reciprocal estimate
     float *eB;                                     // per entry: bound B of its estimates
+    float *eMu;                                    // per entry: expected nodes per estimate, B / mean(f/q) (0: unknown)
     uint32_t *esig;
     int32_t *work;                                 // work counters, per-slot work offsets
     struct ChainState *chains;                     // estimates continued by whole blocks

@@ -310,17 +310,28 @@ __global__ void __launch_bounds__(128) k_recip_pilot(DScene S, DTables T, KParam
         int k = item - offs[slot] / P.repeats;
         int Sp, C;
         Entry E = load_entry(S, P, B, slot, k, Sp, C);
-        float best = 0.0f;
+        float best = 0.0f, sum = 0.0f;
+        int draws = 0;
         for (int base = 0; base < P.pilot_max; base += 32) {
             if (base >= P.pilot_min && best > 0.0f) break;   // best is warp-uniform
             Rng R;
             R.init(P.seed, K_PILOT, iter_base + slot, (uint32_t)k, (uint32_t)(base + lane));
             float x = entry_ratio<COUNT>(S, E, R, &tc);
-            for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
-            best = fmaxf(best, x);
+            float m = x, t = x;
+            for (int o = 16; o > 0; o >>= 1) {
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                t += __shfl_xor_sync(0xffffffffu, t, o);
+            }
+            best = fmaxf(best, m);
+            sum += t;
+            draws += 32;
         }
-        if (lane == 0)
-            B.eB[(size_t)slot * B.ML + k] = best > 0.0f ? best : T.Bt[((E.u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
+        if (lane == 0) {
+            float Bv = best > 0.0f ? best : T.Bt[((E.u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
+            B.eB[(size_t)slot * B.ML + k] = Bv;
+            // a scheduling hint only: the expected chain length B / mean(f/q) when g stays in [0, 1]
+            B.eMu[(size_t)slot * B.ML + k] = sum > 0.0f ? Bv * (float)draws / sum : 0.0f;
+        }
     }
     if (COUNT) {
         atomicAdd(&B.counters[CNT_REC_NODES], (unsigned long long)tc.nodes);
@@ -358,6 +369,8 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
         int Sp, C;
         Entry E = load_entry(S, P, B, slot, k, Sp, C);
         float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
+        // chains expected to run far past the hand-off start in the block phase
+        const bool long_chain = B.eMu[(size_t)slot * B.ML + k] > 8.0f * (float)P.handoff;
         double sum_t = 0.0;   // long chains add thousands of terms
         int nodes = 0;
         bool done = false, trunc = false, handed = false;
@@ -367,7 +380,7 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
         float cur_sign = 1.0f;
         bool deep = false;   // the walk needs more frames than a warp keeps
         for (int base = 0; !done; base += 32) {
-            if (base >= P.handoff || deep) {
+            if (base >= P.handoff || deep || long_chain) {
                 int slot_q = 0;
                 if (lane == 0) slot_q = atomicAdd(chain_count, 1);
                 slot_q = __shfl_sync(0xffffffffu, slot_q, 0);
@@ -450,18 +463,34 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
 #define PH2_NPT 8
 #define PH2_BATCH (PH2_THREADS * PH2_NPT)
 
-// Phase 2: a block per long chain. Each batch draws PH2_BATCH consecutive
-// nodes in parallel. While every pending node has sign +1 and the batch has
-// no negative g, the walk reduces to counts: pending_v = pending - 1 + n_v
-// per node, the chain ends at the first node where pending reaches 0, and
-// the estimate adds g_v / B for the nodes up to there -- a block prefix sum.
-// Otherwise one thread replays the exact sequential walk over the batch.
+// Phase 2: a block per long chain. Each batch draws nb = 256 * npt
+// consecutive nodes in parallel, npt in {1, 2, 4, 8} sized from the entry's
+// expected chain length so that little is drawn past the chain's end. The
+// nodes are evaluated grouped by the branch their first uniforms select
+// (mixture component, side of the lens), so that whole warps trace alike;
+// the walk still consumes them in pre-order. While every pending node has
+// sign +1 and the batch has no negative g, the walk reduces to counts:
+// pending_v = pending - 1 + n_v per node, the chain ends at the first node
+// where pending reaches 0, and the estimate adds g_v / B for the nodes up to
+// there -- a block prefix sum. Otherwise one thread replays the exact
+// sequential walk over the batch.
+
+// the branch of entry_ratio a node takes before its first ray: 0 / 1 trace
+// from y_{s-1} on the front / back side, 2 the first component when u = 1
+__device__ __forceinline__ int node_branch(const DScene &S, const Entry &E, Rng &R) {
+    if (E.u == 1 && R.u(0) < 0.5f) return 2;
+    return (S.mats[E.Y.mat].kind == MK_DIELECTRIC && !(R.u(19) < 0.5f)) ? 1 : 0;
+}
+
 template <bool COUNT>
 __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T, KParams P, Pool B, int slots,
                                                             uint32_t iter_base) {
     iter_base = eff_iter(P, iter_base);
     __shared__ float sg[PH2_BATCH];
     __shared__ int sn[PH2_BATCH];
+    __shared__ uint8_t skey[PH2_BATCH];
+    __shared__ int16_t sperm[PH2_BATCH];
+    __shared__ int s_cnt[4];
     __shared__ int s_item, s_done, s_end, s_neg;
     __shared__ double s_sum;
     __shared__ int s_pending[PH2_THREADS];
@@ -482,13 +511,47 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
         int Sp, C;
         Entry E = load_entry(S, P, B, slot, k, Sp, C);
         float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
+        // nodes per thread: about half the expected chain length per batch
+        const float mu = B.eMu[(size_t)slot * B.ML + k];
+        int npt = PH2_NPT;
+        if (mu > 0.0f) {
+            npt = 1;
+            while (npt < PH2_NPT && (float)(PH2_THREADS * npt) < 0.5f * mu) npt <<= 1;
+        }
+        const int nb = PH2_THREADS * npt;
         bool trunc = false;
         int done = 0;
         while (!done) {
             int base = st.next;
-            // draw the batch
-            for (int j = 0; j < PH2_NPT; ++j) {
-                int idx = tid * PH2_NPT + j;
+            // group the batch by branch: counting sort of node indices
+            if (tid < 4) s_cnt[tid] = 0;
+            __syncthreads();
+            for (int j = 0; j < npt; ++j) {
+                int idx = tid * npt + j;
+                Rng R;
+                R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)(base + idx));
+                int key = node_branch(S, E, R);
+                skey[idx] = (uint8_t)key;
+                atomicAdd(&s_cnt[key], 1);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int acc = 0;
+                for (int q = 0; q < 4; ++q) {
+                    int c = s_cnt[q];
+                    s_cnt[q] = acc;
+                    acc += c;
+                }
+            }
+            __syncthreads();
+            for (int j = 0; j < npt; ++j) {
+                int idx = tid * npt + j;
+                sperm[atomicAdd(&s_cnt[skey[idx]], 1)] = (int16_t)idx;
+            }
+            __syncthreads();
+            // draw the batch: at step j the block evaluates sorted positions j*256 .. j*256+255
+            for (int j = 0; j < npt; ++j) {
+                int idx = sperm[j * PH2_THREADS + tid];
                 int v = base + idx;
                 float g = 1.0f;
                 int nch = 0;
@@ -512,16 +575,17 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
             __syncthreads();
             // any negative g in the batch?
             int anyneg = 0;
-            for (int j = 0; j < PH2_NPT; ++j) anyneg |= (sg[tid * PH2_NPT + j] < 0.0f);
+            for (int j = 0; j < npt; ++j) anyneg |= (sg[tid * npt + j] < 0.0f);
             anyneg = __syncthreads_or(anyneg | s_neg);
-            if (!anyneg && base + PH2_BATCH <= P.trial_cap) {
+            if (!anyneg && base + nb <= P.trial_cap) {
                 // parallel walk: pending counts by a block prefix sum
                 int pend0 = 1;
                 for (int i = 0; i < st.sp; ++i) pend0 += st.fr_rem[i];
                 int loc[PH2_NPT];
                 int acc = 0;
+#pragma unroll
                 for (int j = 0; j < PH2_NPT; ++j) {
-                    acc += sn[tid * PH2_NPT + j] - 1;
+                    if (j < npt) acc += sn[tid * npt + j] - 1;
                     loc[j] = acc;
                 }
                 s_pending[tid] = acc;
@@ -533,21 +597,19 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
                     __syncthreads();
                 }
                 int excl = pend0 + s_pending[tid] - acc;
-                int first = PH2_BATCH;
-                for (int j = 0; j < PH2_NPT; ++j)
-                    if (excl + loc[j] <= 0) {
-                        first = tid * PH2_NPT + j;
-                        break;
-                    }
-                if (tid == 0) s_end = PH2_BATCH;
+                int first = nb;
+#pragma unroll
+                for (int j = PH2_NPT - 1; j >= 0; --j)
+                    if (j < npt && excl + loc[j] <= 0) first = tid * npt + j;
+                if (tid == 0) s_end = nb;
                 __syncthreads();
-                if (first < PH2_BATCH) atomicMin(&s_end, first);
+                if (first < nb) atomicMin(&s_end, first);
                 __syncthreads();
-                int end = s_end;   // last node processed (inclusive), or PH2_BATCH if none
+                int end = s_end;   // last node processed (inclusive), or nb if none
                 double part = 0.0;
-                for (int j = 0; j < PH2_NPT; ++j) {
-                    int idx = tid * PH2_NPT + j;
-                    if (idx <= end && idx < PH2_BATCH) part += (double)(sg[idx] * invB);
+                for (int j = 0; j < npt; ++j) {
+                    int idx = tid * npt + j;
+                    if (idx <= end && idx < nb) part += (double)(sg[idx] * invB);
                 }
                 s_part[tid] = part;
                 __syncthreads();
@@ -557,12 +619,12 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
                 }
                 if (tid == 0) {
                     st.sum_t += s_part[0];
-                    if (end < PH2_BATCH) {
+                    if (end < nb) {
                         st.next = base + end + 1;
                         s_done = 1;
                     } else {
                         int pend = pend0 + s_pending[PH2_THREADS - 1];
-                        st.next = base + PH2_BATCH;
+                        st.next = base + nb;
                         st.cur_sign = 1.0f;
                         st.sp = 0;
                         if (pend - 1 > 0) {
@@ -576,7 +638,7 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
             } else if (tid == 0) {
                 // exact sequential walk over the batch
                 s_done = 0;
-                for (int j = 0; j < PH2_BATCH; ++j) {
+                for (int j = 0; j < nb; ++j) {
                     int v = base + j;
                     if (v >= P.trial_cap) {
                         s_done = 1;
