@@ -121,6 +121,10 @@ typedef struct {
      * eager path. The cache is dropped when the scene, the tables or the
      * buffers it points to change. */
     int graph;
+    /* Supporting distribution (Sec. 5.3): share of the cosine draws at a
+     * dielectric y_{s-1} that go to the side of the dropped vertex y_{s-2}
+     * (0: 0.5, an even split; must be < 1 so that q covers both sides). */
+    float side_in;
 } pb_config;
 
 typedef struct {
@@ -254,7 +258,8 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
  * contexts or streams at once) race on it. The call is synchronous.
  *
  * Device inputs (caller-owned): d_tri[2n] (y_{s-1} triangle, h_c triangle),
- * d_bary[4n] (their barycentrics), d_info[n] (u | type << 3, type 1 = L D S^u),
+ * d_bary[4n] (their barycentrics), d_info[n] (u | type << 3 | back << 30, type 1 =
+ * L D S^u, back 1 when y_{s-2} lies behind y_{s-1}'s normal),
  * d_B[n] (bound B > 0 per entry). Device outputs: d_rhat[n], d_nodes[n] (total
  * estimator nodes over the repeats, may be NULL). *n_truncated (may be NULL)
  * counts entries with a repeat that hit trial_cap. Only cfg->seed, repeats

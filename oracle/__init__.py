@@ -55,7 +55,7 @@ class TablesDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("max_depth", C.c_int), ("M", C.c_int), ("M_p", C.c_int),
                 ("repeats", C.c_int), ("proxy", C.c_int), ("trial_cap", C.c_int), ("conn", C.c_int),
-                ("pilot_min", C.c_int), ("pilot_max", C.c_int)]
+                ("pilot_min", C.c_int), ("pilot_max", C.c_int), ("side_in", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -68,7 +68,8 @@ class Stats(C.Structure):
 
 class Entry(C.Structure):
     _fields_ = [("y_tri", C.c_int), ("y_b1", C.c_double), ("y_b2", C.c_double), ("u", C.c_int),
-                ("type", C.c_int), ("h_tri", C.c_int), ("h_b1", C.c_double), ("h_b2", C.c_double)]
+                ("type", C.c_int), ("h_tri", C.c_int), ("h_b1", C.c_double), ("h_b2", C.c_double),
+                ("back", C.c_int), ("side_in", C.c_double)]
 
 
 _lib = None
@@ -257,9 +258,10 @@ class Oracle:
 
 
 def params(seed=7, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, trial_cap=1 << 16, conn=1, pilot_min=64,
-           pilot_max=1024):
-    """pilot_max = 0 turns the per-entry pilot off (B from the learned table)."""
-    return Params(seed, max_depth, M, M_p, repeats, proxy, trial_cap, conn, pilot_min, pilot_max)
+           pilot_max=1024, side_in=0.0):
+    """pilot_max = 0 turns the per-entry pilot off (B from the learned table);
+    side_in = 0 is an even split of the cosine draws at dielectric vertices."""
+    return Params(seed, max_depth, M, M_p, repeats, proxy, trial_cap, conn, pilot_min, pilot_max, side_in)
 
 
 def philox(ctr, key):

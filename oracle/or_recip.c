@@ -125,6 +125,9 @@ typedef struct {
     const or_scene_t *s;
     or_vtx Y, H;
     int u, type;        /* type 0: L S^u, 1: L D S^u */
+    int back;           /* y_{s-2} lies behind Y's normal */
+    double pin;         /* share of the cosine draws at a dielectric Y toward y_{s-2}; the rest
+                         * go to the other side, so q stays positive wherever f can be */
     uint32_t seed, kind, a, b;
     double last_f, last_q;
 } entry_ctx;
@@ -154,21 +157,21 @@ double or_fwd_density(const or_scene_t *s, const or_vtx *ys, int j) {
 }
 
 /* cosine density at the specular vertex Y: conductors use their front
- * hemisphere; dielectrics both, each with probability 1/2. */
-static double cosY_pdf(const or_scene_t *s, const or_vtx *Y, v3 w) {
+ * hemisphere; dielectrics both, the side of y_{s-2} with probability pin. */
+static double cosY_pdf(const or_scene_t *s, const or_vtx *Y, v3 w, int back, double pin) {
     const or_mat *m = &s->mats[Y->mat];
     double c = vdot(Y->n, w);
-    if (m->kind == MK_DIELECTRIC) return fabs(c) / (2.0 * M_PI);
+    if (m->kind == MK_DIELECTRIC) return (((c < 0.0) == (back != 0)) ? pin : 1.0 - pin) * fabs(c) / M_PI;
     return c > 0.0 ? c / M_PI : 0.0;
 }
 
 /* density that tracing from Y produces g_1..g_u (ys ordered light-first) */
-static double q_from_Y(const or_scene_t *s, const or_vtx *gs, int u, const or_vtx *Y) {
+static double q_from_Y(const or_scene_t *s, const or_vtx *gs, int u, const or_vtx *Y, int back, double pin) {
     /* gs[0] = Y, gs[r] = r-th retraced vertex */
     v3 d = vsub(gs[1].p, Y->p);
     double d2 = vdot(d, d);
     v3 w = vscale(d, 1.0 / sqrt(d2));
-    double q = cosY_pdf(s, Y, w) * fabs(vdot(gs[1].n, w)) / d2;
+    double q = cosY_pdf(s, Y, w, back, pin) * fabs(vdot(gs[1].n, w)) / d2;
     for (int r = 1; r < u; ++r) {
         const or_mat *m = &s->mats[gs[r].mat];
         v3 dd = vsub(gs[r + 1].p, gs[r].p);
@@ -205,7 +208,7 @@ static void eval_fq(const entry_ctx *e, const or_vtx *gs, double *f, double *q, 
         fv = 1.0;
         for (int j = (e->type == 1 ? 1 : 0); j < n; ++j) fv *= or_fwd_density(s, ys, j);
     }
-    double qB = vis_extra || !comp_A ? q_from_Y(s, gs, u, &e->Y) : 0.0;
+    double qB = vis_extra || !comp_A ? q_from_Y(s, gs, u, &e->Y, e->back, e->pin) : 0.0;
     double qv = qB;
     if (u == 1) {
         double qA;
@@ -269,7 +272,10 @@ static double entry_ratio(void *c, uint32_t node) {
     /* trace from Y */
     const or_mat *mY = &s->mats[e->Y.mat];
     v3 nside = e->Y.n;
-    if (mY->kind == MK_DIELECTRIC && !(R(e, node, 19) < 0.5)) nside = vneg(nside);
+    if (mY->kind == MK_DIELECTRIC) {
+        v3 nin = e->back ? vneg(e->Y.n) : e->Y.n;   /* toward y_{s-2} */
+        nside = R(e, node, 19) < e->pin ? nin : vneg(nin);
+    }
     v3 w = or_cosine_dir(nside, R(e, node, 4), R(e, node, 5));
     if (!trace_vertex(s, e->Y.p, w, e->Y.tri, &gs[1])) return 0.0;
     for (int r = 1; r < u; ++r) {
@@ -302,6 +308,8 @@ static void entry_setup(entry_ctx *e, const or_scene_t *s, const or_entry *en) {
     e->Y = or_vertex_at(s, en->y_tri, en->y_b1, en->y_b2);
     e->u = en->u;
     e->type = en->type;
+    e->back = en->back;
+    e->pin = en->side_in > 0.0 ? en->side_in : 0.5;
     if (en->type == 1) {
         e->H = or_vertex_at(s, en->h_tri, en->h_b1, en->h_b2);
         e->H.is_light = 1;

@@ -238,6 +238,8 @@ static int collect_entries(const or_scene_t *s, const or_params *p, const or_lpa
                 E->u = u;
                 E->type = (j == 1);
                 E->h_tri = lp[l].v[0].tri; E->h_b1 = lp[l].v[0].b1; E->h_b2 = lp[l].v[0].b2;
+                E->back = vdot(lp[l].v[e].n, vsub(lp[l].v[e - 1].p, lp[l].v[e].p)) < 0.0;
+                E->side_in = p->side_in;
                 if (ol) ol[n] = l;
                 if (oe) oe[n] = e;
             }

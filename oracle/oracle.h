@@ -62,6 +62,7 @@ typedef struct {
     int conn;          /* subspace connection strategy on/off */
     int pilot_min;     /* pilot draws per entry for its B, at least (rounded up to 32) */
     int pilot_max;     /* at most; 0 = no pilot (B from the table) */
+    double side_in;    /* cosine draws at a dielectric y_{s-1} toward y_{s-2} (0: 0.5) */
 } or_params;
 
 typedef struct {
@@ -102,6 +103,8 @@ typedef struct {
     int u;                              /* trailing specular count 1..4 */
     int type;                           /* 0: L S^u (no control vertex), 1: L D S^u (h_c = y_0) */
     int h_tri; double h_b1, h_b2;       /* control vertex h_c = y_0 (type 1) */
+    int back;                           /* y_{s-2} lies behind y_{s-1}'s normal */
+    double side_in;                     /* cosine draws at a dielectric y_{s-1} toward y_{s-2} (0: 0.5) */
 } or_entry;
 
 /* f and q of n proxy-path samples drawn from the supporting distribution of

@@ -128,6 +128,7 @@ pb_status check_cfg(pb_ctx *ctx, const pb_config *c) {
     if (c->trial_cap < 1) return fail(ctx, PB_ERR_ARG, "trial_cap must be positive");
     if (c->spp < 0) return fail(ctx, PB_ERR_ARG, "spp must be >= 0");
     if (c->proposal < 0 || c->proposal > 1) return fail(ctx, PB_ERR_ARG, "proposal must be 0 (table) or 1 (learned)");
+    if (!(c->side_in >= 0.0f && c->side_in < 1.0f)) return fail(ctx, PB_ERR_ARG, "side_in must lie in [0, 1)");
     return PB_OK;
 }
 
@@ -154,6 +155,7 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
         P.pilot_min = lo;
         P.pilot_max = hi;
     }
+    P.side_in = c->side_in > 0.0f ? c->side_in : 0.5f;
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
     P.smp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};

@@ -33,20 +33,24 @@ __device__ __forceinline__ float fwd_density(const DScene &S, const Vtx *ys, int
 struct Entry {
     Vtx Y, H;
     int u, type;
+    int back;     // y_{s-2} lies behind Y's normal
+    float pin;    // share of the cosine draws at a dielectric Y on the side of y_{s-2}
 };
 
-__device__ __forceinline__ float cosY_pdf(const DScene &S, const Vtx &Y, float3 w) {
+// cosine density at Y: conductors use their front hemisphere, dielectrics
+// both, the side of y_{s-2} with probability pin
+__device__ __forceinline__ float cosY_pdf(const DScene &S, const Vtx &Y, float3 w, int back, float pin) {
     const DMat &m = S.mats[Y.mat];
     float c = dot(Y.n, w);
-    if (m.kind == MK_DIELECTRIC) return fabsf(c) / (2.0f * PB_PI);
+    if (m.kind == MK_DIELECTRIC) return (((c < 0.0f) == (back != 0)) ? pin : 1.0f - pin) * fabsf(c) / PB_PI;
     return c > 0.0f ? c / PB_PI : 0.0f;
 }
 
-__device__ __forceinline__ float q_from_Y(const DScene &S, const Vtx *gs, int u) {
+__device__ __forceinline__ float q_from_Y(const DScene &S, const Vtx *gs, int u, int back, float pin) {
     float3 d = gs[1].p - gs[0].p;
     float d2 = len2(d);
     float3 w = d * (1.0f / sqrtf(d2));
-    float q = cosY_pdf(S, gs[0], w) * fabsf(dot(gs[1].n, w)) / d2;
+    float q = cosY_pdf(S, gs[0], w, back, pin) * fabsf(dot(gs[1].n, w)) / d2;
     for (int r = 1; r < u; ++r) {
         const DMat &m = S.mats[gs[r].mat];
         float3 dd = gs[r + 1].p - gs[r].p;
@@ -77,7 +81,7 @@ __device__ __forceinline__ void eval_fq(const DScene &S, const Entry &E, const V
         fv = 1.0f;
         for (int j = (E.type == 1 ? 1 : 0); j < n; ++j) fv *= fwd_density(S, ys, j);
     }
-    float qB = (vis || !compA) ? q_from_Y(S, gs, u) : 0.0f;
+    float qB = (vis || !compA) ? q_from_Y(S, gs, u, E.back, E.pin) : 0.0f;
     float qv = qB;
     if (u == 1) {
         float qA;
@@ -137,7 +141,10 @@ __device__ __forceinline__ float entry_ratio(const DScene &S, const Entry &E, Rn
     }
     const DMat &mY = S.mats[E.Y.mat];
     float3 nside = E.Y.n;
-    if (mY.kind == MK_DIELECTRIC && !(R.u(19) < 0.5f)) nside = -nside;
+    if (mY.kind == MK_DIELECTRIC) {
+        float3 nin = E.back ? -E.Y.n : E.Y.n;   // toward y_{s-2}
+        nside = R.u(19) < E.pin ? nin : -nin;
+    }
     float3 w = cosine_dir(nside, R.u(4), R.u(5));
     if (!trace_vtx<COUNT>(S, E.Y.p, w, E.Y.tri, gs[1], tc, E.type == 0 && u == 1)) return 0.0f;
     for (int r = 1; r < u; ++r) {

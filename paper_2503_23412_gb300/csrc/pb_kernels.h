@@ -51,6 +51,7 @@ struct KParams {
     int count;      // 1: count traversal work (node fetches, triangle tests, rays)
     int handoff;    // estimator nodes walked by a warp before a block continues the chain
     int pilot_min, pilot_max;   // per-entry B pilot draws (multiples of 32; pilot_max 0 = off)
+    float side_in;              // cosine draws at a dielectric y_{s-1} on the side of y_{s-2}
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
     SampleSink smp;         // raw != nullptr: record proposal training samples

@@ -179,6 +179,9 @@ __global__ void k_bsample(DScene S, DTables T, KParams P, Pool B, int slots, uin
     E.H = H;
     E.u = u;
     E.type = type;
+    Vtx Yp = vertex_at(S, B.gtri[gb + e - 1], B.gbary[gb + e - 1].x, B.gbary[gb + e - 1].y);
+    E.back = dot(Y.n, Yp.p - Y.p) < 0.0f ? 1 : 0;
+    E.pin = P.side_in;
     float r = entry_ratio(S, E, R);
     if (r > 0.0f) {
         atomicMax(&cell_max[((u - 1) * T.KSp + Sp) * (T.KC + 1) + C], __float_as_uint(r));

@@ -276,6 +276,9 @@ __device__ __forceinline__ Entry load_entry(const DScene &S, const KParams &P, c
     Entry E;
     E.Y = vertex_at(S, B.gtri[gb + e], B.gbary[gb + e].x, B.gbary[gb + e].y);
     E.H = vertex_at(S, B.gtri[gb], B.gbary[gb].x, B.gbary[gb].y);
+    Vtx Yp = vertex_at(S, B.gtri[gb + e - 1], B.gbary[gb + e - 1].x, B.gbary[gb + e - 1].y);
+    E.back = dot(E.Y.n, Yp.p - E.Y.p) < 0.0f ? 1 : 0;
+    E.pin = P.side_in;
     int info = B.einfo[o + fixed];
     E.u = info & 7;
     E.type = (info >> 3) & 1;
@@ -476,10 +479,11 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
 // sequential walk over the batch.
 
 // the branch of entry_ratio a node takes before its first ray: 0 / 1 trace
-// from y_{s-1} on the front / back side, 2 the first component when u = 1
+// from y_{s-1} toward the side of y_{s-2} / the other side, 2 the first
+// component when u = 1
 __device__ __forceinline__ int node_branch(const DScene &S, const Entry &E, Rng &R) {
     if (E.u == 1 && R.u(0) < 0.5f) return 2;
-    return (S.mats[E.Y.mat].kind == MK_DIELECTRIC && !(R.u(19) < 0.5f)) ? 1 : 0;
+    return (S.mats[E.Y.mat].kind == MK_DIELECTRIC && !(R.u(19) < E.pin)) ? 1 : 0;
 }
 
 template <bool COUNT>

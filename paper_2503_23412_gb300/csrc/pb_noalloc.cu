@@ -56,6 +56,8 @@ __global__ void __launch_bounds__(128) k_na_recip(DScene S, KParams P, uint32_t 
         E.H = vertex_at(S, tri[2 * k + 1], bary[4 * k + 2], bary[4 * k + 3]);
         E.u = info[k] & 7;
         E.type = (info[k] >> 3) & 1;
+        E.back = (info[k] >> 30) & 1;
+        E.pin = P.side_in;
         float invB = 1.0f / Bv[k];
         double sum_t = 0.0;
         int nodes = 0;

@@ -427,18 +427,22 @@ def random_tables(scene, seed=5, KT=32, KS=32, KSp=16, KC=4, tile=10, B=1.0, mis
     )
 
 
-def pin_square_light(a=0.1, h=0.5, spec_size=1e-3, rough=0.1):
+def pin_square_light(a=0.1, h=0.5, spec_size=1e-3, rough=0.1, dielectric=False, flip=False):
     """A square emitter (half-size a, Le=1) at height h facing down over a tiny
-    GGX conductor triangle at the origin facing up; nothing else."""
+    GGX triangle at the origin (conductor, or dielectric of IOR 1.5) facing up
+    (down with `flip`); nothing else."""
     b = _Builder()
     light = b.add_material(material(LAMBERT, (0, 0, 0), Le=(1.0, 1.0, 1.0)))
-    spec = b.add_material(material(CONDUCTOR, (0.9, 0.9, 0.9), rough=rough))
+    if dielectric:
+        spec = b.add_material(material(DIELECTRIC, (1, 1, 1), rough=rough, ior=1.5))
+    else:
+        spec = b.add_material(material(CONDUCTOR, (0.9, 0.9, 0.9), rough=rough))
     b.add_quad((0.0, h, 0.0), (a, 0, 0), (0, 0, a), (0, -1, 0), light)
     s = spec_size
     tri = np.array([[-s, 0, -s], [s, 0, -s], [0, 0, s]], np.float64)
     t = np.array([[0, 1, 2]])
     n = np.cross(tri[1] - tri[0], tri[2] - tri[0])
-    if n[1] < 0:
+    if (n[1] < 0) != flip:
         t = t[:, ::-1]
     b.add_mesh(tri, t, spec)
     cam = [0, 2, -2, 0, 0, 0, 0, 1, 0, 40.0, 4, 4]

@@ -205,6 +205,37 @@ def test_edge_configurations_match_oracle(N, kw):
     r.close()
 
 
+def test_estimator_with_side_weighted_lobe_matches_oracle(N):
+    """side_in = 0.9 (cosine draws at a dielectric y_{s-1} favour the side of
+    y_{s-2}): the device's estimates follow the oracle's node for node on a
+    lens scene, and the chains are shorter than with the even split."""
+    sc = scenes.projector(24, 24, lens_tris_per_cap=1500, flat=True)
+    o = O.Oracle(sc)
+    tab = learned(sc, o, M=1500, M_p=1500, max_depth=8)
+    r = N.Renderer(sc, tab)
+    td = o.tables(tab)
+    nodes = {}
+    for side in (0.0, 0.9):
+        p = O.params(M=1500, M_p=1500, max_depth=8, side_in=side)
+        cfg = N.config(M=1500, M_p=1500, max_depth=8, side_in=side)
+        n_ent = n_same = 0
+        tot = 0.0
+        for it in (3, 4):
+            tri, bary = o.light_pass(p, it)
+            ref = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0)
+            got = r.iteration(cfg, it, tri, bary)
+            es = ref["entry_sig"] == got["entry_sig"]
+            n_ent += len(es)
+            n_same += int(es.sum())
+            assert np.all(rel_close(ref["rhat"][es], got["rhat"][es], 1e-3))
+            assert np.array_equal(ref["entry_nodes"][es], got["entry_nodes"][es])
+            tot += float(ref["entry_nodes"].sum())
+        assert n_ent > 20 and n_same / n_ent >= 0.98
+        nodes[side] = tot
+    assert nodes[0.9] < nodes[0.0]
+    r.close()
+
+
 def test_bad_arguments_return_status(N):
     sc = scenes.caustic_mini(4, 4)
     r = N.Renderer(sc)

@@ -311,6 +311,32 @@ def test_reciprocal_of_incomplete_pdf_diffuse_control_vertex_quadrature():
     assert abs(t.mean() - 1 / P) < 4 * t.std() / math.sqrt(len(t)) + 2e-3 / P
 
 
+@pytest.mark.parametrize("flip", [False, True])
+def test_dielectric_vertex_side_weighted_lobe_is_unbiased(flip):
+    """u = 1 with y_{s-1} on a dielectric: P is the same closed form as for a
+    conductor (it holds only the light tracer's densities), for the vertex
+    facing the light or turned away from it. The cosine lobe puts 0.9 of the
+    draws on the side of y_{s-2} (here the light) and 0.1 on the other side,
+    so the estimate stays unbiased with the side flag right or wrong; with it
+    right the chains are shorter (fewer draws wasted on the far side)."""
+    a, h = 0.1, 0.5
+    sc = scenes.pin_square_light(a=a, h=h, dielectric=True, flip=flip)
+    o = O.Oracle(sc)
+    P = (1.0 / (4 * a * a)) * (1 / math.pi) * 4 * _corner(a, a, h)
+    nodes = {}
+    for back in (0, 1):
+        e = O.Entry(2, 1 / 3, 1 / 3, 1, 0, -1, 0.0, 0.0, back, 0.9)
+        f, q = o.entry_fq(e, 20000)
+        ratio = np.where(q > 0, f / np.where(q > 0, q, 1.0), 0.0)
+        assert abs(ratio.mean() - P) < 4 * ratio.std() / math.sqrt(len(ratio))
+        t, i, nn, tr = o.entry_recip(e, B=1.05 * ratio.max(), n=30000)
+        assert tr == 0
+        assert abs(t.mean() - 1 / P) < 4 * t.std() / math.sqrt(len(t))
+        nodes[back] = nn.mean()
+    right = 1 if flip else 0
+    assert nodes[right] < nodes[1 - right]
+
+
 @pytest.mark.parametrize("scene", ["square", "floor"])
 def test_pilot_bound_keeps_incomplete_pdf_estimate_unbiased(scene):
     """The per-entry bound B is the largest f/q of a pilot on a stream the

@@ -48,7 +48,7 @@ def test_noalloc_estimates_match_pooled_estimator():
     dev = torch.device("cuda", 0)
     d_tri = torch.tensor([[e.y_tri, e.h_tri] for e in ents], dtype=torch.int32, device=dev)
     d_bary = torch.tensor([[e.y_b1, e.y_b2, e.h_b1, e.h_b2] for e in ents], dtype=torch.float32, device=dev)
-    d_info = torch.tensor([e.u | (e.type << 3) for e in ents], dtype=torch.int32, device=dev)
+    d_info = torch.tensor([e.u | (e.type << 3) | (e.back << 30) for e in ents], dtype=torch.int32, device=dev)
     d_B = torch.full((n,), 1.5 * mx, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
     for call in range(2):
