@@ -318,7 +318,7 @@ def run_batch(args):
                       "paths_per_step": paths, "sequential_eager_ms": seq_ms,
                       "sequential_eager_mpaths": paths / (seq_ms * 1e-3) / 1e6,
                       "speedup_vs_sequential": seq_ms / batch_ms, "setup_s": setup_s, "autotuned_buckets": tuned,
-                      "tuned": [{"batch": c.batch, "handoff": c.chain_handoff} for c in cfgs]}}
+                      "tuned": [{"batch": c.batch, "estimator": c.estimator} for c in cfgs]}}
     print(json.dumps(out))
     for r in rs:
         r.close()

@@ -125,6 +125,11 @@ typedef struct {
      * dielectric y_{s-1} that go to the side of the dropped vertex y_{s-2}
      * (0: 0.5, an even split; must be < 1 so that q covers both sides). */
     float side_in;
+    /* Reciprocal-estimator schedule; the estimates are the same either way:
+     * 0 = wavefront (all chains' node windows evaluated in stages, ray queries
+     * answered by traversal-only kernels, then a warp walk per chain);
+     * 1 = a warp phase then a block phase per chain. */
+    int estimator;
 } pb_config;
 
 typedef struct {
@@ -163,13 +168,13 @@ pb_status pb_render_batch(pb_ctx *const *ctxs, const pb_config *cfgs, int n, pb_
 
 /* Autotuner: times trial renders of trial_iters iterations (0: 32; never
  * added to the film) over iterations in flight {4, 8, 16, 32} x estimator
- * hand-off {256, 512, 1024} and writes cfg with the fastest pair into
- * *best. Results are cached per size bucket (log2 of the triangle and
+ * schedule {wavefront, warp/block phases} and writes cfg with the fastest
+ * pair into *best. Results are cached per size bucket (log2 of the triangle and
  * pixel counts, depth, M, M_p, repeats, proposal, proxy) for the process;
  * *from_cache (may be NULL) tells whether the cache answered. Neither
  * parameter changes an image beyond the estimator's summation order. */
 pb_status pb_autotune(pb_ctx *ctx, const pb_config *cfg, int trial_iters, pb_config *best, int *from_cache);
-/* the cache as text lines "bucket batch handoff ms_per_iteration" */
+/* the cache as text lines "bucket batch estimator ms_per_iteration" */
 pb_status pb_autotune_cache_save(const char *path);
 pb_status pb_autotune_cache_load(const char *path);
 void pb_autotune_cache_clear(void);

@@ -129,6 +129,7 @@ pb_status check_cfg(pb_ctx *ctx, const pb_config *c) {
     if (c->spp < 0) return fail(ctx, PB_ERR_ARG, "spp must be >= 0");
     if (c->proposal < 0 || c->proposal > 1) return fail(ctx, PB_ERR_ARG, "proposal must be 0 (table) or 1 (learned)");
     if (!(c->side_in >= 0.0f && c->side_in < 1.0f)) return fail(ctx, PB_ERR_ARG, "side_in must lie in [0, 1)");
+    if (c->estimator < 0 || c->estimator > 1) return fail(ctx, PB_ERR_ARG, "estimator must be 0 or 1");
     return PB_OK;
 }
 
@@ -156,6 +157,7 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
         P.pilot_max = hi;
     }
     P.side_in = c->side_in > 0.0f ? c->side_in : 0.5f;
+    P.estimator = c->estimator;
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
     P.smp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
@@ -167,7 +169,7 @@ pb_status run_wave(pb_ctx *ctx, const KParams &P, int slots, uint32_t iter_base,
                    uint32_t *sig) {
     if (with_light) launch_light_pass(ctx->S, P, ctx->B, slots, iter_base, ctx->stream);
     launch_pool_build(ctx->S, ctx->T, P, ctx->B, slots, ctx->stream);
-    if (with_recip) launch_recip(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->num_sms, ctx->stream);
+    if (with_recip) launch_recip(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->num_sms, ctx->stream, &ctx->wf);
     launch_eye(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->Lbuf, sig, ctx->stream);
     CK(cudaGetLastError());
     return PB_OK;
@@ -312,6 +314,7 @@ void pb_destroy(pb_ctx *ctx) {
     free_all(ctx->table_mem);
     free_graphs(ctx);
     free_all(ctx->pool_mem);
+    free_all(ctx->wf_mem);
     mlp_free(ctx);
     if (ctx->d_iter0) cudaFree(ctx->d_iter0);
     if (ctx->film) cudaFree(ctx->film);
@@ -554,9 +557,10 @@ pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t
     KParams P = kparams(ctx, cfg);
     pb_status s = ensure_pool(ctx, slots, P.M * P.L, P.repeats, P.npix);
     if (s != PB_OK) return s;
+    if (cfg->estimator == 0 && (s = wf_ensure(ctx)) != PB_OK) return s;
     launch_light_pass(ctx->S, P, ctx->B, slots, iter_base, ctx->stream);
     launch_pool_build(ctx->S, ctx->T, P, ctx->B, slots, ctx->stream);
-    launch_recip(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->num_sms, ctx->stream);
+    launch_recip(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->num_sms, ctx->stream, &ctx->wf);
     if (cfg->proposal) {
         s = mlp_wave(ctx, P, slots, iter_base);
         if (s != PB_OK) return s;
@@ -571,6 +575,52 @@ pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t
 extern "C" {
 
 }  // extern "C"
+
+// ---- wavefront estimator buffers ------------------------------------------------
+constexpr int WF_NODE_CAP = 1 << 23;   // nodes per round (about 1 GB of state)
+
+pb_status wf_ensure(pb_ctx *ctx) {
+    const int chains = ctx->B.chain_cap;
+    if (ctx->wf_chain_cap >= chains && ctx->wf.node_cap == WF_NODE_CAP) return PB_OK;
+    free_graphs(ctx);
+    free_all(ctx->wf_mem);
+    WfBufs &W = ctx->wf;
+    W = WfBufs{};
+    auto &o = ctx->wf_mem;
+    const size_t nc = (size_t)std::max(chains, 1), nn = (size_t)WF_NODE_CAP;
+    CK(dalloc(o, &W.ch_w, nc));
+    CK(dalloc(o, &W.ch_off, nc));
+    CK(dalloc(o, &W.ch_win, nc));
+    CK(dalloc(o, &W.ch_done, nc));
+    CK(dalloc(o, &W.node_chain, nn));
+    CK(dalloc(o, &W.node_v, nn));
+    CK(dalloc(o, &W.node_nq, nn));
+    CK(dalloc(o, &W.node_res, 5 * nn));
+    CK(dalloc(o, &W.node_q, nn));
+    CK(dalloc(o, &W.node_g, nn));
+    CK(dalloc(o, &W.node_n, nn));
+    CK(dalloc(o, &W.list[0], nn));
+    CK(dalloc(o, &W.list[1], nn));
+    CK(dalloc(o, &W.ctl, (size_t)16));
+    CK(cudaMemsetAsync(W.ctl, 0, 16 * sizeof(int32_t), ctx->stream));
+    W.node_cap = WF_NODE_CAP;
+    ctx->wf_chain_cap = chains;
+    return PB_OK;
+}
+
+// errors of the last wavefront wave (ctl[3]: low byte = error code)
+pb_status wf_check(pb_ctx *ctx) {
+    if (!ctx->wf.ctl) return PB_OK;
+    int32_t e = 0;
+    CK(cudaMemcpyAsync(&e, ctx->wf.ctl + 3, sizeof(e), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (e & 0xFF) {
+        CK(cudaMemsetAsync(ctx->wf.ctl + 3, 0, sizeof(e), ctx->stream));
+        return fail(ctx, PB_ERR_STATE, (e & 0xFF) == 1 ? "wavefront estimator: more estimates in flight than chain slots"
+                                                        : "wavefront estimator: a node asked for more queries than u allows");
+    }
+    return PB_OK;
+}
 
 // ---- render: prepare, enqueue (eager or captured), finish ---------------------
 constexpr int NEV = 6;   // per wave: light | pool | estimator | proposal | eye | end
@@ -590,6 +640,10 @@ static pb_status prepare_render(pb_ctx *ctx, const pb_config *cfg, KParams &P, i
     if (s != PB_OK) return s;
     if (cfg->proposal) {
         s = mlp_prepare(ctx, slots, P.max_depth);
+        if (s != PB_OK) return s;
+    }
+    if (cfg->estimator == 0) {
+        s = wf_ensure(ctx);
         if (s != PB_OK) return s;
     }
     if (!ctx->d_iter0) CK(cudaMalloc(&ctx->d_iter0, sizeof(uint32_t)));
@@ -616,7 +670,7 @@ static pb_status enqueue_render(pb_ctx *ctx, const pb_config *cfg, const KParams
         CK(cudaEventRecordWithFlags(e[1], st, evf));
         launch_pool_build(ctx->S, ctx->T, P, ctx->B, ns, st);
         CK(cudaEventRecordWithFlags(e[2], st, evf));
-        launch_recip(ctx->S, ctx->T, P, ctx->B, ns, base, ctx->num_sms, st);
+        launch_recip(ctx->S, ctx->T, P, ctx->B, ns, base, ctx->num_sms, st, &ctx->wf);
         CK(cudaEventRecordWithFlags(e[3], st, evf));
         KParams Pw = P;
         if (cfg->proposal) {
@@ -667,10 +721,18 @@ static pb_status finish_render(pb_ctx *ctx, const pb_config *cfg, const KParams 
         st.ms_eye += d;
     }
     st.n_waves = waves;
-    // light, pool, bucket, cdf, offsets, pilot, recip x2, finish, eye, film; proposal: feature pass, network
-    st.n_launches = (11 + (cfg->proposal ? 2 : 0)) * (int64_t)waves;
+    // per wave: light, pool build, bucket, cdf, eye, film (6); the estimator:
+    // warp/block phases = offsets, pilot, two phases, finish (5); wavefront =
+    // offsets, pilot, init, rounds x (plan, nodes, steps, traces, walk),
+    // finisher, finish; the learned proposal adds its feature pass and network
+    const int64_t est = cfg->estimator == 1 ? 5 : 5 + (int64_t)WF_ROUNDS * (3 + 2 * WF_MAXQ + 1);
+    st.n_launches = (6 + est + (cfg->proposal ? 2 : 0)) * (int64_t)waves;
     if (cfg->proposal) {
         pb_status s = mlp_check_err(ctx);
+        if (s != PB_OK) return s;
+    }
+    if (cfg->estimator == 0) {
+        pb_status s = wf_check(ctx);
         if (s != PB_OK) return s;
     }
     read_counters(ctx, &st);
@@ -741,7 +803,7 @@ void free_graphs(pb_ctx *ctx) {
 
 // ---- autotuning: iterations in flight x estimator hand-off per size bucket ----
 struct TuneEntry {
-    int batch, handoff;
+    int batch, estimator;
     double ms_per_iter;
 };
 static std::mutex g_tune_mutex;
@@ -874,7 +936,7 @@ pb_status pb_autotune(pb_ctx *ctx, const pb_config *cfg, int trial_iters, pb_con
         if (it != g_tune.end()) {
             *best = *cfg;
             best->batch = it->second.batch;
-            best->chain_handoff = it->second.handoff;
+            best->estimator = it->second.estimator;
             if (from_cache) *from_cache = 1;
             return PB_OK;
         }
@@ -882,16 +944,16 @@ pb_status pb_autotune(pb_ctx *ctx, const pb_config *cfg, int trial_iters, pb_con
     if (from_cache) *from_cache = 0;
     int n = trial_iters > 0 ? trial_iters : 32;
     const int batches[] = {4, 8, 16, 32};
-    const int handoffs[] = {256, 512, 1024};
+    const int schedules[] = {0, 1};   // wavefront, warp/block phases
     TuneEntry bestE{0, 0, 1e300};
     std::vector<cudaEvent_t> ev;
     bool warmed = false;
     for (int b : batches) {
         if (b > n) continue;
-        for (int h : handoffs) {
+        for (int h : schedules) {
             pb_config c = *cfg;
             c.batch = b;
-            c.chain_handoff = h;
+            c.estimator = h;
             c.spp = n;
             c.iter0 = (1 << 28) + 7919;   // iterations no render uses
             c.graph = 0;
@@ -924,7 +986,7 @@ pb_status pb_autotune(pb_ctx *ctx, const pb_config *cfg, int trial_iters, pb_con
     }
     *best = *cfg;
     best->batch = bestE.batch;
-    best->chain_handoff = bestE.handoff;
+    best->estimator = bestE.estimator;
     return PB_OK;
 }
 
@@ -934,7 +996,7 @@ pb_status pb_autotune_cache_save(const char *path) {
     if (!f) return PB_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_tune_mutex);
     for (auto &kv : g_tune)
-        std::fprintf(f, "%s %d %d %.9g\n", kv.first.c_str(), kv.second.batch, kv.second.handoff, kv.second.ms_per_iter);
+        std::fprintf(f, "%s %d %d %.9g\n", kv.first.c_str(), kv.second.batch, kv.second.estimator, kv.second.ms_per_iter);
     std::fclose(f);
     return PB_OK;
 }
@@ -946,8 +1008,8 @@ pb_status pb_autotune_cache_load(const char *path) {
     char key[256];
     TuneEntry e;
     std::lock_guard<std::mutex> lk(g_tune_mutex);
-    while (std::fscanf(f, "%255s %d %d %lf", key, &e.batch, &e.handoff, &e.ms_per_iter) == 4)
-        if (e.batch > 0 && e.batch <= 64 && e.handoff > 0) g_tune[key] = e;
+    while (std::fscanf(f, "%255s %d %d %lf", key, &e.batch, &e.estimator, &e.ms_per_iter) == 4)
+        if (e.batch > 0 && e.batch <= 64 && (e.estimator == 0 || e.estimator == 1)) g_tune[key] = e;
     std::fclose(f);
     return PB_OK;
 }
@@ -1059,6 +1121,7 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
         if (host_tri[i] < -1 || host_tri[i] >= ctx->S.nt) return fail(ctx, PB_ERR_ARG, "iteration: triangle index out of range");
     s = ensure_pool(ctx, std::max(1, ctx->cap_slots), P.M * P.L, std::max(P.repeats, ctx->cap_rep), P.npix);
     if (s != PB_OK) return s;
+    if (cfg->estimator == 0 && (s = wf_ensure(ctx)) != PB_OK) return s;
     size_t n = (size_t)P.M * P.L;
     CK(cudaMemsetAsync(ctx->B.counters, 0, sizeof(unsigned long long) * CNT_N, ctx->stream));
     CK(cudaMemcpyAsync(ctx->B.gtri, host_tri, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
@@ -1073,7 +1136,7 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
         CK(cudaMemcpyAsync(ctx->B.rhat, r.data(), 4 * (size_t)ne, cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     } else {
-        launch_recip(ctx->S, ctx->T, P, ctx->B, 1, (uint32_t)iteration, ctx->num_sms, ctx->stream);
+        launch_recip(ctx->S, ctx->T, P, ctx->B, 1, (uint32_t)iteration, ctx->num_sms, ctx->stream, &ctx->wf);
     }
     if (cfg->proposal) {
         s = mlp_wave(ctx, P, 1, (uint32_t)iteration);

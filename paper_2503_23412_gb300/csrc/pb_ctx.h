@@ -67,6 +67,10 @@ struct pb_ctx {
     MlpState mlp;
     std::vector<RenderGraph *> graphs;
     uint32_t *d_iter0 = nullptr;     // iteration base of graph replays
+    // wavefront estimator buffers (allocated on first use)
+    WfBufs wf{};
+    std::vector<void *> wf_mem;
+    int wf_chain_cap = 0;
 };
 
 // shared by the host translation units
@@ -80,6 +84,8 @@ pb_status pb_check_cfg(pb_ctx *ctx, const pb_config *c);
 void mlp_free(pb_ctx *ctx);
 pb_status mlp_prepare(pb_ctx *ctx, int slots, int depth);
 void free_graphs(pb_ctx *ctx);
+pb_status wf_ensure(pb_ctx *ctx);
+pb_status wf_check(pb_ctx *ctx);
 pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base);
 pb_status mlp_check_err(pb_ctx *ctx);
 // one wave of iterations that records proposal training samples and leaves the film alone (pb_api.cu)

@@ -113,11 +113,64 @@ __device__ __forceinline__ bool trace_vtx(const DScene &S, float3 o, float3 w, i
     return true;
 }
 
-// one draw from q; returns f/q. Dims: 0 component, 1-3 light sample, 4-5
-// cosine direction, 6+3(r-1) BSDF at the r-th specular vertex, 18 RRS
-// uniform, 19 hemisphere side.
-template <bool COUNT = false>
-__device__ __forceinline__ float entry_ratio(const DScene &S, const Entry &E, Rng &R, TravCount *tc = nullptr) {
+// Tracer policies of entry_ratio. The inline tracer walks the BVH at once.
+// The replay tracer answers a node's first queries from stored results and
+// suspends at the next one, recording it for a traversal kernel (wavefront
+// evaluation); replaying the same uniforms and results reaches the same
+// decisions, so both give the same f/q.
+template <bool COUNT>
+struct InlineTracer {
+    TravCount *tc;
+    static constexpr bool can_suspend = false;
+    __device__ __forceinline__ bool suspended() const { return false; }
+    __device__ __forceinline__ bool closest(const DScene &S, float3 o, float3 w, int skip, bool to_emitter, Vtx &out) {
+        return trace_vtx<COUNT>(S, o, w, skip, out, tc, to_emitter);
+    }
+    __device__ __forceinline__ bool occluded_seg(const DScene &S, float3 a, float3 b, int s1, int s2) {
+        return occluded<COUNT>(S, a, b, s1, s2, tc);
+    }
+};
+
+struct ReplayTracer {
+    const WfResult *res;
+    int nres;
+    int next;
+    bool susp;
+    WfQuery q;
+    static constexpr bool can_suspend = true;
+    __device__ __forceinline__ bool suspended() const { return susp; }
+    __device__ __forceinline__ bool closest(const DScene &S, float3 o, float3 w, int skip, bool to_emitter, Vtx &out) {
+        if (next < nres) {
+            WfResult r = res[next++];
+            if (r.tri < 0) return false;
+            out = vertex_at(S, r.tri, r.b1, r.b2);
+            return true;
+        }
+        q.o = o;
+        q.d = w;
+        q.skip = skip;
+        q.skip2 = -1;
+        q.kind = to_emitter ? 1 : 0;
+        susp = true;
+        return false;
+    }
+    __device__ __forceinline__ bool occluded_seg(const DScene &S, float3 a, float3 b, int s1, int s2) {
+        if (next < nres) return res[next++].tri != 0;
+        q.o = a;
+        q.d = b;
+        q.skip = s1;
+        q.skip2 = s2;
+        q.kind = 2;
+        susp = true;
+        return true;
+    }
+};
+
+// one draw from q; returns f/q (0 also when the tracer suspended). Dims:
+// 0 component, 1-3 light sample, 4-5 cosine direction, 6+3(r-1) BSDF at the
+// r-th specular vertex, 18 RRS uniform, 19 hemisphere side.
+template <bool COUNT, class Tr>
+__device__ __forceinline__ float entry_ratio_t(const DScene &S, const Entry &E, Rng &R, Tr &T) {
     int u = E.u;
     Vtx gs[6];
     gs[0] = E.Y;
@@ -128,15 +181,18 @@ __device__ __forceinline__ float entry_ratio(const DScene &S, const Entry &E, Rn
         float b1, b2;
         if (!sample_light(S, R.u(1), R.u(2), R.u(3), tri, b1, b2)) return 0.0f;
         gs[1] = vertex_at(S, tri, b1, b2);
-        bool vis = !occluded<COUNT>(S, gs[1].p, E.Y.p, gs[1].tri, E.Y.tri, tc);
-        eval_fq(S, E, gs, true, vis, f, q);
+        bool occ = T.occluded_seg(S, gs[1].p, E.Y.p, gs[1].tri, E.Y.tri);
+        if (Tr::can_suspend && T.suspended()) return 0.0f;
+        eval_fq(S, E, gs, true, !occ, f, q);
         return q > 0.0f ? f / q : 0.0f;
     }
     if (compA && E.type == 1) {
         float3 w = cosine_dir(E.H.n, R.u(4), R.u(5));
-        if (!trace_vtx<COUNT>(S, E.H.p, w, E.H.tri, gs[1], tc)) return 0.0f;
-        bool vis = !occluded<COUNT>(S, gs[1].p, E.Y.p, gs[1].tri, E.Y.tri, tc);
-        eval_fq(S, E, gs, true, vis, f, q);
+        bool hit = T.closest(S, E.H.p, w, E.H.tri, false, gs[1]);
+        if ((Tr::can_suspend && T.suspended()) || !hit) return 0.0f;
+        bool occ = T.occluded_seg(S, gs[1].p, E.Y.p, gs[1].tri, E.Y.tri);
+        if (Tr::can_suspend && T.suspended()) return 0.0f;
+        eval_fq(S, E, gs, true, !occ, f, q);
         return q > 0.0f ? f / q : 0.0f;
     }
     const DMat &mY = S.mats[E.Y.mat];
@@ -146,7 +202,8 @@ __device__ __forceinline__ float entry_ratio(const DScene &S, const Entry &E, Rn
         nside = R.u(19) < E.pin ? nin : -nin;
     }
     float3 w = cosine_dir(nside, R.u(4), R.u(5));
-    if (!trace_vtx<COUNT>(S, E.Y.p, w, E.Y.tri, gs[1], tc, E.type == 0 && u == 1)) return 0.0f;
+    bool hit = T.closest(S, E.Y.p, w, E.Y.tri, E.type == 0 && u == 1, gs[1]);
+    if ((Tr::can_suspend && T.suspended()) || !hit) return 0.0f;
     for (int r = 1; r < u; ++r) {
         const DMat &m = S.mats[gs[r].mat];
         float3 wg = dirto(gs[r].p, gs[r - 1].p);
@@ -154,11 +211,21 @@ __device__ __forceinline__ float entry_ratio(const DScene &S, const Entry &E, Rn
         float3 ws;
         int d0 = 6 + 3 * (r - 1);
         if (!bsdf_sample(m, gs[r].n, wg, R.u(d0), R.u(d0 + 1), R.u(d0 + 2), ws)) return 0.0f;
-        if (!trace_vtx<COUNT>(S, gs[r].p, ws, gs[r].tri, gs[r + 1], tc, E.type == 0 && r + 1 == u)) return 0.0f;
+        hit = T.closest(S, gs[r].p, ws, gs[r].tri, E.type == 0 && r + 1 == u, gs[r + 1]);
+        if ((Tr::can_suspend && T.suspended()) || !hit) return 0.0f;
     }
     bool vis = true;
-    if (E.type == 1) vis = !occluded<COUNT>(S, gs[u].p, E.H.p, gs[u].tri, E.H.tri, tc);
+    if (E.type == 1) {
+        bool occ = T.occluded_seg(S, gs[u].p, E.H.p, gs[u].tri, E.H.tri);
+        if (Tr::can_suspend && T.suspended()) return 0.0f;
+        vis = !occ;
+    }
     eval_fq(S, E, gs, false, vis, f, q);
     return q > 0.0f ? f / q : 0.0f;
 }
 
+template <bool COUNT = false>
+__device__ __forceinline__ float entry_ratio(const DScene &S, const Entry &E, Rng &R, TravCount *tc = nullptr) {
+    InlineTracer<COUNT> T{tc};
+    return entry_ratio_t<COUNT>(S, E, R, T);
+}

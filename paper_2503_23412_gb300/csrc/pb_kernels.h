@@ -43,6 +43,37 @@ struct SampleSink {
     int cap;
 };
 
+// Buffers of the wavefront estimator (pb_light.cu): per chain (one per
+// (entry, repeat) of the wave) its window of nodes this round, per node its
+// chain, pre-order index, answered queries, pending query and result.
+// a query of the replay tracer (pb_estimator.cuh): kind 0 closest hit, 1
+// closest hit that only counts on an emitter, 2 occlusion of the segment o -> d
+struct WfQuery {
+    float3 o, d;
+    int skip, skip2, kind;
+};
+// its answer: closest hit (tri, barycentrics; tri -1 for none) or, for an
+// occlusion query, tri = 1 occluded / 0 visible
+struct WfResult {
+    int tri;
+    float b1, b2;
+};
+constexpr int WF_MAXQ = 5;   // at most u = 4 closest hits and one occlusion per node
+constexpr int WF_ROUNDS = 24;   // wavefront rounds launched per wave (idle rounds exit at once)
+
+struct WfBufs {
+    int32_t *ch_w, *ch_off, *ch_win;   // per chain: nodes this round, first node, window size
+    uint8_t *ch_done;
+    int32_t *node_chain, *node_v, *node_nq;
+    struct WfResult *node_res;         // WF_MAXQ per node
+    struct WfQuery *node_q;
+    float *node_g;
+    int32_t *node_n;
+    int32_t *list[2];                  // nodes that need a step (ping-pong)
+    int32_t *ctl;                      // counters (WF_CTL_* in pb_light.cu)
+    int node_cap;
+};
+
 struct KParams {
     uint32_t seed;
     int max_depth, M, M_p, repeats, proxy, conn, trial_cap;
@@ -52,6 +83,7 @@ struct KParams {
     int handoff;    // estimator nodes walked by a warp before a block continues the chain
     int pilot_min, pilot_max;   // per-entry B pilot draws (multiples of 32; pilot_max 0 = off)
     float side_in;              // cosine draws at a dielectric y_{s-1} on the side of y_{s-2}
+    int estimator;              // 0: wavefront; 1: warp and block phases
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
     SampleSink smp;         // raw != nullptr: record proposal training samples
@@ -115,7 +147,7 @@ void launch_light_pass(const DScene &S, const KParams &P, const Pool &B, int slo
 void launch_pool_build(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
                        cudaStream_t st);
 void launch_recip(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
-                  uint32_t iter_base, int num_sms, cudaStream_t st);
+                  uint32_t iter_base, int num_sms, cudaStream_t st, const WfBufs *wf = nullptr);
 void launch_eye(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                 float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st);
 void launch_eye_feat(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,

@@ -13,8 +13,12 @@
 //   k_recip_finish   average of the repeats per entry
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "pb_kernels.h"
 #include "pb_estimator.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -693,6 +697,380 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Wavefront estimator. Every (entry, repeat) of the wave is a chain. Each
+// round gives every unfinished chain a window of consecutive pre-order nodes
+// (sized from the entry's expected chain length, doubling while the chain
+// lasts), then evaluates all nodes of all windows in stages: a step kernel
+// replays a node's draw (entry_ratio with the replay tracer) up to its next
+// ray query, a traversal-only kernel answers the queries, and so on until
+// every node has its f/q. A walk per chain then consumes its window in
+// pre-order exactly as the sequential definition does. Node values depend
+// only on (entry, repeat, node), so the estimates are those of the warp and
+// block phases.
+enum { WF_CTL_ITEMS = 0, WF_CTL_NODES, WF_CTL_ACTIVE, WF_CTL_ERR, WF_CTL_CNT0 };   // CNT0 .. CNT0 + WF_MAXQ + 1
+constexpr int WF_WIN_MAX = 16384;
+
+__device__ __forceinline__ int wf_items(const Pool &B, int slots) { return min(B.work[1 + slots], B.chain_cap); }
+
+__global__ void k_wf_init(KParams P, Pool B, WfBufs W, int slots) {
+    const int32_t *offs = B.work + 1;
+    int total = offs[slots];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        W.ctl[WF_CTL_ITEMS] = min(total, B.chain_cap);
+        W.ctl[WF_CTL_ACTIVE] = min(total, B.chain_cap);
+        W.ctl[WF_CTL_ERR] = total > B.chain_cap ? 1 : 0;
+    }
+    int items = min(total, B.chain_cap);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < items; c += gridDim.x * blockDim.x) {
+        int slot = 0;
+        while (c >= offs[slot + 1]) ++slot;
+        int local = c - offs[slot];
+        ChainState st;
+        st.slot = slot;
+        st.k = local / P.repeats;
+        st.rep = local % P.repeats;
+        st.next = 0;
+        st.sum_t = 0.0;
+        st.cur_sign = 1.0f;
+        st.sp = 0;
+        B.chains[c] = st;
+        W.ch_done[c] = 0;
+        // first window: about half the expected chain length, 64 .. 2048 nodes
+        float mu = B.eMu[(size_t)slot * B.ML + st.k];
+        int win = 256;
+        if (mu > 0.0f) {
+            win = 64;
+            while (win < 2048 && (float)win < 0.5f * mu) win <<= 1;
+        }
+        W.ch_win[c] = win;
+    }
+}
+
+// one block: windows of this round and their node offsets (exclusive scan)
+__global__ void __launch_bounds__(1024) k_wf_plan(KParams P, Pool B, WfBufs W) {
+    __shared__ int part[1024];
+    const int items = W.ctl[WF_CTL_ITEMS];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid <= WF_MAXQ + 1) W.ctl[WF_CTL_CNT0 + tid] = 0;
+    if (W.ctl[WF_CTL_ACTIVE] == 0) {
+        if (tid == 0) W.ctl[WF_CTL_NODES] = 0;
+        return;
+    }
+    const int per = (items + nt - 1) / nt;
+    const int c0 = tid * per, c1 = min(items, c0 + per);
+    int acc = 0;
+    for (int c = c0; c < c1; ++c) {
+        int w = 0;
+        if (!W.ch_done[c]) w = max(0, min(W.ch_win[c], P.trial_cap - B.chains[c].next));
+        W.ch_w[c] = w;
+        acc += w;
+    }
+    part[tid] = acc;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int x = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += x;
+        __syncthreads();
+    }
+    int run = part[tid] - acc;
+    for (int c = c0; c < c1; ++c) {
+        int w = W.ch_w[c];
+        if (run + w > W.node_cap) w = 0;   // no room this round: the chain waits
+        W.ch_w[c] = w;
+        W.ch_off[c] = run;
+        run += w;
+    }
+    __syncthreads();
+    if (tid == nt - 1) W.ctl[WF_CTL_NODES] = min(part[nt - 1], W.node_cap);
+}
+
+__global__ void k_wf_nodes(Pool B, WfBufs W) {
+    const int items = W.ctl[WF_CTL_ITEMS], nodes = W.ctl[WF_CTL_NODES];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += gridDim.x * blockDim.x) {
+        // the last chain whose window starts at or before i (chains with an
+        // empty window share the offset of the next one and come before it)
+        int lo = 0, hi = items - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (W.ch_off[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        W.node_chain[i] = lo;
+        W.node_v[i] = B.chains[lo].next + (i - W.ch_off[lo]);
+        W.node_nq[i] = 0;
+        W.list[0][i] = i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) W.ctl[WF_CTL_CNT0] = nodes;
+}
+
+// stage s: replay each listed node up to its next query (or to its f/q)
+__global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, WfBufs W, int s, uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
+    const int n = W.ctl[WF_CTL_CNT0 + s];
+    const int32_t *in = W.list[s & 1];
+    int32_t *out = W.list[(s + 1) & 1];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int i = in[idx];
+        const ChainState &st = B.chains[W.node_chain[i]];
+        const int slot = st.slot, k = st.k, rep = st.rep;
+        int Sp, C;
+        Entry E = load_entry(S, P, B, slot, k, Sp, C);
+        const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
+        const int v = W.node_v[i];
+        Rng R;
+        R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
+        ReplayTracer T;
+        T.res = W.node_res + (size_t)WF_MAXQ * i;
+        T.nres = W.node_nq[i];
+        T.next = 0;
+        T.susp = false;
+        float ratio = entry_ratio_t<false>(S, E, R, T);
+        if (T.susp && s == WF_MAXQ) {   // cannot happen (u <= 4): keep the walk defined and report
+            atomicExch(&W.ctl[WF_CTL_ERR], 2);
+            W.node_g[i] = 1.0f;
+            W.node_n[i] = 0;
+        } else if (T.susp) {
+            W.node_q[i] = T.q;
+            cg::coalesced_group g = cg::coalesced_threads();
+            int base = 0;
+            if (g.thread_rank() == 0) base = atomicAdd(&W.ctl[WF_CTL_CNT0 + s + 1], (int)g.size());
+            out[g.shfl(base, 0) + g.thread_rank()] = i;
+        } else {
+            float gv = 1.0f - ratio * invB;
+            float r = fabsf(gv);
+            int nch = (int)floorf(r);
+            if (R.u(18) < r - (float)nch) nch += 1;
+            W.node_g[i] = gv;
+            W.node_n[i] = nch;
+        }
+    }
+}
+
+// stage s: answer the queries the step kernel recorded
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_wf_trace(DScene S, KParams P, Pool B, WfBufs W, int s) {
+    TravCount tc{0, 0, 0};
+    const int n = W.ctl[WF_CTL_CNT0 + s + 1];
+    const int32_t *lst = W.list[(s + 1) & 1];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int i = lst[idx];
+        const WfQuery q = W.node_q[i];
+        WfResult res;
+        if (q.kind == 2) {
+            res.tri = occluded<COUNT>(S, q.o, q.d, q.skip, q.skip2, &tc) ? 1 : 0;
+            res.b1 = res.b2 = 0.0f;
+        } else {
+            Hit h = (q.kind == 1 && S.ne <= PB_EMITTER_LIST_MAX) ? closest_emitter_hit<COUNT>(S, q.o, q.d, q.skip, &tc)
+                                                                  : closest_hit<COUNT>(S, q.o, q.d, q.skip, &tc);
+            res.tri = h.tri;
+            res.b1 = h.b1;
+            res.b2 = h.b2;
+        }
+        int nq = W.node_nq[i];
+        if (nq < WF_MAXQ) {
+            W.node_res[(size_t)WF_MAXQ * i + nq] = res;
+            W.node_nq[i] = nq + 1;
+        }
+    }
+    if (COUNT) {
+        atomicAdd(&B.counters[CNT_REC_NODES], (unsigned long long)tc.nodes);
+        atomicAdd(&B.counters[CNT_REC_TRIS], (unsigned long long)tc.tris);
+        atomicAdd(&B.counters[CNT_REC_RAYS], (unsigned long long)tc.rays);
+    }
+}
+
+// one warp per chain: the walk over this round's window in chunks of 32
+// nodes. While every pending node has sign +1 and the chunk has no negative
+// g, the walk reduces to counts (pending_v = pending - 1 + n_v; the chain
+// ends at the first node where pending reaches 0), a warp scan; otherwise
+// lane 0 replays the exact sequential walk over the chunk.
+__global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int items = W.ctl[WF_CTL_ITEMS];
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < items; c += warps) {
+        const int w = W.ch_w[c];
+        if (W.ch_done[c] || w == 0) continue;
+        ChainState &gst = B.chains[c];
+        const int slot = gst.slot, k = gst.k, rep = gst.rep;
+        const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
+        const int off = W.ch_off[c];
+        int next = gst.next;
+        double sum_t = gst.sum_t;
+        // pending-count form of the walk state while all signs are +1
+        bool pos = gst.cur_sign > 0.0f;
+        int pend = 1;
+        for (int f = 0; f < gst.sp; ++f) {
+            pos = pos && gst.fr_sign[f] > 0.0f;
+            pend += gst.fr_rem[f];
+        }
+        bool stack_form = !pos;   // gst holds the authoritative stack
+        int done = 0, trunc = 0;
+        for (int j0 = 0; j0 < w && !done; j0 += 32) {
+            const int j = j0 + lane;
+            const bool in = j < w;
+            const float g = in ? W.node_g[off + j] : 1.0f;
+            const int n = in ? W.node_n[off + j] : 1;
+            const bool anyneg = __any_sync(0xffffffffu, in && g < 0.0f);
+            if (!stack_form && !anyneg) {
+                // inclusive scan of (n - 1) over the chunk
+                int x = in ? n - 1 : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const unsigned endm = __ballot_sync(0xffffffffu, in && pend + x <= 0);
+                const int cnt = min(32, w - j0);
+                const int last = endm ? __ffs(endm) - 1 : cnt - 1;   // last node processed
+                double t = (in && lane <= last) ? (double)(g * invB) : 0.0;
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                sum_t += t;
+                next += last + 1;
+                pend += __shfl_sync(0xffffffffu, x, last);
+                if (endm) done = 1;
+                continue;
+            }
+            // exact sequential walk of this chunk by lane 0, on the stack form
+            if (!stack_form) {
+                if (lane == 0) {
+                    gst.cur_sign = 1.0f;
+                    gst.sp = 0;
+                    if (pend - 1 > 0) {
+                        gst.fr_sign[0] = 1.0f;
+                        gst.fr_rem[0] = pend - 1;
+                        gst.sp = 1;
+                    }
+                }
+                stack_form = true;
+            }
+            if (lane == 0) {
+                const int cnt = min(32, w - j0);
+                for (int q = 0; q < cnt; ++q) {
+                    const float gj = W.node_g[off + j0 + q];
+                    const int nj = W.node_n[off + j0 + q];
+                    sum_t += (double)(gst.cur_sign * gj * invB);
+                    next += 1;
+                    if (nj >= 1) {
+                        if (gst.sp >= MAXF) {
+                            done = 1;
+                            trunc = 1;
+                            break;
+                        }
+                        gst.fr_sign[gst.sp] = gst.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                        gst.fr_rem[gst.sp] = nj;
+                        gst.sp++;
+                    }
+                    if (gst.sp == 0) {
+                        done = 1;
+                        break;
+                    }
+                    gst.cur_sign = gst.fr_sign[gst.sp - 1];
+                    if (--gst.fr_rem[gst.sp - 1] == 0) gst.sp--;
+                }
+            }
+            done = __shfl_sync(0xffffffffu, done, 0);
+            trunc = __shfl_sync(0xffffffffu, trunc, 0);
+            next = __shfl_sync(0xffffffffu, next, 0);
+            sum_t = __shfl_sync(0xffffffffu, sum_t, 0);
+            __syncwarp();
+            // back to the count form when the stack turned all-positive again
+            bool p2 = gst.cur_sign > 0.0f;
+            int pe = 1;
+            for (int f = 0; f < gst.sp; ++f) {
+                p2 = p2 && gst.fr_sign[f] > 0.0f;
+                pe += gst.fr_rem[f];
+            }
+            if (p2) {
+                stack_form = false;
+                pend = pe;
+            }
+            __syncwarp();
+        }
+        if (!done && next >= P.trial_cap) {
+            done = 1;
+            trunc = 1;
+        }
+        if (lane == 0) {
+            if (!stack_form) {   // store the count form as a one-frame stack
+                gst.cur_sign = 1.0f;
+                gst.sp = 0;
+                if (pend - 1 > 0) {
+                    gst.fr_sign[0] = 1.0f;
+                    gst.fr_rem[0] = pend - 1;
+                    gst.sp = 1;
+                }
+            }
+            gst.next = next;
+            gst.sum_t = sum_t;
+            if (done) {
+                size_t o = ((size_t)slot * B.ML + k) * P.repeats + rep;
+                B.rep[o] = (float)((double)invB + sum_t);
+                B.repn[o] = (float)next;
+                B.reptr[o] = trunc;
+                W.ch_done[c] = 1;
+                atomicSub(&W.ctl[WF_CTL_ACTIVE], 1);
+            } else {
+                W.ch_win[c] = min(2 * W.ch_win[c], WF_WIN_MAX);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// chains the rounds left unfinished (deferred by the node capacity): one
+// thread each, inline draws, the same walk; counted in WF_CTL_ERR's high bits
+__global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
+    const int items = W.ctl[WF_CTL_ITEMS];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < items; c += gridDim.x * blockDim.x) {
+        if (W.ch_done[c]) continue;
+        atomicAdd(&W.ctl[WF_CTL_ERR], 1 << 8);
+        ChainState st = B.chains[c];
+        int Sp, C;
+        Entry E = load_entry(S, P, B, st.slot, st.k, Sp, C);
+        const float invB = 1.0f / B.eB[(size_t)st.slot * B.ML + st.k];
+        int done = 0, trunc = 0;
+        while (!done) {
+            if (st.next >= P.trial_cap) {
+                done = trunc = 1;
+                break;
+            }
+            Rng R;
+            R.init(P.seed, K_RECIP, iter_base + st.slot, (uint32_t)(st.k * 8 + st.rep), (uint32_t)st.next);
+            float ratio = entry_ratio<false>(S, E, R, nullptr);
+            float gj = 1.0f - ratio * invB;
+            float r = fabsf(gj);
+            int nj = (int)floorf(r);
+            if (R.u(18) < r - (float)nj) nj += 1;
+            st.sum_t += (double)(st.cur_sign * gj * invB);
+            st.next += 1;
+            if (nj >= 1) {
+                if (st.sp >= MAXF) {
+                    done = trunc = 1;
+                    break;
+                }
+                st.fr_sign[st.sp] = st.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                st.fr_rem[st.sp] = nj;
+                st.sp++;
+            }
+            if (st.sp == 0) {
+                done = 1;
+                break;
+            }
+            st.cur_sign = st.fr_sign[st.sp - 1];
+            if (--st.fr_rem[st.sp - 1] == 0) st.sp--;
+        }
+        size_t o = ((size_t)st.slot * B.ML + st.k) * P.repeats + st.rep;
+        B.rep[o] = (float)((double)invB + st.sum_t);
+        B.repn[o] = (float)st.next;
+        B.reptr[o] = trunc;
+        W.ch_done[c] = 1;
+        B.chains[c] = st;
+    }
+}
+
 __global__ void k_recip_offsets(KParams P, Pool B, int slots) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         B.work[0] = 0;
@@ -748,8 +1126,29 @@ void launch_pool_build(const DScene &S, const DTables &T, const KParams &P, cons
 }
 
 void launch_recip(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
-                  int num_sms, cudaStream_t st) {
+                  int num_sms, cudaStream_t st, const WfBufs *wf) {
     k_recip_offsets<<<1, 32, 0, st>>>(P, B, slots);
+    if (P.estimator == 0 && wf && wf->node_cap > 0) {
+        const WfBufs W = *wf;
+        if (P.count) k_recip_pilot<true><<<num_sms * 4, 128, 0, st>>>(S, T, P, B, slots, iter_base);
+        else k_recip_pilot<false><<<num_sms * 4, 128, 0, st>>>(S, T, P, B, slots, iter_base);
+        k_wf_init<<<num_sms * 2, 256, 0, st>>>(P, B, W, slots);
+        for (int round = 0; round < WF_ROUNDS; ++round) {
+            k_wf_plan<<<1, 1024, 0, st>>>(P, B, W);
+            k_wf_nodes<<<num_sms * 8, 256, 0, st>>>(B, W);
+            for (int s = 0; s <= WF_MAXQ; ++s) {
+                k_wf_step<<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s, iter_base);
+                if (s == WF_MAXQ) break;
+                if (P.count) k_wf_trace<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+                else k_wf_trace<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+            }
+            k_wf_walk<<<num_sms * 16, 128, 0, st>>>(P, B, W);
+        }
+        k_wf_finish_rest<<<num_sms * 2, 128, 0, st>>>(S, P, B, W, iter_base);
+        dim3 g2((B.ML + 127) / 128, slots);
+        k_recip_finish<<<g2, 128, 0, st>>>(P, B);
+        return;
+    }
     if (P.count) {
         k_recip_pilot<true><<<num_sms * 4, 128, 0, st>>>(S, T, P, B, slots, iter_base);
         k_recip<true><<<num_sms * 8, 128, 0, st>>>(S, T, P, B, slots, iter_base);

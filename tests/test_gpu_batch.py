@@ -3,9 +3,9 @@
 Iterations are independent and the film adds them in iteration order, so
 how iterations are grouped into waves, whether the waves are replayed from a
 captured CUDA graph, and whether several scenes share one graph launch must
-not change a single bit of any film. The estimator's hand-off point only
-changes its summation order, so a tuned configuration matches the default
-up to rounding.
+not change a single bit of any film. The estimator's schedule (wavefront or
+warp/block phases) only changes its summation order, so a tuned
+configuration matches the default up to rounding.
 """
 
 import numpy as np
@@ -103,18 +103,18 @@ def test_autotune_chooses_cached_valid_configuration(N, tmp_path):
     cfg = N.config(spp=16, iter0=50, **base)
     best, cached = r.autotune(cfg, trial_iters=16)
     assert not cached
-    assert best.batch in (4, 8, 16) and best.chain_handoff in (256, 512, 1024)
+    assert best.batch in (4, 8, 16) and best.estimator in (0, 1)
     assert (best.spp, best.iter0, best.M, best.max_depth) == (16, 50, 1500, 6)
     best2, cached2 = r.autotune(cfg, trial_iters=16)
-    assert cached2 and (best2.batch, best2.chain_handoff) == (best.batch, best.chain_handoff)
+    assert cached2 and (best2.batch, best2.estimator) == (best.batch, best.estimator)
     # the cache survives a save / clear / load round trip
     path = str(tmp_path / "tune.txt")
     N.autotune_cache_save(path)
     N.autotune_cache_clear()
     N.autotune_cache_load(path)
     best3, cached3 = r.autotune(cfg, trial_iters=16)
-    assert cached3 and (best3.batch, best3.chain_handoff) == (best.batch, best.chain_handoff)
-    # tuned and default renders agree (the hand-off changes only the estimator's summation order)
+    assert cached3 and (best3.batch, best3.estimator) == (best.batch, best.estimator)
+    # tuned and default renders agree (the schedule changes only the estimator's summation order)
     a, _ = _film(N, r, cfg)
     b, _ = _film(N, r, best)
     np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6 * float(np.abs(a).max()))

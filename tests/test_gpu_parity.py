@@ -165,7 +165,7 @@ def test_block_phase_of_the_estimator_matches_oracle(N, handoff):
         t2["B_tab"] = (tab["B_tab"] * scale).astype(np.float32)
         r = N.Renderer(sc, t2)
         p = O.params(M=1500, M_p=1500, max_depth=8)
-        cfg = N.config(M=1500, M_p=1500, max_depth=8, chain_handoff=handoff)
+        cfg = N.config(M=1500, M_p=1500, max_depth=8, chain_handoff=handoff, estimator=1)   # warp/block phases
         tri, bary = o.light_pass(p, 9)
         ref = o.iteration(p, o.tables(t2), 9, tri, bary, pix_lo=0, pix_hi=0)
         got = r.iteration(cfg, 9, tri, bary)
@@ -233,6 +233,39 @@ def test_estimator_with_side_weighted_lobe_matches_oracle(N):
         assert n_ent > 20 and n_same / n_ent >= 0.98
         nodes[side] = tot
     assert nodes[0.9] < nodes[0.0]
+    r.close()
+
+
+@pytest.mark.parametrize("make", [lambda: scenes.projector(24, 24, lens_tris_per_cap=1500, flat=True),
+                                  lambda: scenes.cornell(20, 16)])
+def test_wavefront_estimator_matches_phases_and_oracle(N, make):
+    """The wavefront schedule (all chains' node windows evaluated in stages,
+    queries answered by traversal-only kernels) gives the estimates of the
+    warp/block schedule: the same nodes, the same values up to the order of
+    double sums; and matches the oracle like the default schedule."""
+    sc = make()
+    o = O.Oracle(sc)
+    tab = learned(sc, o, M=1500, M_p=1500, max_depth=8)
+    r = N.Renderer(sc, tab)
+    td = o.tables(tab)
+    p = O.params(M=1500, M_p=1500, max_depth=8)
+    n_ent = n_same = 0
+    for it in (3, 4):
+        tri, bary = o.light_pass(p, it)
+        a = r.iteration(N.config(M=1500, M_p=1500, max_depth=8, estimator=1), it, tri, bary)   # warp/block phases
+        b = r.iteration(N.config(M=1500, M_p=1500, max_depth=8), it, tri, bary)                # wavefront
+        assert len(a["rhat"]) == len(b["rhat"]) > 0
+        np.testing.assert_array_equal(a["entry_nodes"], b["entry_nodes"])
+        np.testing.assert_array_equal(a["entry_sig"], b["entry_sig"])
+        np.testing.assert_allclose(b["rhat"], a["rhat"], rtol=1e-6)
+        np.testing.assert_array_equal(a["sig"], b["sig"])
+        ref = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0)
+        es = ref["entry_sig"] == b["entry_sig"]
+        n_ent += len(es)
+        n_same += int(es.sum())
+        assert np.array_equal(ref["entry_nodes"][es], b["entry_nodes"][es])
+        assert np.all(rel_close(ref["rhat"][es], b["rhat"][es], 1e-3))
+    assert n_same / n_ent >= 0.98
     r.close()
 
 
