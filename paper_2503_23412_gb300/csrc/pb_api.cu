@@ -602,6 +602,10 @@ pb_status wf_ensure(pb_ctx *ctx) {
     CK(dalloc(o, &W.list[0], nn));
     CK(dalloc(o, &W.list[1], nn));
     CK(dalloc(o, &W.ctl, (size_t)16));
+    CK(dalloc(o, &W.pil_next, nc));
+    CK(dalloc(o, &W.pil_best, nc));
+    CK(dalloc(o, &W.pil_sum, nc));
+    CK(dalloc(o, &W.pil_draws, nc));
     CK(cudaMemsetAsync(W.ctl, 0, 16 * sizeof(int32_t), ctx->stream));
     W.node_cap = WF_NODE_CAP;
     ctx->wf_chain_cap = chains;
@@ -723,9 +727,15 @@ static pb_status finish_render(pb_ctx *ctx, const pb_config *cfg, const KParams 
     st.n_waves = waves;
     // per wave: light, pool build, bucket, cdf, eye, film (6); the estimator:
     // warp/block phases = offsets, pilot, two phases, finish (5); wavefront =
-    // offsets, pilot, init, rounds x (plan, nodes, steps, traces, walk),
-    // finisher, finish; the learned proposal adds its feature pass and network
-    const int64_t est = cfg->estimator == 1 ? 5 : 5 + (int64_t)WF_ROUNDS * (3 + 2 * WF_MAXQ + 1);
+    // offsets, pilot (init + rounds x (plan, nodes, steps, traces, reduce), or
+    // one kernel without a pilot), init, rounds x (plan, nodes, steps, traces,
+    // walk), finisher, finish; the learned proposal adds its feature pass and
+    // network
+    const int per_round = 3 + 2 * WF_MAXQ + 1;
+    const int pr = wf_pilot_rounds(P);
+    const int64_t est = cfg->estimator == 1 ? 5
+                                            : 4 + (pr > 0 ? 1 + (int64_t)pr * per_round : 1) +
+                                                  (int64_t)WF_ROUNDS * per_round;
     st.n_launches = (6 + est + (cfg->proposal ? 2 : 0)) * (int64_t)waves;
     if (cfg->proposal) {
         pb_status s = mlp_check_err(ctx);

@@ -72,6 +72,10 @@ struct WfBufs {
     int32_t *list[2];                  // nodes that need a step (ping-pong)
     int32_t *ctl;                      // counters (WF_CTL_* in pb_light.cu)
     int node_cap;
+    // pilot of the per-entry bound, run as the same stages: per entry
+    int32_t *pil_next;                 // draws evaluated so far
+    float *pil_best, *pil_sum;         // largest f/q and sum of f/q over the counted draws
+    int32_t *pil_draws;                // draws counted (whole blocks of 32 before the stop)
 };
 
 struct KParams {
@@ -89,6 +93,17 @@ struct KParams {
     SampleSink smp;         // raw != nullptr: record proposal training samples
     const uint32_t *iter_dev;   // non-null (graph replay): iteration numbers are *iter_dev + the launch's base
 };
+
+// rounds of the wavefront pilot: windows pilot_min, then doubling, until pilot_max
+__host__ __device__ inline int wf_pilot_rounds(const KParams &P) {
+    if (P.pilot_max <= 0) return 0;
+    int nr = 1;
+    for (int tot = P.pilot_min, w = P.pilot_min; tot < P.pilot_max; w *= 2) {
+        tot += w;
+        ++nr;
+    }
+    return nr;
+}
 
 __device__ __forceinline__ uint32_t eff_iter(const KParams &P, uint32_t iter_base) {
     return P.iter_dev ? iter_base + *P.iter_dev : iter_base;

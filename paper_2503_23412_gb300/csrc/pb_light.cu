@@ -711,8 +711,6 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
 enum { WF_CTL_ITEMS = 0, WF_CTL_NODES, WF_CTL_ACTIVE, WF_CTL_ERR, WF_CTL_CNT0 };   // CNT0 .. CNT0 + WF_MAXQ + 1
 constexpr int WF_WIN_MAX = 16384;
 
-__device__ __forceinline__ int wf_items(const Pool &B, int slots) { return min(B.work[1 + slots], B.chain_cap); }
-
 __global__ void k_wf_init(KParams P, Pool B, WfBufs W, int slots) {
     const int32_t *offs = B.work + 1;
     int total = offs[slots];
@@ -786,6 +784,7 @@ __global__ void __launch_bounds__(1024) k_wf_plan(KParams P, Pool B, WfBufs W) {
     if (tid == nt - 1) W.ctl[WF_CTL_NODES] = min(part[nt - 1], W.node_cap);
 }
 
+template <bool PILOT>
 __global__ void k_wf_nodes(Pool B, WfBufs W) {
     const int items = W.ctl[WF_CTL_ITEMS], nodes = W.ctl[WF_CTL_NODES];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += gridDim.x * blockDim.x) {
@@ -798,29 +797,49 @@ __global__ void k_wf_nodes(Pool B, WfBufs W) {
             else hi = mid - 1;
         }
         W.node_chain[i] = lo;
-        W.node_v[i] = B.chains[lo].next + (i - W.ch_off[lo]);
+        W.node_v[i] = (PILOT ? W.pil_next[lo] : B.chains[lo].next) + (i - W.ch_off[lo]);
         W.node_nq[i] = 0;
         W.list[0][i] = i;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) W.ctl[WF_CTL_CNT0] = nodes;
 }
 
-// stage s: replay each listed node up to its next query (or to its f/q)
-__global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, WfBufs W, int s, uint32_t iter_base) {
+// the (slot, entry) of the e-th entry of the wave
+__device__ __forceinline__ void wave_entry(const Pool &B, const KParams &P, int slots, int e, int &slot, int &k) {
+    const int32_t *offs = B.work + 1;   // per slot: first (entry, repeat) item
+    slot = 0;
+    while (e * P.repeats >= offs[slot + 1] && slot < slots - 1) ++slot;
+    k = e - offs[slot] / P.repeats;
+}
+
+// stage s: replay each listed node up to its next query (or to its f/q).
+// PILOT: the node is draw v of the pilot of entry node_chain (stream PILOT),
+// and its result is f/q itself.
+template <bool PILOT>
+__global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, WfBufs W, int s, uint32_t iter_base,
+                                                 int slots) {
     iter_base = eff_iter(P, iter_base);
     const int n = W.ctl[WF_CTL_CNT0 + s];
     const int32_t *in = W.list[s & 1];
     int32_t *out = W.list[(s + 1) & 1];
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const int i = in[idx];
-        const ChainState &st = B.chains[W.node_chain[i]];
-        const int slot = st.slot, k = st.k, rep = st.rep;
+        int slot, k, rep = 0;
+        if (PILOT) {
+            wave_entry(B, P, slots, W.node_chain[i], slot, k);
+        } else {
+            const ChainState &st = B.chains[W.node_chain[i]];
+            slot = st.slot;
+            k = st.k;
+            rep = st.rep;
+        }
         int Sp, C;
         Entry E = load_entry(S, P, B, slot, k, Sp, C);
-        const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
+        const float invB = PILOT ? 0.0f : 1.0f / B.eB[(size_t)slot * B.ML + k];
         const int v = W.node_v[i];
         Rng R;
-        R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
+        if (PILOT) R.init(P.seed, K_PILOT, iter_base + slot, (uint32_t)k, (uint32_t)v);
+        else R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
         ReplayTracer T;
         T.res = W.node_res + (size_t)WF_MAXQ * i;
         T.nres = W.node_nq[i];
@@ -837,6 +856,8 @@ __global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, Wf
             int base = 0;
             if (g.thread_rank() == 0) base = atomicAdd(&W.ctl[WF_CTL_CNT0 + s + 1], (int)g.size());
             out[g.shfl(base, 0) + g.thread_rank()] = i;
+        } else if (PILOT) {
+            W.node_g[i] = ratio;
         } else {
             float gv = 1.0f - ratio * invB;
             float r = fabsf(gv);
@@ -844,6 +865,112 @@ __global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, Wf
             if (R.u(18) < r - (float)nch) nch += 1;
             W.node_g[i] = gv;
             W.node_n[i] = nch;
+        }
+    }
+}
+
+// pilot: entries of the wave, first window pilot_min draws
+__global__ void k_wfp_init(KParams P, Pool B, WfBufs W, int slots) {
+    const int32_t *offs = B.work + 1;
+    const int ents = min(offs[slots] / P.repeats, B.chain_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        W.ctl[WF_CTL_ITEMS] = ents;
+        W.ctl[WF_CTL_ACTIVE] = ents;
+    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ents; e += gridDim.x * blockDim.x) {
+        W.pil_next[e] = 0;
+        W.pil_best[e] = 0.0f;
+        W.pil_sum[e] = 0.0f;
+        W.pil_draws[e] = 0;
+        W.ch_done[e] = 0;
+        W.ch_win[e] = P.pilot_min;
+    }
+}
+
+// one block: pilot windows of this round and their node offsets
+__global__ void __launch_bounds__(1024) k_wfp_plan(KParams P, WfBufs W) {
+    __shared__ int part[1024];
+    const int items = W.ctl[WF_CTL_ITEMS];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid <= WF_MAXQ + 1) W.ctl[WF_CTL_CNT0 + tid] = 0;
+    const int per = (items + nt - 1) / nt;
+    const int c0 = tid * per, c1 = min(items, c0 + per);
+    int acc = 0;
+    for (int c = c0; c < c1; ++c) {
+        int w = W.ch_done[c] ? 0 : max(0, min(W.ch_win[c], P.pilot_max - W.pil_next[c]));
+        W.ch_w[c] = w;
+        acc += w;
+    }
+    part[tid] = acc;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int x = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += x;
+        __syncthreads();
+    }
+    int run = part[tid] - acc;
+    for (int c = c0; c < c1; ++c) {
+        int w = W.ch_w[c];
+        if (run + w > W.node_cap) w = 0;   // no room this round
+        W.ch_w[c] = w;
+        W.ch_off[c] = run;
+        run += w;
+    }
+    __syncthreads();
+    if (tid == nt - 1) W.ctl[WF_CTL_NODES] = min(part[nt - 1], W.node_cap);
+}
+
+// one warp per entry: the pilot's stopping rule over this round's draws, in
+// blocks of 32 (stop at the first block boundary >= pilot_min once some
+// draw had f > 0; draws evaluated past the stop are not counted)
+__global__ void __launch_bounds__(128) k_wfp_reduce(DScene S, KParams P, Pool B, DTables T, WfBufs W, int slots,
+                                                    int last_round) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int items = W.ctl[WF_CTL_ITEMS];
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < items; e += warps) {
+        if (W.ch_done[e]) continue;
+        const int w = W.ch_w[e], off = W.ch_off[e];
+        int next = W.pil_next[e];
+        float best = W.pil_best[e], sum = W.pil_sum[e];
+        int draws = W.pil_draws[e];
+        bool stop = false;
+        for (int b = 0; b < w; b += 32) {
+            if (next + b >= P.pilot_min && best > 0.0f) {
+                stop = true;
+                break;
+            }
+            float x = W.node_g[off + b + lane];
+            float m = x, t = x;
+            for (int o = 16; o > 0; o >>= 1) {
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                t += __shfl_xor_sync(0xffffffffu, t, o);
+            }
+            best = fmaxf(best, m);
+            sum += t;
+            draws += 32;
+        }
+        next += w;
+        if (!stop && next >= P.pilot_min && best > 0.0f) stop = true;
+        if (!stop && (next >= P.pilot_max || last_round)) stop = true;
+        if (lane == 0) {
+            W.pil_next[e] = next;
+            W.pil_best[e] = best;
+            W.pil_sum[e] = sum;
+            W.pil_draws[e] = draws;
+            if (stop) {
+                int slot, k;
+                wave_entry(B, P, slots, e, slot, k);
+                int Sp, C;
+                Entry E = load_entry(S, P, B, slot, k, Sp, C);
+                float Bv = best > 0.0f ? best : T.Bt[((E.u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
+                B.eB[(size_t)slot * B.ML + k] = Bv;
+                B.eMu[(size_t)slot * B.ML + k] = sum > 0.0f ? Bv * (float)draws / sum : 0.0f;
+                W.ch_done[e] = 1;
+            } else {
+                W.ch_win[e] = 2 * W.ch_win[e];
+            }
         }
     }
 }
@@ -908,11 +1035,29 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
         }
         bool stack_form = !pos;   // gst holds the authoritative stack
         int done = 0, trunc = 0;
+        // four chunks are loaded ahead of their walk (128 nodes per trip)
+        float gq[4];
+        int nq4[4];
         for (int j0 = 0; j0 < w && !done; j0 += 32) {
+            const int qi = (j0 >> 5) & 3;
+            if (qi == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int jj = j0 + 32 * q + lane;
+                    gq[q] = jj < w ? W.node_g[off + jj] : 1.0f;
+                    nq4[q] = jj < w ? W.node_n[off + jj] : 1;
+                }
+            }
             const int j = j0 + lane;
             const bool in = j < w;
-            const float g = in ? W.node_g[off + j] : 1.0f;
-            const int n = in ? W.node_n[off + j] : 1;
+            float g = gq[0];
+            int n = nq4[0];
+#pragma unroll
+            for (int q = 1; q < 4; ++q)
+                if (qi == q) {
+                    g = gq[q];
+                    n = nq4[q];
+                }
             const bool anyneg = __any_sync(0xffffffffu, in && g < 0.0f);
             if (!stack_form && !anyneg) {
                 // inclusive scan of (n - 1) over the chunk
@@ -1130,14 +1275,31 @@ void launch_recip(const DScene &S, const DTables &T, const KParams &P, const Poo
     k_recip_offsets<<<1, 32, 0, st>>>(P, B, slots);
     if (P.estimator == 0 && wf && wf->node_cap > 0) {
         const WfBufs W = *wf;
-        if (P.count) k_recip_pilot<true><<<num_sms * 4, 128, 0, st>>>(S, T, P, B, slots, iter_base);
-        else k_recip_pilot<false><<<num_sms * 4, 128, 0, st>>>(S, T, P, B, slots, iter_base);
+        if (P.pilot_max <= 0) {
+            // no pilot: the kernel writes the table bounds without drawing
+            k_recip_pilot<false><<<num_sms * 4, 128, 0, st>>>(S, T, P, B, slots, iter_base);
+        } else {
+            // the pilot as wavefront rounds: windows pilot_min, then doubling up to pilot_max
+            k_wfp_init<<<num_sms * 2, 256, 0, st>>>(P, B, W, slots);
+            const int nr = wf_pilot_rounds(P);
+            for (int round = 0; round < nr; ++round) {
+                k_wfp_plan<<<1, 1024, 0, st>>>(P, W);
+                k_wf_nodes<true><<<num_sms * 8, 256, 0, st>>>(B, W);
+                for (int s = 0; s <= WF_MAXQ; ++s) {
+                    k_wf_step<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s, iter_base, slots);
+                    if (s == WF_MAXQ) break;
+                    if (P.count) k_wf_trace<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+                    else k_wf_trace<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+                }
+                k_wfp_reduce<<<num_sms * 16, 128, 0, st>>>(S, P, B, T, W, slots, round == nr - 1 ? 1 : 0);
+            }
+        }
         k_wf_init<<<num_sms * 2, 256, 0, st>>>(P, B, W, slots);
         for (int round = 0; round < WF_ROUNDS; ++round) {
             k_wf_plan<<<1, 1024, 0, st>>>(P, B, W);
-            k_wf_nodes<<<num_sms * 8, 256, 0, st>>>(B, W);
+            k_wf_nodes<false><<<num_sms * 8, 256, 0, st>>>(B, W);
             for (int s = 0; s <= WF_MAXQ; ++s) {
-                k_wf_step<<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s, iter_base);
+                k_wf_step<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s, iter_base, slots);
                 if (s == WF_MAXQ) break;
                 if (P.count) k_wf_trace<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
                 else k_wf_trace<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);

@@ -239,10 +239,10 @@ def test_estimator_with_side_weighted_lobe_matches_oracle(N):
 @pytest.mark.parametrize("make", [lambda: scenes.projector(24, 24, lens_tris_per_cap=1500, flat=True),
                                   lambda: scenes.cornell(20, 16)])
 def test_wavefront_estimator_matches_phases_and_oracle(N, make):
-    """The wavefront schedule (all chains' node windows evaluated in stages,
-    queries answered by traversal-only kernels) gives the estimates of the
-    warp/block schedule: the same nodes, the same values up to the order of
-    double sums; and matches the oracle like the default schedule."""
+    """The wavefront schedule (the pilot and all chains' node windows
+    evaluated in stages, queries answered by traversal-only kernels) gives
+    the estimates of the warp/block schedule: the same nodes, the same values
+    up to rounding; and matches the oracle like the default schedule."""
     sc = make()
     o = O.Oracle(sc)
     tab = learned(sc, o, M=1500, M_p=1500, max_depth=8)
@@ -257,7 +257,11 @@ def test_wavefront_estimator_matches_phases_and_oracle(N, make):
         assert len(a["rhat"]) == len(b["rhat"]) > 0
         np.testing.assert_array_equal(a["entry_nodes"], b["entry_nodes"])
         np.testing.assert_array_equal(a["entry_sig"], b["entry_sig"])
-        np.testing.assert_allclose(b["rhat"], a["rhat"], rtol=1e-6)
+        # the bound B comes from the pilot kernel of each schedule: the same draws,
+        # but f/q compiled in different kernels may fuse multiply-adds differently,
+        # and an estimate sums about B/P terms g/B, which amplifies a last-bit
+        # difference of B along the chain
+        np.testing.assert_allclose(b["rhat"], a["rhat"], rtol=1e-4)
         np.testing.assert_array_equal(a["sig"], b["sig"])
         ref = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0)
         es = ref["entry_sig"] == b["entry_sig"]
