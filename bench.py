@@ -46,6 +46,27 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_iter_base(rank):
+    """First iteration number of a rank. Ranks are replicas: each renders its
+    own iterations (disjoint ranges), with no collective on the data path."""
+    return rank * (1 << 24)
+
+
+def job_ms(local_ms, dist=None, device="cpu"):
+    """Whole-job time of the timed region: the slowest rank's (MAX over ranks)."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(paths_per_rank, ws, total_ms):
+    """Whole-job throughput in Mpaths/s: the paths of all ranks over the slowest rank's time."""
+    return paths_per_rank * ws / (total_ms * 1e-3) / 1e6
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -349,7 +370,7 @@ def run_ours(args):
     frac = st["n_entries"] / float(n_learn * M)
     M_p = int(min(M, max(1, round(ENTRY_TARGET / max(frac, 1e-9)))))
     tables = r.tables_readback()
-    base_iter = rank * (1 << 24)
+    base_iter = rank_iter_base(rank)
     cfg = N.config(M=M, M_p=M_p, max_depth=DEPTH, spp=SPP, seed=7)
     trained = None
     if args.proposal == "learned":
@@ -383,13 +404,9 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1))
     if dist:
         dist.barrier()
-    total_ms = float(np.sum(times))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_ms(float(np.sum(times)), dist, "cuda")
     paths = W * H * SPP * args.steps * ws
-    value = paths / (total_ms * 1e-3) / 1e6
+    value = job_value(W * H * SPP * args.steps, ws, total_ms)
     # traversal work of one step (untimed counting run) -> algorithmic bytes
     cst = step(args.warmup + args.steps, count=True)
     mean = {k: float(np.mean([s[k] for s in stats])) for k in ("ms_light", "ms_pool", "ms_recip", "ms_mlp", "ms_eye")}
