@@ -471,6 +471,29 @@ def pin_floor_light(a=0.1, h=1.0, floor=1.0, albedo=0.5, ypos=(0.5, 0.3, 0.0), s
     return b.build(np.zeros((1, 1, 3)), cam)
 
 
+def pin_mirror_light(a=0.2, h=0.5, floor=1.0, ypos=(0.35, 0.3, 0.0), rough=0.03, spec_size=1e-3):
+    """Square emitter (half-size a, Le=1) at height h facing down, a GGX
+    conductor floor (half-size `floor`, roughness `rough`) at y=0 facing up,
+    and a tiny GGX conductor triangle at `ypos` facing down toward the floor:
+    light reaches the triangle through one near-mirror bounce (L S S)."""
+    b = _Builder()
+    light = b.add_material(material(LAMBERT, (0, 0, 0), Le=(1.0, 1.0, 1.0)))
+    mir = b.add_material(material(CONDUCTOR, (0.9, 0.9, 0.9), rough=rough))
+    spec = b.add_material(material(CONDUCTOR, (0.9, 0.9, 0.9), rough=0.1))
+    b.add_quad((0.0, h, 0.0), (a, 0, 0), (0, 0, a), (0, -1, 0), light)
+    b.add_quad((0.0, 0.0, 0.0), (floor, 0, 0), (0, 0, floor), (0, 1, 0), mir)
+    s = spec_size
+    c = np.array(ypos, np.float64)
+    tri = np.array([c + [-s, 0, -s], c + [s, 0, -s], c + [0, 0, s]])
+    t = np.array([[0, 1, 2]])
+    n = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+    if n[1] > 0:
+        t = t[:, ::-1]
+    b.add_mesh(tri, t, spec)
+    cam = [0, 2, -2, 0, 0, 0, 0, 1, 0, 40.0, 4, 4]
+    return b.build(np.zeros((1, 1, 3)), cam)
+
+
 def caustic_mini(W=16, H=16, rough=0.1):
     """Small open caustic scene: a 0.1 x 0.1 light above a diffuse floor and a
     tilted GGX mirror that focuses part of its light onto the floor (L S D E

@@ -311,6 +311,54 @@ def test_reciprocal_of_incomplete_pdf_diffuse_control_vertex_quadrature():
     assert abs(t.mean() - 1 / P) < 4 * t.std() / math.sqrt(len(t)) + 2e-3 / P
 
 
+def _mirror_light_P(sc, a, h):
+    """P of the L S S pin entry for a near-perfect floor mirror: unfolding the
+    mirror puts the light's image at height -h, and the light tracer's area
+    density at y_2 becomes p_L * int (cos0/pi) cos2/d^2 dA(y_0) over the image,
+    with d the unfolded distance (the mirror's sampling density is a
+    solid-angle delta, and reflection keeps the cosine at the light). Both
+    cosines are H/d for the parallel image, so this is the offset
+    point-to-rectangle integral, by inclusion-exclusion of corner terms."""
+    Y = sc["verts"].astype(np.float64)[sc["tris"][4]].mean(0)
+    H = h + Y[1]
+
+    def F(X, Z):
+        return math.copysign(1.0, X) * math.copysign(1.0, Z) * _corner(abs(X), abs(Z), H)
+
+    x1, x2, z1, z2 = -a - Y[0], a - Y[0], -a - Y[2], a - Y[2]
+    integral = F(x2, z2) - F(x1, z2) - F(x2, z1) + F(x1, z1)
+    return (1.0 / (4 * a * a)) * integral / math.pi
+
+
+def test_reciprocal_of_incomplete_pdf_two_dropped_vertices_mirror_closed_form():
+    """L S S, u = 2: the dropped vertices are the light vertex and a floor
+    mirror point. With floor roughness 0.03 (alpha ~ 1e-3, a lobe of about
+    2e-3 rad against a light image of 0.4 rad) P is the unfolded closed form
+    to well below the statistical tolerance. This exercises the BSDF density
+    at a dropped specular vertex on both sides of f/q, the distances of both
+    segments and the specular pattern check."""
+    a, h = 0.2, 0.5
+    sc = scenes.pin_mirror_light(a=a, h=h, rough=0.03)
+    P = _mirror_light_P(sc, a, h)
+    o = O.Oracle(sc)
+    e = O.Entry(4, 1 / 3, 1 / 3, 2, 0, -1, 0.0, 0.0)
+    f, q = o.entry_fq(e, 200000)
+    ratio = np.where(q > 0, f / np.where(q > 0, q, 1.0), 0.0)
+    assert 0.02 < (ratio > 0).mean() < 0.2
+    assert abs(ratio.mean() - P) < 4 * ratio.std() / math.sqrt(len(ratio))
+    t, i, nodes, tr = o.entry_recip(e, B=1.05 * ratio.max(), n=200000)
+    assert tr == 0
+    assert abs(t.mean() - 1 / P) < 4 * t.std() / math.sqrt(len(t))
+    assert abs(i.mean() - 1 / P) < 4 * i.std() / math.sqrt(len(i))
+    # the closed form itself against a midpoint rule over the light
+    Y = sc["verts"].astype(np.float64)[sc["tris"][4]].mean(0)
+    m, H = 400, h + Y[1]
+    xs = (np.arange(m) + 0.5) / m * 2 * a - a
+    X, Z = np.meshgrid(xs - Y[0], xs - Y[2], indexing="ij")
+    quad = (H * H / (X * X + Z * Z + H * H) ** 2).sum() * (2 * a / m) ** 2
+    assert abs(quad / (math.pi * 4 * a * a) - P) < 1e-5 * P
+
+
 @pytest.mark.parametrize("flip", [False, True])
 def test_dielectric_vertex_side_weighted_lobe_is_unbiased(flip):
     """u = 1 with y_{s-1} on a dielectric: P is the same closed form as for a
@@ -337,7 +385,7 @@ def test_dielectric_vertex_side_weighted_lobe_is_unbiased(flip):
     assert nodes[right] < nodes[1 - right]
 
 
-@pytest.mark.parametrize("scene", ["square", "floor"])
+@pytest.mark.parametrize("scene", ["square", "floor", "mirror"])
 def test_pilot_bound_keeps_incomplete_pdf_estimate_unbiased(scene):
     """The per-entry bound B is the largest f/q of a pilot on a stream the
     estimate never reads (kind PILOT). It usually sits below the supremum, so
@@ -349,11 +397,16 @@ def test_pilot_bound_keeps_incomplete_pdf_estimate_unbiased(scene):
         P = (1.0 / (4 * a * a)) * (1 / math.pi) * 4 * _corner(a, a, h)
         e = O.Entry(2, 1 / 3, 1 / 3, 1, 0, -1, 0.0, 0.0)
         tol = 0.0
-    else:
+    elif scene == "floor":
         sc = scenes.pin_floor_light(a=0.1, h=1.0, floor=1.0, ypos=(0.5, 0.3, 0.0))
         P = _floor_light_P(sc)
         e = O.Entry(4, 1 / 3, 1 / 3, 1, 1, 0, 0.5, 0.5)
         tol = 2e-3 / P
+    else:
+        sc = scenes.pin_mirror_light(a=0.2, h=0.5, rough=0.03)
+        P = _mirror_light_P(sc, 0.2, 0.5)
+        e = O.Entry(4, 1 / 3, 1 / 3, 2, 0, -1, 0.0, 0.0)
+        tol = 0.0
     o = O.Oracle(sc)
     B = o.entry_pilot(e, seed=1, a=9, b=0, min_draws=64, max_draws=1024)
     f, q = o.entry_fq(e, 20000)
