@@ -434,6 +434,56 @@ def test_pilot_bound_stopping_rule():
         assert b256 >= b32
 
 
+def test_learned_tables_obey_their_definitions():
+    """Properties fixed by the learning rules (Sec. 5.4-5.5, Sec. 6.1.1),
+    checked on subspaces that no vertex can be labelled with (centroids moved
+    far outside the normalised box) and on the rest:
+    - a Gamma row is 0.9 x a normalised contribution share + 0.1 uniform, so it
+      sums to 1, no entry is below 0.1/K, and a column that never holds a
+      light vertex is exactly 0.1/K; a row whose eye subspace never occurs
+      stays uniform;
+    - a B cell that no entry reaches takes the largest learned value;
+    - a MIS cell that no entry reaches takes the pooled mean(R)/mean(R^2).
+      That ratio of sums is a convex combination of every occupied cell's
+      r1/r2 (weights r2), so it is at most the largest of them. It may sit
+      below the smallest printed one, because a cell whose estimates sum to
+      a negative value (R is a signed estimate) enters the pooled sums but
+      itself takes the pooled value;
+    - the tile probabilities are 1.0 or 0.2, and all 0.2 with the proxy
+      strategy off, when the proxy selection rows also stay uniform."""
+    sc = scenes.cornell(16, 16)
+    tab = scenes.random_tables(sc, KT=8, KS=8, KSp=6, KC=2, seed=2)
+    far_S, far_Sp, far_T = [2, 5], [1, 4], [3]
+    tab["cent_S"][far_S, :3] = 9.0
+    tab["cent_Sp"][far_Sp, :3] = 9.0
+    tab["cent_T"][far_T, :3] = 9.0
+    o = O.Oracle(sc)
+    L = o.learn(O.params(M=400, M_p=400, max_depth=6), tab, 100, 2, n_bsamples=24)
+    for g, far in ((L["gamma_conn"], far_S), (L["gamma_proxy"], far_Sp)):
+        K = g.shape[1]
+        np.testing.assert_allclose(g.sum(1), 1.0, rtol=1e-6)
+        assert np.all(g >= np.float32(0.1 / K) * (1 - 1e-6))
+        np.testing.assert_array_equal(g[far_T], np.float32(1.0 / K))
+        live = [r for r in range(g.shape[0]) if r not in far_T and not np.all(g[r] == np.float32(1.0 / K))]
+        assert len(live) >= 3
+        for r in live:
+            np.testing.assert_array_equal(g[r, far], np.float32(0.1 / K))
+    B, mis = L["B_tab"], L["mis_tab"]
+    assert np.all(B > 0)
+    np.testing.assert_array_equal(B[:, far_Sp, :], B.max())
+    pooled = mis[:, far_Sp, :]
+    assert np.all(pooled == pooled.flat[0])
+    occ = np.ones(B.shape, bool)
+    occ[:, far_Sp, :] = False
+    occ &= mis != pooled.flat[0]
+    assert occ.sum() >= 5
+    assert 0 < pooled.flat[0] <= mis[occ].max() * (1 + 1e-6)
+    assert set(np.unique(L["pi_grid"])) <= {np.float32(0.2), np.float32(1.0)}
+    L0 = o.learn(O.params(M=400, M_p=400, max_depth=6, proxy=0), tab, 100, 1, n_bsamples=8)
+    np.testing.assert_array_equal(L0["pi_grid"], np.float32(0.2))
+    np.testing.assert_array_equal(L0["gamma_proxy"], np.float32(1.0 / 6))
+
+
 # --- whole estimator ------------------------------------------------------------
 
 def _render_mean(sc, tab, n_iter, **kw):
