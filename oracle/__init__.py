@@ -96,6 +96,8 @@ def lib():
         L.or_bsdf_sample_x.argtypes = [vp, vp, vp, C.c_double, C.c_double, C.c_double, vp]
         L.or_recip_1d.restype = C.c_int
         L.or_recip_1d.argtypes = [C.c_int, C.c_double, C.c_int, C.c_uint32, C.c_int, vp, vp, vp]
+        L.or_recip_1d_booth.restype = C.c_int
+        L.or_recip_1d_booth.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_uint32, C.c_int, vp, vp, vp]
         L.or_entry_fq.argtypes = [vp, C.POINTER(Entry), C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, vp, vp]
         L.or_bf16.restype = C.c_double
         L.or_bf16.argtypes = [C.c_double]
@@ -111,6 +113,9 @@ def lib():
         L.or_entry_pilot.argtypes = [vp, C.POINTER(Entry), C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_int]
         L.or_entry_recip.restype = C.c_int
         L.or_entry_recip.argtypes = [vp, C.POINTER(Entry), C.c_double, C.c_int, C.c_uint32, C.c_int, vp, vp, vp]
+        L.or_entry_recip_booth.restype = C.c_int
+        L.or_entry_recip_booth.argtypes = [vp, C.POINTER(Entry), C.c_double, C.c_double, C.c_int, C.c_uint32,
+                                           C.c_int, vp, vp, vp]
         L.or_light_pass.argtypes = [vp, C.POINTER(Params), C.c_int, vp, vp]
         L.or_iteration.argtypes = [vp, C.POINTER(Params), C.POINTER(TablesDesc), C.c_int, vp, vp, C.c_int,
                                    C.c_int, vp, vp, vp, C.c_int, vp, vp, vp, vp, C.POINTER(Stats)]
@@ -249,11 +254,12 @@ class Oracle:
     def entry_pilot(self, entry, seed=1, a=0, b=0, min_draws=64, max_draws=1024):
         return self.L.or_entry_pilot(self.h, C.byref(entry), seed, a, b, min_draws, max_draws)
 
-    def entry_recip(self, entry, B, n, seed=1, cap=1 << 16):
+    def entry_recip(self, entry, B, n, seed=1, cap=1 << 16, booth=0.0):
         t = np.zeros(n, np.float64)
         i = np.zeros(n, np.float64)
         nn = np.zeros(n, np.float64)
-        tr = self.L.or_entry_recip(self.h, C.byref(entry), B, n, seed, cap, _p(t), _p(i), _p(nn))
+        tr = self.L.or_entry_recip_booth(self.h, C.byref(entry), B, float(booth), n, seed, cap, _p(t), _p(i),
+                                         _p(nn))
         return t, i, nn, tr
 
 
@@ -334,11 +340,13 @@ def mlp_adam(w, g, m1, m2, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return w, m1, m2
 
 
-def recip_1d(fn, B, n, seed=1, cap=1 << 20):
+def recip_1d(fn, B, n, seed=1, cap=1 << 20, booth=0.0):
+    """booth > 0: Booth's Russian roulette with that scale instead of the
+    paper's RRS function."""
     t = np.zeros(n, np.float64)
     i = np.zeros(n, np.float64)
     nn = np.zeros(n, np.float64)
-    tr = lib().or_recip_1d(fn, B, n, seed, cap, _p(t), _p(i), _p(nn))
+    tr = lib().or_recip_1d_booth(fn, B, float(booth), n, seed, cap, _p(t), _p(i), _p(nn))
     return t, i, nn, tr
 
 

@@ -14,7 +14,17 @@
  * visit() walks the tree in pre-order and adds each node's term. Node v
  * draws its variates from the counter-based stream with word c = its
  * pre-order index. A node cap bounds the work; reaching it truncates the
- * estimate and is reported. */
+ * estimate and is reported.
+ *
+ * Booth's Russian roulette (the baseline of the paper's RR ablation, Sec. 4.2
+ * and Fig. RR-ablation) uses the same Taylor terms on one chain without
+ * splitting: the k-vertex prefix continues with probability
+ * rho_k = min(1, c * prod_{i<k} |g_i|), and the prefix's term is
+ * prod_{i<k} g_i / prod_{1<=j<k} rho_j (Eq. RRS_estimator). The printed
+ * factor is 1/r for a hyper-parameter r of order 10^2..10^3; it is read as
+ * the weight cutoff 1/r, i.e. c = r (with c = 1/r every step would survive
+ * with probability at most 1/r, which cannot improve as r grows to 10^3,
+ * as the ablation reports). c > 0 selects this rule; c = 0 the paper's. */
 #include "or_internal.h"
 
 typedef struct {
@@ -25,6 +35,7 @@ typedef struct {
     uint32_t cap, next;
     int truncated;
     double sum_t, sum_i;
+    double booth;       /* > 0: Booth's roulette with scale c (no splitting); 0: the paper's RRS */
 } rec_state;
 
 static void visit(rec_state *st, double sign_anc) {
@@ -47,13 +58,36 @@ static void visit(rec_state *st, double sign_anc) {
     }
 }
 
-/* one estimate: returns I~, sets *I (Alg. I), *nodes, *trunc */
+/* Booth's roulette: one chain; node k holds the k+1-vertex prefix */
+static void walk_booth(rec_state *st) {
+    double prod = 1.0;   /* prod_{i<=k} g_i */
+    double surv = 1.0;   /* prod of the continuation probabilities taken so far */
+    for (;;) {
+        if (st->next >= st->cap) {
+            st->truncated = 1;
+            return;
+        }
+        uint32_t node = st->next++;
+        prod *= 1.0 - st->ratio(st->ctx, node) / st->B;
+        st->sum_t += prod / surv / st->B;
+        double rho = st->booth * fabs(prod);
+        if (rho > 1.0) rho = 1.0;
+        if (!(st->unif(st->ctx, node) < rho)) return;
+        surv *= rho;
+    }
+}
+
+/* one estimate: returns I~, sets *I (Alg. I; 0 under Booth's roulette),
+ * *nodes, *trunc */
 static double estimate(rec_state *st, double *I, double *nodes, int *trunc) {
     st->next = 0;
     st->truncated = 0;
     st->sum_t = 0.0;
     st->sum_i = 0.0;
-    visit(st, 1.0);
+    if (st->booth > 0.0)
+        walk_booth(st);
+    else
+        visit(st, 1.0);
     *I = st->sum_i;
     *nodes = (double)st->next;
     *trunc = st->truncated;
@@ -79,11 +113,14 @@ static double one_d_ratio(void *c, uint32_t node) {
         f = 3.0 * x * x;
         q = 1.0;
         break;
-    default:
+    case 2:
         x = (u0 < 0.5) ? u1 : sqrt(u1);
         f = 3.0 * x * x;
         q = 0.5 * 1.0 + 0.5 * (2.0 * x);
         break;
+    default:   /* f = q: the ratio is exactly 1 (integral 1) */
+        (void)u0;
+        return 1.0;
     }
     return f / q;
 }
@@ -95,8 +132,13 @@ static double one_d_unif(void *c, uint32_t node) {
 
 int or_recip_1d(int fn, double B, int n_runs, uint32_t seed, int trial_cap, double *out_t,
                 double *out_i, double *out_n) {
+    return or_recip_1d_booth(fn, B, 0.0, n_runs, seed, trial_cap, out_t, out_i, out_n);
+}
+
+int or_recip_1d_booth(int fn, double B, double c, int n_runs, uint32_t seed, int trial_cap, double *out_t,
+                      double *out_i, double *out_n) {
     one_d o = {fn, seed, 0};
-    rec_state st = {one_d_ratio, one_d_unif, &o, B, (uint32_t)trial_cap, 0, 0, 0, 0};
+    rec_state st = {one_d_ratio, one_d_unif, &o, B, (uint32_t)trial_cap, 0, 0, 0, 0, c};
     int ntr = 0;
     for (int r = 0; r < n_runs; ++r) {
         o.run = (uint32_t)r;
@@ -396,11 +438,16 @@ void or_entry_fq(void *hs, const or_entry *en, int n, uint32_t seed, uint32_t a,
 
 int or_entry_recip(void *hs, const or_entry *en, double B, int n, uint32_t seed, int trial_cap,
                    double *out_t, double *out_i, double *out_n) {
+    return or_entry_recip_booth(hs, en, B, 0.0, n, seed, trial_cap, out_t, out_i, out_n);
+}
+
+int or_entry_recip_booth(void *hs, const or_entry *en, double B, double c, int n, uint32_t seed, int trial_cap,
+                         double *out_t, double *out_i, double *out_n) {
     entry_ctx e;
     entry_setup(&e, (const or_scene_t *)hs, en);
     e.seed = seed;
     e.kind = K_RECIP;
-    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)trial_cap, 0, 0, 0, 0};
+    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)trial_cap, 0, 0, 0, 0, c};
     int ntr = 0;
     for (int i = 0; i < n; ++i) {
         e.a = 0xFFFFu;

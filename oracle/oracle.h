@@ -91,11 +91,15 @@ int or_bsdf_sample_x(const float *mat, const double *n, const double *wg, double
 
 /* Reciprocal estimator on a 1-D test integrand (pins; see or_recip.c).
  * fn: 0 f=1+sin(2 pi x)/2 on [0,1], q uniform; 1 f=3x^2, q uniform;
- *     2 f=3x^2, q = 0.5 uniform + 0.5 * 2x.
+ *     2 f=3x^2, q = 0.5 uniform + 0.5 * 2x; 3 f = q (the ratio is 1).
  * out_t[i] = I~, out_i[i] = I (sign estimator), out_n[i] = nodes; returns
  * the number of truncated runs. */
 int or_recip_1d(int fn, double B, int n_runs, uint32_t seed, int trial_cap, double *out_t,
                 double *out_i, double *out_n);
+/* The same with Booth's Russian roulette of scale c > 0 in place of the
+ * paper's RRS function (one chain, no splitting; out_i is 0). */
+int or_recip_1d_booth(int fn, double B, double c, int n_runs, uint32_t seed, int trial_cap, double *out_t,
+                      double *out_i, double *out_n);
 
 /* One incomplete light sub-path, as stored in the pool. */
 typedef struct {
@@ -119,6 +123,9 @@ double or_entry_pilot(void *h, const or_entry *e, uint32_t seed, uint32_t a, uin
 /* n independent reciprocal estimates (Alg. I~ and I) for entry e with bound B. */
 int or_entry_recip(void *h, const or_entry *e, double B, int n, uint32_t seed, int trial_cap,
                    double *out_t, double *out_i, double *out_n);
+/* The same with Booth's Russian roulette of scale c > 0. */
+int or_entry_recip_booth(void *h, const or_entry *e, double B, double c, int n, uint32_t seed, int trial_cap,
+                         double *out_t, double *out_i, double *out_n);
 
 /* Light pass of one iteration: light sub-path geometry. tri/bary are
  * [M][max_depth-1] (tri = -1 past the end). */

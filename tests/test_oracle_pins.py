@@ -99,6 +99,89 @@ def test_main_estimator_beats_sign_estimator(fn, B):
     assert t.var() <= i.var() * 1.001
 
 
+# --- Booth's Russian roulette (the baseline of the paper's RR ablation) -----------
+
+def _booth_law(B, c, kmax=400):
+    """Exact law of Booth's roulette when f/q = 1 (beta = 1, g = 1 - 1/B on
+    every node): the chain's node count K and the estimate for each K. The
+    k-vertex prefix continues with probability min(1, c |g|^k) and its term is
+    g^k over the product of the earlier continuation probabilities."""
+    g = 1.0 - 1.0 / B
+    reach, est = [1.0], []
+    surv, acc, prod = 1.0, 0.0, 1.0
+    for k in range(1, kmax + 1):
+        prod *= g
+        acc += prod / surv
+        est.append((1.0 + acc) / B)
+        rho = min(1.0, c * abs(prod))
+        reach.append(reach[-1] * rho)
+        surv *= rho
+        if reach[-1] < 1e-300:
+            break
+    reach = np.array(reach)
+    return reach[:-1] - reach[1:], np.array(est)
+
+
+@pytest.mark.parametrize("B,c", [(2.0, 4.0), (1.25, 10.0), (0.8, 3.0), (4.0, 100.0)])
+def test_booth_roulette_constant_ratio_exact_law(B, c):
+    """With f/q = 1 the only randomness is the roulette: the estimate is a
+    fixed function of the node count K, whose law is explicit. The law's
+    exact mean is 1/beta = 1 (unbiasedness of the rule, including a
+    negative g when B < 1); every oracle estimate must equal the law's value
+    for its K, and the K frequencies must match the law."""
+    pK, est = _booth_law(B, c)
+    assert abs((pK * est[:len(pK)]).sum() - 1.0) < 1e-9
+    n = 100000
+    t, i, nn, tr = O.recip_1d(3, B, n, booth=c)
+    assert tr == 0
+    K = nn.astype(np.int64)
+    assert K.min() >= 1 and K.max() <= len(pK)
+    np.testing.assert_allclose(t, est[K - 1], rtol=1e-12, atol=1e-12)
+    freq = np.bincount(K, minlength=len(pK) + 1)[1:] / n
+    big = pK > 1e-4
+    z = np.abs(freq[big] - pK[big]) / np.sqrt(pK[big] * (1 - pK[big]) / n)
+    assert z.max() < 4.5, z.max()
+    assert abs(nn.mean() - (pK * np.arange(1, len(pK) + 1)).sum()) < 0.02 * nn.mean()
+
+
+@pytest.mark.parametrize("fn", [0, 1, 2])
+def test_booth_roulette_is_unbiased_on_1d_integrands(fn):
+    """B = 1.5 is the maximum of f/q for fn 0 and below it for fn 1 and 2
+    (signed terms). Booth's rule has heavy tails (rare long chains carry
+    large weights), so the tolerance uses the spread of batch means."""
+    t, i, nn, tr = O.recip_1d(fn, 1.5, 800000, booth=100.0)
+    assert tr == 0
+    bm = t.reshape(8, -1).mean(1)
+    assert abs(t.mean() - 1.0) < 4 * bm.std(ddof=1) / math.sqrt(len(bm)) + 1e-3
+
+
+def test_booth_roulette_on_an_incomplete_sub_path_and_the_ablation_claim():
+    """u = 1 square-light entry (closed form as above): Booth's roulette is
+    unbiased for every scale, and the paper's RRS function (Eq. rr) has a
+    lower variance x mean-nodes product than Booth's at each scale tried
+    (the paper's RR ablation: ours wins whatever r). The best scale sits
+    inside the range, as the ablation reports for its r."""
+    a, h = 0.1, 0.5
+    o = O.Oracle(scenes.pin_square_light(a=a, h=h))
+    P = (1.0 / (4 * a * a)) * (1 / math.pi) * 4 * _corner(a, a, h)
+    e = O.Entry(2, 1 / 3, 1 / 3, 1, 0, -1, 0.0, 0.0)
+    f, q = o.entry_fq(e, 20000)
+    B = 1.05 * np.where(q > 0, f / np.where(q > 0, q, 1.0), 0.0).max()
+    t, _, nn, tr = o.entry_recip(e, B=B, n=100000)
+    assert tr == 0
+    ours = t.var() * nn.mean()
+    cost = {}
+    for c in (10.0, 100.0, 1000.0, 10000.0):
+        t, _, nn, tr = o.entry_recip(e, B=B, n=100000, booth=c)
+        assert tr == 0
+        bm = t.reshape(10, -1).mean(1)
+        assert abs(t.mean() - 1 / P) < 4 * bm.std(ddof=1) / math.sqrt(len(bm))
+        cost[c] = t.var() * nn.mean()
+        assert ours < cost[c], (c, ours, cost[c])
+    best = min(cost, key=cost.get)
+    assert best not in (10.0, 10000.0), cost
+
+
 def test_estimator_diverges_outside_convergence_domain():
     """App. "Convergence Condition": (1/B) int f must lie in (0, 2); at
     B = 0.45 (ratio 2.2) the splitting tree grows without bound and hits
