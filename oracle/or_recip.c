@@ -359,9 +359,10 @@ static void entry_setup(entry_ctx *e, const or_scene_t *s, const or_entry *en) {
 }
 
 /* Reciprocal of the incomplete sub-path pdf for one entry: the mean of
- * `repeats` independent estimates I~ (Sec. 6.1.1 averages 5). Stream:
+ * `repeats` independent estimates I~ (Sec. 6.1.1 averages 5), with Booth's
+ * roulette of scale `booth` when it is positive. Stream:
  * kind RECIP, a = iteration, b = entry*8 + repeat, c = node. */
-double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, uint32_t seed,
+double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, double booth, uint32_t seed,
                      uint32_t iteration, uint32_t entry, int repeats, int cap, double *nodes,
                      int *trunc, uint32_t *sig) {
     entry_ctx e;
@@ -369,7 +370,7 @@ double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, uint32_t
     e.seed = seed;
     e.kind = K_RECIP;
     e.a = iteration;
-    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)cap, 0, 0, 0, 0};
+    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)cap, 0, 0, 0, 0, booth};
     double acc = 0.0, nn = 0.0;
     int tr = 0;
     uint32_t h = 2166136261u;

@@ -31,7 +31,7 @@
 #include "or_internal.h"
 
 double or_fwd_density(const or_scene_t *s, const or_vtx *ys, int j);
-double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, uint32_t seed,
+double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, double booth, uint32_t seed,
                      uint32_t iteration, uint32_t entry, int repeats, int cap, double *nodes,
                      int *trunc, uint32_t *sig);
 double or_pilot_B(const or_scene_t *s, const or_entry *en, uint32_t seed, uint32_t iteration, uint32_t entry,
@@ -304,7 +304,7 @@ static void build_iter(const or_scene_t *s, const or_params *p, const or_tab *T,
         double nodes;
         int trunc;
         uint32_t sg;
-        it->rhat[k] = or_entry_rhat(s, &it->ent[k], B, p->seed, iteration, (uint32_t)k, p->repeats,
+        it->rhat[k] = or_entry_rhat(s, &it->ent[k], B, p->booth, p->seed, iteration, (uint32_t)k, p->repeats,
                                     p->trial_cap, &nodes, &trunc, &sg);
         if (st) {
             st->n_nodes += (int64_t)nodes;
@@ -793,9 +793,12 @@ void or_render(void *hs, const or_params *p, const or_tables_desc *td, int iter0
  * to expected contribution, learned during the first iterations, then
  * frozen). Grid: proxy share of the weighted contribution per tile; >= 5%
  * -> probability 1.0, else 0.2 (Sec. 6.1.1). */
-void or_learn(void *hs, const or_params *p, const or_tables_desc *td, int iter0, int n_iter, int n_bsamples,
+void or_learn(void *hs, const or_params *p_in, const or_tables_desc *td, int iter0, int n_iter, int n_bsamples,
               float *B_out, float *mis_out, float *gconn_out, float *gproxy_out, float *pi_out) {
     const or_scene_t *s = (const or_scene_t *)hs;
+    or_params p_learn = *p_in;
+    p_learn.booth = 0.0;   /* statistics are learned with the paper's RRS function */
+    const or_params *p = &p_learn;
     or_tab T;
     tab_init(&T, td);
     int ncell = 4 * T.KSp * (T.KC + 1);

@@ -63,6 +63,8 @@ typedef struct {
     int pilot_min;     /* pilot draws per entry for its B, at least (rounded up to 32) */
     int pilot_max;     /* at most; 0 = no pilot (B from the table) */
     double side_in;    /* cosine draws at a dielectric y_{s-1} toward y_{s-2} (0: 0.5) */
+    double booth;      /* > 0: Booth's Russian roulette of this scale in the reciprocal estimates
+                        * (learning always uses the paper's RRS function) */
 } or_params;
 
 typedef struct {

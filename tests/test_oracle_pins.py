@@ -604,9 +604,10 @@ def test_furnace_with_glass_sphere_converges_to_closed_form():
 
 
 def test_proxy_on_off_and_path_tracing_agree_per_pixel():
-    """Unbiasedness (Sec. 4.1, 5.2): with independent seeds, proxy on,
-    proxy off, and plain PT+NEE give per-pixel means of a caustic scene that
-    agree within their standard errors (z-scores of an N(0,1) family)."""
+    """Unbiasedness (Sec. 4.1, 5.2): with independent seeds, proxy on (with
+    the paper's RRS function or Booth's roulette), proxy off, and plain
+    PT+NEE give per-pixel means of a caustic scene that agree within their
+    standard errors (z-scores of an N(0,1) family)."""
     sc = scenes.caustic_mini(8, 8)
     o = O.Oracle(sc)
     tab = scenes.random_tables(sc, KT=8, KS=8, KSp=4, KC=2)
@@ -628,8 +629,9 @@ def test_proxy_on_off_and_path_tracing_agree_per_pixel():
     m_on, v_on, k_on = run(7, n, proxy=1)
     m_off, v_off, _ = run(8, n, proxy=0)
     m_pt, v_pt, _ = run(9, n, proxy=0, conn=0)
-    assert k_on > 500
-    for m, v in ((m_on, v_on), (m_off, v_off)):
+    m_bo, v_bo, k_bo = run(10, n, proxy=1, booth=100.0)   # Booth's roulette in the proxy estimates
+    assert k_on > 500 and k_bo > 500
+    for m, v in ((m_on, v_on), (m_off, v_off), (m_bo, v_bo)):
         den = np.sqrt(v + v_pt)
         live = den > 0
         z = (m[live] - m_pt[live]) / den[live]
