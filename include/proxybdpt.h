@@ -130,6 +130,15 @@ typedef struct {
      * answered by traversal-only kernels, then a warp walk per chain);
      * 1 = a warp phase then a block phase per chain. */
     int estimator;
+    /* Russian roulette of the reciprocal estimator (Sec. 4.2): 0 = the
+     * paper's RRS function r = |g| with splitting (Eq. rr); c > 0 = Booth's
+     * roulette, the baseline of the paper's RR ablation: one chain without
+     * splitting, whose k-node prefix continues with probability
+     * min(1, c * prod_{i<k} |g_i|) (the printed factor 1/r read as a weight
+     * cutoff, c = r). Both are unbiased. Booth's runs on the wavefront
+     * schedule only (estimator 0; PB_ERR_ARG otherwise); table learning
+     * always uses the paper's function. */
+    float booth;
 } pb_config;
 
 typedef struct {
@@ -268,7 +277,8 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
  * d_B[n] (bound B > 0 per entry). Device outputs: d_rhat[n], d_nodes[n] (total
  * estimator nodes over the repeats, may be NULL). *n_truncated (may be NULL)
  * counts entries with a repeat that hit trial_cap. Only cfg->seed, repeats
- * and trial_cap are read from cfg. */
+ * and trial_cap are read from cfg (the roulette is always the paper's RRS
+ * function). */
 #define PB_NOALLOC_MAX_ESTIMATES 16384
 pb_status pb_recip_estimates_noalloc(pb_ctx *ctx, const pb_config *cfg, int iteration, int n,
                                      const int32_t *d_tri, const float *d_bary, const int32_t *d_info,

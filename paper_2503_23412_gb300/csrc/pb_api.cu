@@ -130,6 +130,9 @@ pb_status check_cfg(pb_ctx *ctx, const pb_config *c) {
     if (c->proposal < 0 || c->proposal > 1) return fail(ctx, PB_ERR_ARG, "proposal must be 0 (table) or 1 (learned)");
     if (!(c->side_in >= 0.0f && c->side_in < 1.0f)) return fail(ctx, PB_ERR_ARG, "side_in must lie in [0, 1)");
     if (c->estimator < 0 || c->estimator > 1) return fail(ctx, PB_ERR_ARG, "estimator must be 0 or 1");
+    if (!(c->booth >= 0.0f && c->booth < 3.0e38f)) return fail(ctx, PB_ERR_ARG, "booth must be finite and >= 0");
+    if (c->booth > 0.0f && c->estimator != 0)
+        return fail(ctx, PB_ERR_ARG, "Booth's roulette runs on the wavefront estimator (estimator 0) only");
     return PB_OK;
 }
 
@@ -158,6 +161,7 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
     }
     P.side_in = c->side_in > 0.0f ? c->side_in : 0.5f;
     P.estimator = c->estimator;
+    P.booth = c->booth;
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
     P.smp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
@@ -825,11 +829,16 @@ static std::string tune_key(const pb_ctx *ctx, const pb_config *cfg) {
         while ((1ll << (b + 1)) <= v) ++b;
         return b;
     };
-    char buf[160];
+    char buf[192];
     std::snprintf(buf, sizeof(buf), "tris2^%d|pix2^%d|depth%d|M%d|Mp%d|rep%d|prop%d|proxy%d", lg(ctx->S.nt),
                   lg((long long)ctx->S.W * ctx->S.H), cfg->max_depth, cfg->M, cfg->M_p, cfg->repeats, cfg->proposal,
                   cfg->proxy);
-    return std::string(buf);
+    std::string key(buf);
+    if (cfg->booth > 0.0f) {   // Booth's roulette has one schedule and its own chain lengths
+        std::snprintf(buf, sizeof(buf), "|booth%g", (double)cfg->booth);
+        key += buf;
+    }
+    return key;
 }
 
 extern "C" {
@@ -954,13 +963,15 @@ pb_status pb_autotune(pb_ctx *ctx, const pb_config *cfg, int trial_iters, pb_con
     if (from_cache) *from_cache = 0;
     int n = trial_iters > 0 ? trial_iters : 32;
     const int batches[] = {4, 8, 16, 32};
-    const int schedules[] = {0, 1};   // wavefront, warp/block phases
+    const int schedules[] = {0, 1};   // wavefront, warp/block phases (Booth's roulette: wavefront only)
+    const int n_sched = cfg->booth > 0.0f ? 1 : 2;
     TuneEntry bestE{0, 0, 1e300};
     std::vector<cudaEvent_t> ev;
     bool warmed = false;
     for (int b : batches) {
         if (b > n) continue;
-        for (int h : schedules) {
+        for (int hi = 0; hi < n_sched; ++hi) {
+            const int h = schedules[hi];
             pb_config c = *cfg;
             c.batch = b;
             c.estimator = h;

@@ -88,6 +88,7 @@ struct KParams {
     int pilot_min, pilot_max;   // per-entry B pilot draws (multiples of 32; pilot_max 0 = off)
     float side_in;              // cosine draws at a dielectric y_{s-1} on the side of y_{s-2}
     int estimator;              // 0: wavefront; 1: warp and block phases
+    float booth;                // > 0: Booth's roulette of this scale (wavefront only); 0: the paper's RRS
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
     SampleSink smp;         // raw != nullptr: record proposal training samples
@@ -120,6 +121,7 @@ struct ChainState {
     int sp;
     float fr_sign[PB_MAXF];
     int fr_rem[PB_MAXF];
+    double prod, surv;   // Booth's roulette: product of g so far, product of the continuation probabilities
 };
 
 // Device buffers of the iterations in flight ("slots"). Per-light-vertex

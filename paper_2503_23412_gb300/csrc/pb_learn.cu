@@ -299,6 +299,7 @@ extern "C" pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_lear
     pb_status s = upload_tables();
     if (s != PB_OK) return s;
     KParams P = pb_kparams(ctx, cfg);
+    P.booth = 0.0f;   // statistics are learned with the paper's RRS function
     int slots = std::max(1, std::min(ld->n_iter, std::max(1, (1 << 20) / std::max(1, P.npix))));
     s = pb_ensure_pool(ctx, slots, P.M * P.L, P.repeats);
     if (s != PB_OK) return s;

@@ -732,6 +732,8 @@ __global__ void k_wf_init(KParams P, Pool B, WfBufs W, int slots) {
         st.sum_t = 0.0;
         st.cur_sign = 1.0f;
         st.sp = 0;
+        st.prod = 1.0;
+        st.surv = 1.0;
         B.chains[c] = st;
         W.ch_done[c] = 0;
         // first window: about half the expected chain length, 64 .. 2048 nodes
@@ -1164,6 +1166,87 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
     }
 }
 
+// Booth's roulette (one chain, no splitting; Sec. 4.2's RR ablation): node j
+// of a chain adds prod_{i<=j} g_i over the product of the continuation
+// probabilities taken before it, and the chain continues past j with
+// probability rho_j = min(1, c |prod_{i<=j} g_i|), drawn with the node's RRS
+// uniform. A warp takes 32 consecutive nodes at a time: product scans give
+// each lane its prefix product and survival, and a ballot finds the first
+// node whose roulette ends the chain.
+__global__ void __launch_bounds__(128) k_wf_walk_booth(KParams P, Pool B, WfBufs W, uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int items = W.ctl[WF_CTL_ITEMS];
+    const double cb = (double)P.booth;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < items; c += warps) {
+        const int w = W.ch_w[c];
+        if (W.ch_done[c] || w == 0) continue;
+        ChainState &gst = B.chains[c];
+        const int slot = gst.slot, k = gst.k, rep = gst.rep;
+        const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
+        const int off = W.ch_off[c];
+        int next = gst.next;
+        double sum_t = gst.sum_t, prod = gst.prod, surv = gst.surv;
+        int done = 0, trunc = 0;
+        for (int j0 = 0; j0 < w && !done; j0 += 32) {
+            const bool in = j0 + lane < w;
+            double pg = in ? (double)W.node_g[off + j0 + lane] : 1.0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const double y = __shfl_up_sync(FULL, pg, o);
+                if (lane >= o) pg *= y;
+            }
+            const double pr = prod * pg;   // product of g through this node
+            const double rho = fmin(1.0, cb * fabs(pr));
+            bool stop = false;
+            if (in) {
+                Rng R;
+                R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)(next + lane));
+                stop = !((double)R.u(18) < rho);
+            }
+            double rs = in ? rho : 1.0;    // survival through this node
+            for (int o = 1; o < 32; o <<= 1) {
+                const double y = __shfl_up_sync(FULL, rs, o);
+                if (lane >= o) rs *= y;
+            }
+            double before = __shfl_up_sync(FULL, rs, 1);
+            if (lane == 0) before = 1.0;
+            const unsigned stopm = __ballot_sync(FULL, stop);
+            const int cnt = min(32, w - j0);
+            const int last = stopm ? __ffs(stopm) - 1 : cnt - 1;
+            double t = (in && lane <= last) ? pr / (surv * before) * (double)invB : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+            sum_t += t;
+            next += last + 1;
+            prod = __shfl_sync(FULL, pr, last);
+            surv *= __shfl_sync(FULL, rs, last);
+            if (stopm) done = 1;
+        }
+        if (!done && next >= P.trial_cap) {
+            done = 1;
+            trunc = 1;
+        }
+        if (lane == 0) {
+            gst.next = next;
+            gst.sum_t = sum_t;
+            gst.prod = prod;
+            gst.surv = surv;
+            if (done) {
+                size_t o = ((size_t)slot * B.ML + k) * P.repeats + rep;
+                B.rep[o] = (float)((double)invB + sum_t);
+                B.repn[o] = (float)next;
+                B.reptr[o] = trunc;
+                W.ch_done[c] = 1;
+                atomicSub(&W.ctl[WF_CTL_ACTIVE], 1);
+            } else {
+                W.ch_win[c] = min(2 * W.ch_win[c], WF_WIN_MAX);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // chains the rounds left unfinished (deferred by the node capacity): one
 // thread each, inline draws, the same walk; counted in WF_CTL_ERR's high bits
 __global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t iter_base) {
@@ -1177,6 +1260,22 @@ __global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t
         Entry E = load_entry(S, P, B, st.slot, st.k, Sp, C);
         const float invB = 1.0f / B.eB[(size_t)st.slot * B.ML + st.k];
         int done = 0, trunc = 0;
+        while (!done && P.booth > 0.0f) {   // Booth's roulette, as k_wf_walk_booth
+            if (st.next >= P.trial_cap) {
+                done = trunc = 1;
+                break;
+            }
+            Rng R;
+            R.init(P.seed, K_RECIP, iter_base + st.slot, (uint32_t)(st.k * 8 + st.rep), (uint32_t)st.next);
+            float ratio = entry_ratio<false>(S, E, R, nullptr);
+            float gj = 1.0f - ratio * invB;
+            st.prod *= (double)gj;
+            st.sum_t += st.prod / st.surv * (double)invB;
+            st.next += 1;
+            const double rho = fmin(1.0, (double)P.booth * fabs(st.prod));
+            if (!((double)R.u(18) < rho)) done = 1;
+            else st.surv *= rho;
+        }
         while (!done) {
             if (st.next >= P.trial_cap) {
                 done = trunc = 1;
@@ -1304,7 +1403,8 @@ void launch_recip(const DScene &S, const DTables &T, const KParams &P, const Poo
                 if (P.count) k_wf_trace<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
                 else k_wf_trace<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
             }
-            k_wf_walk<<<num_sms * 16, 128, 0, st>>>(P, B, W);
+            if (P.booth > 0.0f) k_wf_walk_booth<<<num_sms * 16, 128, 0, st>>>(P, B, W, iter_base);
+            else k_wf_walk<<<num_sms * 16, 128, 0, st>>>(P, B, W);
         }
         k_wf_finish_rest<<<num_sms * 2, 128, 0, st>>>(S, P, B, W, iter_base);
         dim3 g2((B.ML + 127) / 128, slots);

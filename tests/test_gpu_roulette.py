@@ -1,0 +1,78 @@
+"""Booth's Russian roulette on the device (the baseline of the paper's RR
+ablation, Sec. 4.2) against the oracle's.
+
+Booth's rule runs one chain without splitting: the k-node prefix continues
+with probability min(1, c * prod |g_i|), and its term is prod g_i over the
+product of the earlier continuation probabilities. The device walks 32 nodes
+of a chain at a time with product scans and a ballot.
+
+Chain lengths are decided by comparing the node's RRS uniform with that
+probability, so they agree with the oracle's wherever the rounding of f/q
+does not move a comparison. The values agree less tightly than the paper's
+estimator. The paper's estimate is a sum of +-g/B terms. Booth's multiplies
+about 10^3 factors g, each carrying the device's FP32 error of f/q (about
+1e-6 relative, amplified by 1/|g| where f/q is close to B), so the error
+compounds along the chain.
+
+Emulating that error (1e-6 relative per node) on 600 Cornell estimates gives
+errors, relative to max(|a|, median |a|), with a median of 3e-7, a 99th
+percentile of 9e-6 and a maximum of 3e-4. The bounds below leave 30 to 100
+times that.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_23412_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2503_23412_gb300 import build
+    build.build()
+    from paper_2503_23412_gb300 import native
+    native.lib()
+    return native
+
+
+def test_booth_roulette_matches_oracle(N):
+    sc = scenes.cornell(20, 16)
+    o = O.Oracle(sc)
+    tab = scenes.random_tables(sc, KT=16, KS=16, KSp=8, KC=2)
+    tab = o.learn(O.params(M=1500, M_p=1500, max_depth=8), tab, 1000, 2, n_bsamples=48)
+    r = N.Renderer(sc, tab)
+    td = o.tables(tab)
+    p = O.params(M=1500, M_p=1500, max_depth=8, booth=100.0)
+    cfg = N.config(M=1500, M_p=1500, max_depth=8, booth=100.0)
+    n_ent = n_same = differs = 0
+    errs = []
+    for it in (3, 4):
+        tri, bary = o.light_pass(p, it)
+        ref = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0)
+        got = r.iteration(cfg, it, tri, bary)
+        assert len(ref["rhat"]) == len(got["rhat"]) > 0
+        es = ref["entry_sig"] == got["entry_sig"]
+        n_ent += len(es)
+        n_same += int(es.sum())
+        # the same node count in every repeat where the signatures agree
+        assert np.array_equal(ref["entry_nodes"][es], got["entry_nodes"][es])
+        a = ref["rhat"][es]
+        b = got["rhat"][es].astype(np.float64)
+        scale = np.maximum(np.abs(a), np.median(np.abs(a)))
+        errs.append(np.abs(a - b) / scale)
+        rrs = r.iteration(N.config(M=1500, M_p=1500, max_depth=8), it, tri, bary)
+        differs += int((rrs["entry_nodes"] != got["entry_nodes"]).sum())
+    err = np.concatenate(errs)
+    assert n_ent > 100 and n_same / n_ent >= 0.98
+    assert np.median(err) < 1e-5, np.median(err)
+    assert np.quantile(err, 0.99) < 1e-3, np.quantile(err, 0.99)
+    assert err.max() < 3e-2, err.max()
+    # Booth's chains are not the paper's RRS chains
+    assert differs > n_ent // 2
+    # and the warp/block schedule refuses the rule
+    with pytest.raises(N.PBError):
+        r.iteration(N.config(M=1500, M_p=1500, max_depth=8, booth=100.0, estimator=1), 3, tri, bary)
+    r.close()
