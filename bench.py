@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpaths/s and equal-time MAPE vs CPU oracle; learned vs plain proposal, 1 GB300"
 W, H, SPP, DEPTH, M = 256, 256, 64, 8, 10000   # projector workload; --workload small shrinks it
 ENTRY_TARGET = 400          # incomplete light sub-paths estimated per iteration (paper: up to 400)
+BOOTH = 0.0                 # --booth: Booth's Russian roulette scale in the estimator (0: the paper's RRS)
 WORKLOAD = ("projector 256x256, 64 spp, max depth 8: textured 0.1x0.1 emitter in an absorbing box, "
             "biconvex GGX dielectric lens (IOR 1.5, ~19.5k triangles), diffuse room; M=10000 light "
             "sub-paths/iteration, 5 reciprocal repeats, 300 eye / 300 light / 100 specular / 10 control subspaces")
@@ -173,7 +174,7 @@ def oracle_iteration_rate(o, td, M_p, it, npx, keep=False):
     extrapolated full-iteration rate W*H / (t_light + W*H * t_pixel) in
     Mpaths/s and the CPU seconds spent."""
     import oracle as O
-    p = O.params(M=M, M_p=M_p, max_depth=DEPTH)
+    p = O.params(M=M, M_p=M_p, max_depth=DEPTH, booth=BOOTH)
     t0 = time.perf_counter()
     tri, bary = o.light_pass(p, it)
     r = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0)
@@ -198,6 +199,10 @@ def oracle_sample(scene, M_p, npx=2048):
     desc = ("1 iteration, 1 thread: light pass (M=%d), reciprocal estimates (M_p=%d) and eye paths of %d of %d "
             "pixels (%.1f s); extrapolated to the full %dx%d iteration" % (M, M_p, npx, W * H, secs, W, H))
     return rate, desc, rgb
+
+
+def roulette_name():
+    return "paper's RRS function" if BOOTH <= 0 else "Booth's roulette, c = %g" % BOOTH
 
 
 def mape(x, ref):
@@ -228,7 +233,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpaths/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sample": desc, "M_p": M_p},
+           "config": {"workload": WORKLOAD, "sample": desc, "M_p": M_p, "roulette": roulette_name()},
            "cpu_baseline": {"value": v, "unit": "Mpaths/s", "cores": 1, "kind": "oracle", "sample": desc},
            "e2e": {"value": v, "unit": "Mpaths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -371,7 +376,7 @@ def run_ours(args):
     M_p = int(min(M, max(1, round(ENTRY_TARGET / max(frac, 1e-9)))))
     tables = r.tables_readback()
     base_iter = rank_iter_base(rank)
-    cfg = N.config(M=M, M_p=M_p, max_depth=DEPTH, spp=SPP, seed=7)
+    cfg = N.config(M=M, M_p=M_p, max_depth=DEPTH, spp=SPP, seed=7, booth=BOOTH)
     trained = None
     if args.proposal == "learned":
         # the network is trained before timing, like the tables
@@ -439,7 +444,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     study = None
-    if args.workload != "small" and args.proposal == "table":
+    if args.workload != "small" and args.proposal == "table" and BOOTH <= 0:
         study = equal_time_study(N, r, M_p, base_iter, total_ms / args.steps)
     cpu_v, cpu_desc, cpu_px = oracle_sample(sc, M_p)
     if study is not None:
@@ -458,7 +463,7 @@ def run_ours(args):
                    "stage_ms_per_step": mean, "entries_per_iteration": stats[-1]["n_entries"] / SPP,
                    "truncated_estimates_per_step": stats[-1]["n_truncated"],
                    "estimator_nodes_per_step": stats[-1]["n_nodes"], "parallelism": "replicas" if ws > 1 else "1 GPU",
-                   "proposal": args.proposal},
+                   "proposal": args.proposal, "roulette": roulette_name()},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom, sha),
                      "algorithmic_bytes_per_launch": b, "launch_ms": ms, "src_sha": sha},
@@ -477,7 +482,7 @@ def run_ours(args):
 
 
 def main():
-    global W, H, SPP, M, WORKLOAD
+    global W, H, SPP, M, WORKLOAD, BOOTH
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -489,7 +494,11 @@ def main():
                     help="small: the same scene and pipeline at 64x64, 4 spp, M=2000 (profiling captures); "
                          "batch: procedural scenes of uneven size in one graph launch")
     ap.add_argument("--scenes", type=int, default=16, help="scenes of the batch workload")
+    ap.add_argument("--booth", type=float, default=0.0,
+                    help="Booth's Russian roulette of this scale in the reciprocal estimator (the RR ablation's "
+                         "baseline; 0: the paper's RRS function)")
     args = ap.parse_args()
+    BOOTH = max(0.0, args.booth)
     if args.workload == "small":
         W, H, SPP, M = 64, 64, 4, 2000
         WORKLOAD = WORKLOAD.replace("256x256, 64 spp", "64x64, 4 spp").replace("M=10000", "M=2000")
