@@ -66,6 +66,10 @@ pb_status ensure_pool(pb_ctx *ctx, int slots, int ML, int repeats, int npix) {
     CK(cudaStreamSynchronize(ctx->stream));
     free_graphs(ctx);   // captured renders point into the old buffers
     free_all(ctx->pool_mem);
+    // until every buffer below exists, the next call must allocate again
+    ctx->cap_slots = ctx->cap_ML = ctx->cap_rep = ctx->cap_Lslots = 0;
+    ctx->Lbuf = nullptr;
+    ctx->sigbuf = nullptr;
     Pool &B = ctx->B;
     B = Pool{};
     B.slots = slots;
@@ -575,10 +579,6 @@ pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t
     if (cfg->proposal) return mlp_check_err(ctx);
     return PB_OK;
 }
-
-extern "C" {
-
-}  // extern "C"
 
 // ---- wavefront estimator buffers ------------------------------------------------
 constexpr int WF_NODE_CAP = 1 << 23;   // nodes per round (about 1 GB of state)
