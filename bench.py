@@ -167,38 +167,63 @@ def oracle_tables(scene):
     return o, o.tables(tab)
 
 
-def oracle_iteration_rate(o, td, M_p, it, npx, keep=False):
+def oracle_iteration_rate(o, td, M_p, it, npx, keep=False, threads=1):
     """CPU oracle, one iteration of the workload measured in two parts: the
     light side (light pass, pool, all reciprocal estimates) and the eye paths
-    of the first `npx` pixels (reusing those estimates). Returns the
-    extrapolated full-iteration rate W*H / (t_light + W*H * t_pixel) in
-    Mpaths/s and the CPU seconds spent."""
+    of the first `npx` pixels (reusing those estimates). With threads > 1 the
+    estimates (in small entry ranges) and the eye paths (split by pixel) run
+    on that many threads; the oracle only reads its scene, and its C calls
+    release the GIL. Returns the extrapolated full-iteration rate
+    W*H / (t_light + W*H * t_pixel) in Mpaths/s and the wall seconds spent."""
     import oracle as O
+    from concurrent.futures import ThreadPoolExecutor
     p = O.params(M=M, M_p=M_p, max_depth=DEPTH, booth=BOOTH)
     t0 = time.perf_counter()
     tri, bary = o.light_pass(p, it)
-    r = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0)
+    if threads > 1:
+        _, n = o.iteration_estimates(p, td, it, tri, bary, 0, 0)
+        parts = 4 * threads   # chain lengths vary widely: small ranges, taken as threads free up
+        ranges = [(n * i // parts, n * (i + 1) // parts) for i in range(parts)]
+        with ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(lambda kr: o.iteration_estimates(p, td, it, tri, bary, kr[0], kr[1])[0], ranges))
+        rhat = np.concatenate(parts)
+    else:
+        rhat = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0)["rhat"]
     t_light = time.perf_counter() - t0
     t0 = time.perf_counter()
-    o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0, rhat=r["rhat"])
+    o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0, rhat=rhat)
     t_pool = time.perf_counter() - t0
     t0 = time.perf_counter()
-    px = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=npx, rhat=r["rhat"])
+    if threads > 1:
+        ranges = [(npx * i // threads, npx * (i + 1) // threads) for i in range(threads)]
+        with ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(lambda pr: o.iteration(p, td, it, tri, bary, pix_lo=pr[0], pix_hi=pr[1],
+                                                       rhat=rhat)["rgb"], ranges))
+        rgb = np.concatenate(parts)
+    else:
+        rgb = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=npx, rhat=rhat)["rgb"]
     t_eye = max(time.perf_counter() - t0 - t_pool, 1e-9)
     rate = W * H / (t_light + W * H * t_eye / npx) / 1e6
     if keep:
-        return rate, t_light + t_pool + t_eye, np.asarray(px["rgb"], np.float64)
+        return rate, t_light + t_pool + t_eye, np.asarray(rgb, np.float64)
     return rate, t_light + t_pool + t_eye
 
 
+def oracle_threads():
+    return max(1, os.cpu_count() or 1)
+
+
 def oracle_sample(scene, M_p, npx=2048):
-    """Returns the extrapolated rate, its description and the sampled
-    pixels' 1-spp radiance (first `npx` pixels)."""
+    """Returns the extrapolated rate on all host cores, its description, the
+    thread count and the sampled pixels' 1-spp radiance (first `npx`
+    pixels)."""
     o, td = oracle_tables(scene)
-    rate, secs, rgb = oracle_iteration_rate(o, td, M_p, 0, npx, keep=True)
-    desc = ("1 iteration, 1 thread: light pass (M=%d), reciprocal estimates (M_p=%d) and eye paths of %d of %d "
-            "pixels (%.1f s); extrapolated to the full %dx%d iteration" % (M, M_p, npx, W * H, secs, W, H))
-    return rate, desc, rgb
+    nt = oracle_threads()
+    rate, secs, rgb = oracle_iteration_rate(o, td, M_p, 0, npx, keep=True, threads=nt)
+    desc = ("1 iteration on %d threads: light pass (M=%d), reciprocal estimates (M_p=%d, split by entry) and eye "
+            "paths of %d of %d pixels (split by pixel; %.1f s); extrapolated to the full %dx%d iteration"
+            % (nt, M, M_p, npx, W * H, secs, W, H))
+    return rate, desc, nt, rgb
 
 
 def roulette_name():
@@ -221,20 +246,22 @@ def run_reference(args):
     o, td = oracle_tables(sc)
     M_p = int(os.environ.get("PB_BENCH_MP", "1400"))
     npx = 1024
+    nt = oracle_threads()
     vals, secs = [], []
     for k in range(args.warmup + args.steps):
-        v, sec = oracle_iteration_rate(o, td, M_p, k, npx)
+        v, sec = oracle_iteration_rate(o, td, M_p, k, npx, threads=nt)
         if k >= args.warmup:
             vals.append(v)
             secs.append(sec)
     v = float(np.mean(vals))
-    desc = ("per step 1 iteration, 1 thread: light pass (M=%d), reciprocal estimates (M_p=%d), eye paths of %d "
-            "of %d pixels; extrapolated to the full iteration" % (M, M_p, npx, W * H))
+    desc = ("per step 1 iteration on %d threads: light pass (M=%d), reciprocal estimates (M_p=%d, split by "
+            "entry), eye paths of %d of %d pixels (split by pixel); extrapolated to the full iteration"
+            % (nt, M, M_p, npx, W * H))
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpaths/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "sample": desc, "M_p": M_p, "roulette": roulette_name()},
-           "cpu_baseline": {"value": v, "unit": "Mpaths/s", "cores": 1, "kind": "oracle", "sample": desc},
+           "cpu_baseline": {"value": v, "unit": "Mpaths/s", "cores": nt, "kind": "oracle", "sample": desc},
            "e2e": {"value": v, "unit": "Mpaths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -446,12 +473,13 @@ def run_ours(args):
     study = None
     if args.workload != "small" and args.proposal == "table" and BOOTH <= 0:
         study = equal_time_study(N, r, M_p, base_iter, total_ms / args.steps)
-    cpu_v, cpu_desc, cpu_px = oracle_sample(sc, M_p)
+    cpu_v, cpu_desc, cpu_nt, cpu_px = oracle_sample(sc, M_p)
     if study is not None:
         ref = study.pop("_ref")
         npx = len(cpu_px)
         study["mape"]["cpu_oracle_1spp"] = mape(cpu_px, ref[:npx])
-        study["cpu_oracle"] = {"spp": 1, "pixels": npx, "seconds_per_spp_full_image": W * H / (cpu_v * 1e6),
+        study["cpu_oracle"] = {"spp": 1, "pixels": npx, "threads": cpu_nt,
+                               "seconds_per_spp_full_image": W * H / (cpu_v * 1e6),
                                "note": "oracle's own learned tables; MAPE over its first %d pixels" % npx}
     out = {
         "metric": METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": ws, "steps": args.steps,
@@ -467,7 +495,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom, sha),
                      "algorithmic_bytes_per_launch": b, "launch_ms": ms, "src_sha": sha},
-        "cpu_baseline": {"value": cpu_v, "unit": "Mpaths/s", "cores": 1, "kind": "oracle", "sample": cpu_desc},
+        "cpu_baseline": {"value": cpu_v, "unit": "Mpaths/s", "cores": cpu_nt, "kind": "oracle", "sample": cpu_desc},
         "e2e": {"value": e2e, "unit": "Mpaths/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
         "gpu_launches": int(sum(s["n_launches"] for s in stats)),

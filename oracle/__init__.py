@@ -117,6 +117,9 @@ def lib():
         L.or_entry_recip_booth.argtypes = [vp, C.POINTER(Entry), C.c_double, C.c_double, C.c_int, C.c_uint32,
                                            C.c_int, vp, vp, vp]
         L.or_light_pass.argtypes = [vp, C.POINTER(Params), C.c_int, vp, vp]
+        L.or_iteration_estimates.restype = C.c_int
+        L.or_iteration_estimates.argtypes = [vp, C.POINTER(Params), C.POINTER(TablesDesc), C.c_int, vp, vp, C.c_int,
+                                             C.c_int, vp]
         L.or_iteration.argtypes = [vp, C.POINTER(Params), C.POINTER(TablesDesc), C.c_int, vp, vp, C.c_int,
                                    C.c_int, vp, vp, vp, C.c_int, vp, vp, vp, vp, C.POINTER(Stats)]
         L.or_entries.restype = C.c_int
@@ -221,6 +224,17 @@ class Oracle:
                             _p(en), C.byref(st))
         k = min(ne.value, cap)
         return dict(rgb=rgb, sig=sig, rhat=er[:k], entry_sig=es[:k], entry_nodes=en[:k], stats=st.as_dict())
+
+    def iteration_estimates(self, params, tables, iteration, tri, bary, k_lo, k_hi):
+        """Estimates of entries [k_lo, k_hi) of an iteration (as iteration()
+        computes them) and the iteration's entry count. The C call releases
+        the GIL and only reads the handle, so threads can share it."""
+        out = np.zeros(max(k_hi - k_lo, 1), np.float64)
+        tri = np.ascontiguousarray(tri, np.int32)
+        bary = np.ascontiguousarray(bary, np.float32)
+        n = self.L.or_iteration_estimates(self.h, C.byref(params), C.byref(tables), iteration, _p(tri), _p(bary),
+                                          k_lo, k_hi, _p(out))
+        return out[:max(0, min(k_hi, n) - k_lo)], n
 
     def render(self, params, tables, iter0, n_iter, pix_lo=0, pix_hi=None):
         pix_hi = self.W * self.H if pix_hi is None else pix_hi

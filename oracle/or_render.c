@@ -253,6 +253,20 @@ static int table_cell(const or_tab *T, int u, int Sp, int C) {
     return ((u - 1) * T->KSp + Sp) * (T->KC + 1) + C;
 }
 
+/* The reciprocal estimate of entry k of an iteration whose entries are
+ * labelled. B is the entry's pilot maximum of f/q, or the learned cell value
+ * when the pilot is off or saw only f = 0. */
+static double entry_estimate(const or_scene_t *s, const or_params *p, const or_tab *T, const or_iter *it,
+                             uint32_t iteration, int k, double *nodes, int *trunc, uint32_t *sig) {
+    double B = T->Bt[table_cell(T, it->ent[k].u, it->ent_Sp[k], it->ent_C[k])];
+    if (p->pilot_max > 0) {
+        double Bp = or_pilot_B(s, &it->ent[k], p->seed, iteration, (uint32_t)k, p->pilot_min, p->pilot_max);
+        if (Bp > 0.0) B = Bp;
+    }
+    return or_entry_rhat(s, &it->ent[k], B, p->booth, p->seed, iteration, (uint32_t)k, p->repeats, p->trial_cap,
+                         nodes, trunc, sig);
+}
+
 static void build_iter(const or_scene_t *s, const or_params *p, const or_tab *T, uint32_t iteration,
                        const int *tri, const float *bary, const double *rhat_override, or_iter *it,
                        double *entry_nodes, uint32_t *entry_sig, or_stats *st) {
@@ -294,18 +308,10 @@ static void build_iter(const or_scene_t *s, const or_params *p, const or_tab *T,
             it->rhat[k] = rhat_override[k];
             continue;
         }
-        /* B: the entry's pilot maximum of f/q; the learned cell value when
-         * the pilot is off or saw only f = 0 */
-        double B = T->Bt[table_cell(T, it->ent[k].u, it->ent_Sp[k], it->ent_C[k])];
-        if (p->pilot_max > 0) {
-            double Bp = or_pilot_B(s, &it->ent[k], p->seed, iteration, (uint32_t)k, p->pilot_min, p->pilot_max);
-            if (Bp > 0.0) B = Bp;
-        }
         double nodes;
         int trunc;
         uint32_t sg;
-        it->rhat[k] = or_entry_rhat(s, &it->ent[k], B, p->booth, p->seed, iteration, (uint32_t)k, p->repeats,
-                                    p->trial_cap, &nodes, &trunc, &sg);
+        it->rhat[k] = entry_estimate(s, p, T, it, iteration, k, &nodes, &trunc, &sg);
         if (st) {
             st->n_nodes += (int64_t)nodes;
             st->n_truncated += trunc;
@@ -756,6 +762,38 @@ void or_iteration(void *hs, const or_params *p, const or_tables_desc *td, int it
     free(nodes);
     free(esig);
     free_iter(&it);
+}
+
+/* The estimates of entries [k_lo, k_hi) of one iteration, the values
+ * or_iteration computes for them (lets a caller spread one iteration's
+ * estimates over threads; the handle is only read). Returns the number of
+ * entries of the iteration. */
+int or_iteration_estimates(void *hs, const or_params *p, const or_tables_desc *td, int iteration, const int *tri,
+                           const float *bary, int k_lo, int k_hi, double *out_rhat) {
+    const or_scene_t *s = (const or_scene_t *)hs;
+    or_tab T;
+    tab_init(&T, td);
+    int ncount;
+    {
+        or_iter tmp;
+        memset(&tmp, 0, sizeof(tmp));
+        build_lpaths(s, p, tri, bary, &tmp);
+        ncount = collect_entries(s, p, tmp.lp, 0, NULL, NULL, NULL);
+        free(tmp.lp);
+    }
+    double *zero = (double *)calloc((size_t)ncount + 1, sizeof(double));
+    or_iter it;
+    build_iter(s, p, &T, (uint32_t)iteration, tri, bary, zero, &it, NULL, NULL, NULL);
+    for (int k = k_lo < 0 ? 0 : k_lo; k < k_hi && k < it.nent; ++k) {
+        double nodes;
+        int trunc;
+        uint32_t sg;
+        out_rhat[k - k_lo] = entry_estimate(s, p, &T, &it, (uint32_t)iteration, k, &nodes, &trunc, &sg);
+    }
+    int n = it.nent;
+    free(zero);
+    free_iter(&it);
+    return n;
 }
 
 void or_render(void *hs, const or_params *p, const or_tables_desc *td, int iter0, int n_iter, int pix_lo,

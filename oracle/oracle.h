@@ -129,6 +129,12 @@ int or_entry_recip(void *h, const or_entry *e, double B, int n, uint32_t seed, i
 int or_entry_recip_booth(void *h, const or_entry *e, double B, double c, int n, uint32_t seed, int trial_cap,
                          double *out_t, double *out_i, double *out_n);
 
+/* Reciprocal estimates of entries [k_lo, k_hi) of one iteration, equal to
+ * those or_iteration computes (out_rhat[k - k_lo]); returns the iteration's
+ * entry count. Only reads the handle, so threads may share it. */
+int or_iteration_estimates(void *h, const or_params *p, const or_tables_desc *td, int iteration, const int *tri,
+                           const float *bary, int k_lo, int k_hi, double *out_rhat);
+
 /* Light pass of one iteration: light sub-path geometry. tri/bary are
  * [M][max_depth-1] (tri = -1 past the end). */
 void or_light_pass(void *h, const or_params *p, int iteration, int *tri, float *bary);
