@@ -157,12 +157,27 @@ typedef struct {
     double batch_ms;           /* pb_render_batch: device time of the whole batch (first entry only) */
 } pb_stats;
 
+/* Creates a context on CUDA device `device`. cuda_stream: a cudaStream_t
+ * the caller owns and keeps alive (all work of the context is issued on it),
+ * or NULL for a stream the context creates and owns. *out receives the
+ * context. PB_ERR_ARG for a NULL out, PB_ERR_CUDA if the device cannot be
+ * used (no context is returned then). */
 pb_status pb_create(pb_ctx **out, int device, void *cuda_stream /* NULL: own stream */);
+/* Waits for the context's work, frees all its device memory, captured
+ * graphs and its own stream (never a caller's stream). NULL is a no-op. */
 void pb_destroy(pb_ctx *ctx);
+/* One-line description of the last error on ctx ("null context" for NULL);
+ * the string stays valid until the next call on ctx. */
 const char *pb_last_error(const pb_ctx *ctx);
 
-/* Builds the BVH on the host (binned SAH) and uploads scene and BVH. */
+/* Builds the BVH on the host (binned SAH), checks its structure, and uploads
+ * scene and BVH. Replaces any earlier scene and drops captured graphs. */
 pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *scene);
+/* Copies the tables to the device, replacing earlier ones and dropping
+ * captured graphs. PB_ERR_ARG on sizes out of range (every K >= 1, KS and
+ * KSp <= 1023, KC <= 1000, tile >= 1, grid_w x grid_h = the image in tiles),
+ * a NULL array or a B entry that is not positive; PB_ERR_STATE before a
+ * scene upload. */
 pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *tables);
 
 /* Renders n scenes (one context each, same device, each context at most
@@ -181,7 +196,8 @@ pb_status pb_render_batch(pb_ctx *const *ctxs, const pb_config *cfgs, int n, pb_
  * pair into *best. Results are cached per size bucket (log2 of the triangle and
  * pixel counts, depth, M, M_p, repeats, proposal, proxy) for the process;
  * *from_cache (may be NULL) tells whether the cache answered. Neither
- * parameter changes an image beyond the estimator's summation order. */
+ * parameter changes an image beyond the estimator's summation order. With
+ * booth > 0 only the wavefront schedule is tried, under its own cache key. */
 pb_status pb_autotune(pb_ctx *ctx, const pb_config *cfg, int trial_iters, pb_config *best, int *from_cache);
 /* the cache as text lines "bucket batch estimator ms_per_iteration" */
 pb_status pb_autotune_cache_save(const char *path);
