@@ -210,7 +210,12 @@ def oracle_iteration_rate(o, td, M_p, it, npx, keep=False, threads=1):
 
 
 def oracle_threads():
-    return max(1, os.cpu_count() or 1)
+    """Host cores this process may run on (its CPU affinity), at most 64."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        n = os.cpu_count() or 1
+    return max(1, min(64, n))
 
 
 def oracle_sample(scene, M_p, npx=2048):
