@@ -331,6 +331,56 @@ def test_hierarchy_matches_brute_force():
     assert 0 < oa.mean() < 1
 
 
+# --- light sub-paths (Sec. 3.2) --------------------------------------------------
+
+def test_light_pass_first_vertices_follow_area_and_cosine_emission():
+    """y_0 is uniform over the emitter (area x power sampling with one
+    emitter) and y_1 is where the cosine-distributed emission first lands.
+    On the floor below a square light (half-size a, height h) y_1 has the
+    density (1/(4a^2)) (1/pi) int_light h^2 / d^4 dA(y_0). That is the same
+    corner integral as the u = 1 pin, evaluated here by a midpoint rule per
+    bin of a 4x4 floor grid. Bin counts must match within binomial noise."""
+    a, h = 0.1, 1.0
+    sc = scenes.pin_floor_light(a=a, h=h, floor=1.0, ypos=(0.5, 0.3, 0.0))
+    o = O.Oracle(sc)
+    p = O.params(M=20000, M_p=0, max_depth=3)
+    V = sc["verts"].astype(np.float64)
+    Tr = sc["tris"]
+    y0, y1, n = [], [], 0
+    for it in range(10):
+        tri, bary = o.light_pass(p, it)
+        n += tri.shape[0]
+        for col, out in ((0, y0), (1, y1)):
+            ok = tri[:, col] >= 0
+            t, b = tri[ok, col], bary[ok, col].astype(np.float64)
+            v = V[Tr[t]]
+            out.append(v[:, 0] + b[:, :1] * (v[:, 1] - v[:, 0]) + b[:, 1:2] * (v[:, 2] - v[:, 0]))
+    y0, y1 = np.concatenate(y0), np.concatenate(y1)
+    assert len(y0) == n
+    # y_0 on the light, uniform over its four quadrants
+    assert np.allclose(y0[:, 1], h) and np.all(np.abs(y0[:, [0, 2]]) <= a + 1e-6)
+    q = np.bincount((y0[:, 0] > 0) * 2 + (y0[:, 2] > 0), minlength=4) / n
+    assert np.all(np.abs(q - 0.25) < 4.5 * math.sqrt(0.25 * 0.75 / n))
+    # y_1 on the floor: 4x4 bins against the emission density
+    floor = np.abs(y1[:, 1]) < 1e-6
+    xs = y1[floor][:, [0, 2]]
+    cnt = np.histogram2d(xs[:, 0], xs[:, 1], bins=4, range=[[-1, 1], [-1, 1]])[0] / n
+    m = 40
+    g = (np.arange(m) + 0.5) / m * 2 * a - a
+    L0x, L0z = np.meshgrid(g, g, indexing="ij")
+    expect = np.zeros((4, 4))
+    f = (np.arange(m) + 0.5) / m * 0.5
+    for i in range(4):
+        for j in range(4):
+            fx, fz = np.meshgrid(-1 + 0.5 * i + f, -1 + 0.5 * j + f, indexing="ij")
+            d2 = (fx[..., None, None] - L0x) ** 2 + (fz[..., None, None] - L0z) ** 2 + h * h
+            dens = (h * h / d2 ** 2).mean(axis=(-1, -2)) / math.pi
+            expect[i, j] = dens.mean() * 0.25
+    z = np.abs(cnt - expect) / np.sqrt(expect * (1 - expect) / n)
+    assert z.max() < 4.5, z.max()
+    assert abs(cnt.sum() - expect.sum()) < 4.5 * math.sqrt(expect.sum() * (1 - expect.sum()) / n)
+
+
 # --- incomplete sub-path density (Sec. 5.2, Eq. reciprocalFinal) ------------------
 
 def _corner(A, B, h):
