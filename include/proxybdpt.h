@@ -49,7 +49,9 @@ typedef enum {
  *     is a specular vertex, Sec. 1 footnote), ior, Le rgb (front side),
  *     textured flag, 2 reserved;
  *   tex[tex_h*tex_w*3] emission texture (may be NULL when tex_w == 0);
- *   cam[12]: position, look-at, up, vertical fov (degrees), width, height.
+ *   cam[12]: position, look-at, up, vertical fov (degrees), width, height;
+ *     a pinhole with image x along forward x up (right-handed), image row 0
+ *     at the top, and a box-filtered sample per pixel and iteration.
  * Errors: PB_ERR_ARG on empty or inconsistent sizes, out-of-range indices. */
 typedef struct {
     int nv, nt, nm;

@@ -331,6 +331,47 @@ def test_hierarchy_matches_brute_force():
     assert 0 < oa.mean() < 1
 
 
+# --- camera -------------------------------------------------------------------------
+
+def test_pinhole_camera_sees_a_light_where_the_projection_puts_it():
+    """A fronto-parallel emitter rectangle seen by the pinhole camera. With
+    the camera's basis right = forward x up (right-handed), image row 0 at the
+    top, vertical fov and aspect W/H, the rectangle projects to an
+    axis-aligned screen rectangle, so every pixel's covered fraction is a
+    product of two interval overlaps. A pixel's value is Le times a box-filter
+    sample, so fully covered pixels read exactly Le, uncovered ones 0, and
+    partial ones average to their coverage. A flipped row order, a transposed
+    pixel index or a wrong fov or aspect fails this."""
+    W, H, vfov, xr, yr, z = 32, 24, 40.0, (0.1, 0.5), (0.05, 0.3), 2.0
+    sc = scenes.pin_visible_light(W, H, vfov, xr, yr, z)
+    o = O.Oracle(sc)
+    td = o.tables(scenes.random_tables(sc, KT=2, KS=2, KSp=2, KC=1))
+    p = O.params(M=10, M_p=0, max_depth=2, proxy=0, conn=0)
+    t = math.tan(math.radians(vfov) / 2)
+    aspect = W / H
+    # right = (0,0,1) x (0,1,0) = (-1,0,0): screen x grows toward -x
+    sx = sorted(-np.array(xr) / (z * t * aspect))
+    sy = sorted(np.array(yr) / (z * t))
+    px = (np.array(sx) + 1) / 2 * W                 # pixel-column interval
+    py = (1 - np.array(sy[::-1])) / 2 * H           # pixel-row interval (row 0 at the top)
+    cols = np.clip(np.minimum(np.arange(W) + 1, px[1]) - np.maximum(np.arange(W), px[0]), 0, 1)
+    rows = np.clip(np.minimum(np.arange(H) + 1, py[1]) - np.maximum(np.arange(H), py[0]), 0, 1)
+    cover = rows[:, None] * cols[None, :]
+    assert (cover == 1).sum() > 10 and (cover == 0).sum() > 100
+    n = 64
+    acc = np.zeros((H, W))
+    for it in range(n):
+        tri, bary = o.light_pass(p, it)
+        img = o.iteration(p, td, it, tri, bary)["rgb"][:, 0].reshape(H, W)
+        np.testing.assert_array_equal(img[cover == 1], 1.0)
+        np.testing.assert_array_equal(img[cover == 0], 0.0)
+        acc += img
+    part = (cover > 0) & (cover < 1)
+    assert part.sum() > 10
+    z_part = (acc[part] / n - cover[part]) / np.sqrt(cover[part] * (1 - cover[part]) / n)
+    assert np.abs(z_part).max() < 4.5
+
+
 # --- light sub-paths (Sec. 3.2) --------------------------------------------------
 
 def test_light_pass_first_vertices_follow_area_and_cosine_emission():
