@@ -494,16 +494,18 @@ def pin_mirror_light(a=0.2, h=0.5, floor=1.0, ypos=(0.35, 0.3, 0.0), rough=0.03,
     return b.build(np.zeros((1, 1, 3)), cam)
 
 
-def pin_visible_light(W=32, H=24, vfov=40.0, x=(0.1, 0.5), y=(0.05, 0.3), z=2.0):
+def pin_visible_light(W=32, H=24, vfov=40.0, x=(0.1, 0.5), y=(0.05, 0.3), z=2.0, tex=None):
     """Pinhole camera at the origin looking along +z (up +y) and one
     emitter rectangle x0..x1 by y0..y1 in the plane at depth z, facing the
-    camera (Le = 1); nothing else."""
+    camera (Le = 1, or the texture `tex` [th][tw][3] with u along +x from x0
+    and v along +y from y0); nothing else."""
     b = _Builder()
-    light = b.add_material(material(LAMBERT, (0, 0, 0), Le=(1.0, 1.0, 1.0)))
+    light = b.add_material(material(LAMBERT, (0, 0, 0), Le=(1.0, 1.0, 1.0), textured=tex is not None))
     cx, cy = 0.5 * (x[0] + x[1]), 0.5 * (y[0] + y[1])
-    b.add_quad((cx, cy, z), (0.5 * (x[1] - x[0]), 0, 0), (0, 0.5 * (y[1] - y[0]), 0), (0, 0, -1), light)
+    b.add_quad((cx, cy, z), (0.5 * (x[1] - x[0]), 0, 0), (0, 0.5 * (y[1] - y[0]), 0), (0, 0, -1), light,
+               uv=tex is not None)
     cam = [0, 0, 0, 0, 0, 1, 0, 1, 0, vfov, W, H]
-    return b.build(np.zeros((1, 1, 3)), cam)
+    return b.build(np.zeros((1, 1, 3)) if tex is None else tex, cam)
 
 
 def caustic_mini(W=16, H=16, rough=0.1):

@@ -372,6 +372,62 @@ def test_pinhole_camera_sees_a_light_where_the_projection_puts_it():
     assert np.abs(z_part).max() < 4.5
 
 
+def test_textured_emitter_is_the_bilinear_texture_at_the_hit_uv():
+    """Emission texture (the projector's emitter): texels hold an affine
+    function of their centres, R = 0.2 + 0.6 u and G = 0.3 + 0.5 v, with
+    B = 0.7. Bilinear interpolation between texel centres reproduces an
+    affine function exactly. So where a pixel's footprint maps inside the
+    texel-centre box, every sample must lie between the function's values at
+    the footprint's corners, and the mean must be its value at the pixel
+    centre (the plane is fronto-parallel, so uv is affine in the screen
+    position). Swapping u and v, flipping v, or misplacing texel centres fails
+    this."""
+    W, H, vfov, xr, yr, z = 32, 24, 40.0, (-0.6, 0.6), (-0.4, 0.4), 2.0
+    tw, th = 8, 6
+    iu = (np.arange(tw) + 0.5) / tw
+    iv = (np.arange(th) + 0.5) / th
+    tex = np.zeros((th, tw, 3), np.float32)
+    tex[..., 0] = 0.2 + 0.6 * iu[None, :]
+    tex[..., 1] = 0.3 + 0.5 * iv[:, None]
+    tex[..., 2] = 0.7
+    sc = scenes.pin_visible_light(W, H, vfov, xr, yr, z, tex=tex)
+    o = O.Oracle(sc)
+    td = o.tables(scenes.random_tables(sc, KT=2, KS=2, KSp=2, KC=1))
+    p = O.params(M=10, M_p=0, max_depth=2, proxy=0, conn=0)
+    t = math.tan(math.radians(vfov) / 2)
+    aspect = W / H
+
+    def uv(col, row):   # pixel-grid coordinates -> (u, v) on the light
+        sx = 2 * col / W - 1
+        sy = 1 - 2 * row / H
+        x, y = -sx * z * t * aspect, sy * z * t   # right = forward x up = -x
+        return (x - xr[0]) / (xr[1] - xr[0]), (y - yr[0]) / (yr[1] - yr[0])
+
+    C, R = np.meshgrid(np.arange(W), np.arange(H))
+    u0, v0 = uv(C, R)
+    u1, v1 = uv(C + 1, R + 1)
+    ulo, uhi = np.minimum(u0, u1), np.maximum(u0, u1)
+    vlo, vhi = np.minimum(v0, v1), np.maximum(v0, v1)
+    inside = (ulo >= iu[0]) & (uhi <= iu[-1]) & (vlo >= iv[0]) & (vhi <= iv[-1])
+    assert inside.sum() > 100
+    uc, vc = uv(C + 0.5, R + 0.5)
+    n, eps = 32, 2e-6
+    acc = np.zeros((H, W, 3))
+    for it in range(n):
+        tri, bary = o.light_pass(p, it)
+        img = o.iteration(p, td, it, tri, bary)["rgb"].reshape(H, W, 3)
+        r, g, b = img[..., 0][inside], img[..., 1][inside], img[..., 2][inside]
+        assert np.all(r >= 0.2 + 0.6 * ulo[inside] - eps) and np.all(r <= 0.2 + 0.6 * uhi[inside] + eps)
+        assert np.all(g >= 0.3 + 0.5 * vlo[inside] - eps) and np.all(g <= 0.3 + 0.5 * vhi[inside] + eps)
+        np.testing.assert_allclose(b, 0.7, atol=eps)
+        acc += img
+    mean = acc / n
+    sd_r = 0.6 * (uhi - ulo) / math.sqrt(12 * n)
+    sd_g = 0.5 * (vhi - vlo) / math.sqrt(12 * n)
+    assert np.all(np.abs(mean[..., 0] - (0.2 + 0.6 * uc))[inside] < 5 * sd_r[inside] + eps)
+    assert np.all(np.abs(mean[..., 1] - (0.3 + 0.5 * vc))[inside] < 5 * sd_g[inside] + eps)
+
+
 # --- light sub-paths (Sec. 3.2) --------------------------------------------------
 
 def test_light_pass_first_vertices_follow_area_and_cosine_emission():
