@@ -494,6 +494,19 @@ def pin_mirror_light(a=0.2, h=0.5, floor=1.0, ypos=(0.35, 0.3, 0.0), rough=0.03,
     return b.build(np.zeros((1, 1, 3)), cam)
 
 
+def pin_lit_floor(W=12, H=12, a=0.1, h=1.0, floor=1.0, albedo=0.5, cam_pos=(0.0, 2.0, -2.0)):
+    """Square emitter (half-size a, Le=1) at height h facing down over a
+    diffuse floor quad (half-size `floor`, albedo) at y=0; a W x H pinhole
+    camera at cam_pos looking at the origin (up +y, 40 degrees)."""
+    b = _Builder()
+    light = b.add_material(material(LAMBERT, (0, 0, 0), Le=(1.0, 1.0, 1.0)))
+    fl = b.add_material(material(LAMBERT, (albedo, albedo, albedo)))
+    b.add_quad((0.0, h, 0.0), (a, 0, 0), (0, 0, a), (0, -1, 0), light)
+    b.add_quad((0.0, 0.0, 0.0), (floor, 0, 0), (0, 0, floor), (0, 1, 0), fl)
+    cam = [cam_pos[0], cam_pos[1], cam_pos[2], 0, 0, 0, 0, 1, 0, 40.0, W, H]
+    return b.build(np.zeros((1, 1, 3)), cam)
+
+
 def pin_visible_light(W=32, H=24, vfov=40.0, x=(0.1, 0.5), y=(0.05, 0.3), z=2.0, tex=None):
     """Pinhole camera at the origin looking along +z (up +y) and one
     emitter rectangle x0..x1 by y0..y1 in the plane at depth z, facing the

@@ -723,6 +723,66 @@ def _render_mean(sc, tab, n_iter, **kw):
     return film / n_iter, st
 
 
+def test_direct_light_on_a_diffuse_floor_closed_form():
+    """Paths of at most two segments (camera -> floor -> light) under a square
+    light: the floor's outgoing radiance is (rho/pi) Le int cos cos' / d^2 dA
+    = (rho/pi) Le int h^2 / d^4 dA over the light, the offset
+    point-to-rectangle integral in corner form. Both strategies that make
+    these paths, an emitter hit and next-event estimation, are MIS-combined.
+    Pixels whose footprint lies wholly on the floor must match the footprint
+    average (a 16x16 sub-pixel midpoint rule through the pinhole model pinned
+    above) within their standard errors. Pixels that see no floor must be
+    exactly 0."""
+    W = H = 12
+    a, h, rho = 0.1, 1.0, 0.5
+    cam = np.array([0.0, 2.0, -2.0])
+    sc = scenes.pin_lit_floor(W, H, a, h, 1.0, rho, tuple(cam))
+    o = O.Oracle(sc)
+    td = o.tables(scenes.random_tables(sc, KT=2, KS=2, KSp=2, KC=1))
+    p = O.params(M=10, M_p=0, max_depth=2, proxy=0, conn=0)
+    n = 4000
+    vals = np.zeros((n, H, W))
+    for it in range(n):
+        tri, bary = o.light_pass(p, it)
+        vals[it] = o.iteration(p, td, it, tri, bary)["rgb"][:, 0].reshape(H, W)
+
+    def corner(A, B):
+        ra, rb = np.hypot(A, h), np.hypot(B, h)
+        return 0.5 * (A / ra * np.arctan(B / ra) + B / rb * np.arctan(A / rb))
+
+    def form(x, z):   # int over the light of h^2 / d^4 for floor points (x, 0, z)
+        def F(X, Z):
+            return np.sign(X) * np.sign(Z) * corner(np.abs(X), np.abs(Z))
+        x1, x2, z1, z2 = -a - x, a - x, -a - z, a - z
+        return F(x2, z2) - F(x1, z2) - F(x2, z1) + F(x1, z1)
+
+    fwd = -cam / np.linalg.norm(cam)
+    right = np.cross(fwd, [0.0, 1.0, 0.0])
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    t, S = math.tan(math.radians(20.0)), 16
+    f = (np.arange(S) + 0.5) / S
+    PY, PX, FJ, FI = np.meshgrid(np.arange(H), np.arange(W), f, f, indexing="ij")
+    sx, sy = 2 * (PX + FI) / W - 1, 1 - 2 * (PY + FJ) / H
+    d = fwd + right * (sx * t * W / H)[..., None] + up * (sy * t)[..., None]
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    down = d[..., 1] < 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ql = cam + ((h - cam[1]) / d[..., 1])[..., None] * d
+        qf = cam + (-cam[1] / d[..., 1])[..., None] * d
+    behind_light = down & (np.abs(ql[..., 0]) <= a) & (np.abs(ql[..., 2]) <= a)
+    floor = down & (np.abs(qf[..., 0]) <= 1.0) & (np.abs(qf[..., 2]) <= 1.0) & ~behind_light
+    full, empty = floor.all(axis=(2, 3)), (~floor).all(axis=(2, 3))
+    assert full.sum() > 50 and empty.sum() > 5
+    expect = (rho / math.pi) * form(qf[..., 0], qf[..., 2])[full].mean(axis=(1, 2))
+    m = vals.mean(0)[full]
+    se = vals.std(0, ddof=1)[full] / math.sqrt(n)
+    z = (m - expect) / se
+    assert np.abs(z).max() < 4.5, np.abs(z).max()
+    assert (z * z).mean() < 1.6, (z * z).mean()
+    assert np.all(vals[:, empty] == 0.0)
+
+
 def test_white_furnace_diffuse_enclosure():
     """All six inward walls emit Le and reflect with albedo rho; the camera
     sees Le * sum_{j<K} rho^j through paths of at most K segments, whatever
