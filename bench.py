@@ -224,10 +224,16 @@ def oracle_sample(scene, M_p, npx=2048):
     pixels)."""
     o, td = oracle_tables(scene)
     nt = oracle_threads()
-    rate, secs, rgb = oracle_iteration_rate(o, td, M_p, 0, npx, keep=True, threads=nt)
+    note = ""
+    try:
+        rate, secs, rgb = oracle_iteration_rate(o, td, M_p, 0, npx, keep=True, threads=nt)
+    except Exception as e:   # keep the bench line: time on one thread and say why
+        note = " (threaded timing failed: %s; timed on 1 thread)" % str(e).splitlines()[0][:120]
+        nt = 1
+        rate, secs, rgb = oracle_iteration_rate(o, td, M_p, 0, npx, keep=True, threads=1)
     desc = ("1 iteration on %d threads: light pass (M=%d), reciprocal estimates (M_p=%d, split by entry) and eye "
             "paths of %d of %d pixels (split by pixel; %.1f s); extrapolated to the full %dx%d iteration"
-            % (nt, M, M_p, npx, W * H, secs, W, H))
+            % (nt, M, M_p, npx, W * H, secs, W, H)) + note
     return rate, desc, nt, rgb
 
 
