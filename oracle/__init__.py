@@ -55,7 +55,8 @@ class TablesDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("max_depth", C.c_int), ("M", C.c_int), ("M_p", C.c_int),
                 ("repeats", C.c_int), ("proxy", C.c_int), ("trial_cap", C.c_int), ("conn", C.c_int),
-                ("pilot_min", C.c_int), ("pilot_max", C.c_int), ("side_in", C.c_double), ("booth", C.c_double)]
+                ("pilot_min", C.c_int), ("pilot_max", C.c_int), ("side_in", C.c_double), ("booth", C.c_double),
+                ("film", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -278,11 +279,14 @@ class Oracle:
 
 
 def params(seed=7, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, trial_cap=1 << 16, conn=1, pilot_min=64,
-           pilot_max=1024, side_in=0.0, booth=0.0):
+           pilot_max=1024, side_in=0.0, booth=0.0, film=0):
     """pilot_max = 0 turns the per-entry pilot off (B from the learned table);
     side_in = 0 is an even split of the cosine draws at dielectric vertices;
-    booth > 0 estimates with Booth's Russian roulette of that scale."""
-    return Params(seed, max_depth, M, M_p, repeats, proxy, trial_cap, conn, pilot_min, pilot_max, side_in, booth)
+    booth > 0 estimates with Booth's Russian roulette of that scale;
+    film = 1 keeps only the proxy strategy's weighted contributions in the
+    pixel values, 2 all but those (the strategies and weights are unchanged)."""
+    return Params(seed, max_depth, M, M_p, repeats, proxy, trial_cap, conn, pilot_min, pilot_max, side_in, booth,
+                  film)
 
 
 def philox(ctr, key):

@@ -502,7 +502,7 @@ static v3 eye_path(const or_scene_t *s, const or_tab *T, const or_params *p, con
                 double pa = strat_pdf(fwd, rev, x.n - 1, 0);
                 double w = mis_weight(s, T, p, &x, ST_PT, 0, pix);
                 v3 c = vscale(f, w / pa);
-                L = vadd(L, c);
+                if (p->film != 1) L = vadd(L, c);
                 if (acc) acc->tile_all[tile] += lum(c);
             }
         }
@@ -533,7 +533,7 @@ static v3 eye_path(const or_scene_t *s, const or_tab *T, const or_params *p, con
                         double pa = strat_pdf(fwd, rev, x.n - 1, 1);
                         double w = mis_weight(s, T, p, &x, ST_NEE, 1, pix);
                         v3 c = vscale(f, w / pa);
-                        L = vadd(L, c);
+                        if (p->film != 1) L = vadd(L, c);
                         if (acc) acc->tile_all[tile] += lum(c);
                     }
                 }
@@ -587,7 +587,7 @@ static v3 eye_path(const or_scene_t *s, const or_tab *T, const or_params *p, con
                                 double pa = strat_pdf(fwd, rev, x.n - 1, sl) * (double)it->M * Q;
                                 double w = mis_weight(s, T, p, &x, ST_CONN, sl, pix);
                                 v3 c = vscale(f, w / pa);
-                                L = vadd(L, c);
+                                if (p->film != 1) L = vadd(L, c);
                                 if (acc) {
                                     acc->tile_all[tile] += lum(c);
                                     acc->conn[(size_t)Tl * T->KS + it->pool_S[jp]] += lum(vscale(f, 1.0 / pa));
@@ -673,7 +673,7 @@ static v3 eye_path(const or_scene_t *s, const or_tab *T, const or_params *p, con
                             pa *= (double)it->M_p * Q * pi_pix;
                             double w = mis_weight(s, T, p, &x, ST_PROXY, 0, pix);
                             v3 c = vscale(f, w / pa);
-                            L = vadd(L, c);
+                            if (p->film != 2) L = vadd(L, c);
                             if (st) st->n_proxy_ok++;
                             if (acc) {
                                 acc->tile_all[tile] += lum(c);
@@ -836,6 +836,7 @@ void or_learn(void *hs, const or_params *p_in, const or_tables_desc *td, int ite
     const or_scene_t *s = (const or_scene_t *)hs;
     or_params p_learn = *p_in;
     p_learn.booth = 0.0;   /* statistics are learned with the paper's RRS function */
+    p_learn.film = 0;
     const or_params *p = &p_learn;
     or_tab T;
     tab_init(&T, td);

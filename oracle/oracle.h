@@ -65,6 +65,8 @@ typedef struct {
     double side_in;    /* cosine draws at a dielectric y_{s-1} toward y_{s-2} (0: 0.5) */
     double booth;      /* > 0: Booth's Russian roulette of this scale in the reciprocal estimates
                         * (learning always uses the paper's RRS function) */
+    int film;          /* strategies whose weighted contributions reach the pixel: 0 all, 1 the
+                        * proxy strategy only, 2 all but the proxy strategy */
 } or_params;
 
 typedef struct {

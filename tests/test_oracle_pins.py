@@ -783,6 +783,28 @@ def test_direct_light_on_a_diffuse_floor_closed_form():
     assert np.all(vals[:, empty] == 0.0)
 
 
+def test_film_modes_split_each_sample_into_proxy_and_the_rest():
+    """The film modes (used by the subspace-selection ablation, which renders
+    only the proxy strategy's paths) split every sample exactly: all
+    strategies = the proxy strategy's weighted contributions + the rest, and
+    both parts are non-zero somewhere on a caustic scene."""
+    sc = scenes.caustic_mini(8, 8)
+    o = O.Oracle(sc)
+    tab = scenes.random_tables(sc, KT=8, KS=8, KSp=4, KC=2)
+    tab = o.learn(O.params(M=300, M_p=300, max_depth=4), tab, 1000, 2, n_bsamples=64)
+    td = o.tables(tab)
+    seen = np.zeros(2, bool)
+    for it in range(40):
+        parts = []
+        for film in (0, 1, 2):
+            pp = O.params(seed=3, M=300, M_p=300, max_depth=4, film=film)
+            tri, bary = o.light_pass(pp, it)
+            parts.append(o.iteration(pp, td, it, tri, bary)["rgb"])
+        np.testing.assert_allclose(parts[0], parts[1] + parts[2], rtol=1e-12, atol=1e-300)
+        seen |= [parts[1].max() > 0, parts[2].max() > 0]
+    assert seen.all()
+
+
 def test_white_furnace_diffuse_enclosure():
     """All six inward walls emit Le and reflect with albedo rho; the camera
     sees Le * sum_{j<K} rho^j through paths of at most K segments, whatever
