@@ -321,6 +321,49 @@ def glossy(W=512, H=512, n_inst=2000, seed=1, n_lights=3):
     return b.build(np.zeros((1, 1, 3)), cam)
 
 
+def water(W=128, H=128, grid=48, depth=0.35, amp=0.015, rough=0.1, seed=3):
+    """Diffuse surfaces next to a specular one, for the subspace-selection
+    ablation: a 2 x 2 pool (diffuse floor albedo 0.6 at y = 0, diffuse walls
+    up to y = 0.5) filled to `depth` with water, a GGX dielectric (IOR 1.33)
+    heightfield of grid x grid cells whose height carries three seeded
+    sinusoidal waves of amplitude `amp`. A 0.3 x 0.3 light (Le = 10) hangs at
+    y = 2 off the centre, and the camera looks down into the pool at 45
+    degrees. Light reaches the floor through the surface (L S D), and the
+    camera sees the floor through it (D S E)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = _Builder()
+    floor_m = b.add_material(material(LAMBERT, (0.6, 0.6, 0.6)))
+    wall_m = b.add_material(material(LAMBERT, (0.5, 0.55, 0.6)))
+    water_m = b.add_material(material(DIELECTRIC, (1, 1, 1), rough=rough, ior=1.33))
+    light = b.add_material(material(LAMBERT, (0, 0, 0), Le=(10.0, 10.0, 10.0)))
+    b.add_quad((0.0, 0.0, 0.0), (1.0, 0, 0), (0, 0, 1.0), (0, 1, 0), floor_m)
+    for ax, sgn in ((0, -1.0), (0, 1.0), (2, -1.0), (2, 1.0)):
+        c = np.array([0.0, 0.25, 0.0])
+        c[ax] = sgn
+        eu = np.zeros(3)
+        eu[2 - ax] = 1.0
+        n = np.zeros(3)
+        n[ax] = -sgn
+        b.add_quad(c, eu, (0, 0.25, 0), n, wall_m)
+    k = rng.uniform(4.0, 9.0, (3, 2)) * rng.choice([-1.0, 1.0], (3, 2))
+    ph = rng.uniform(0, 2 * np.pi, 3)
+    g = np.linspace(-1.0, 1.0, grid + 1)
+    X, Z = np.meshgrid(g, g, indexing="ij")
+    Y = depth + amp / 3 * sum(np.sin(k[i, 0] * X + k[i, 1] * Z + ph[i]) for i in range(3))
+    verts = np.stack([X, Y, Z], -1).reshape(-1, 3)
+    idx = np.arange((grid + 1) ** 2).reshape(grid + 1, grid + 1)
+    a0, a1 = idx[:-1, :-1].ravel(), idx[1:, :-1].ravel()
+    b0, b1 = idx[:-1, 1:].ravel(), idx[1:, 1:].ravel()
+    tris = np.concatenate([np.stack([a0, b0, b1], 1), np.stack([a0, b1, a1], 1)])
+    v = verts[tris]
+    up = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])[:, 1] > 0
+    tris[~up] = tris[~up][:, ::-1]   # every surface triangle faces up (out of the water)
+    b.add_mesh(verts, tris, water_m)
+    b.add_quad((0.3, 2.0, 0.2), (0.15, 0, 0), (0, 0, 0.15), (0, -1, 0), light)
+    cam = [0.0, 1.8, -2.4, 0.0, 0.1, 0.0, 0, 1, 0, 45.0, W, H]
+    return b.build(np.zeros((1, 1, 3)), cam)
+
+
 def glossy_mix(W=256, H=256, n_tris=20000, seed=1, n_lights=3, glass=0.2, ggx=0.4):
     """A scene of the batched workload: seeded instances (icospheres of
     80..1280 triangles and boxes) in a 20^3 volume until about `n_tris`

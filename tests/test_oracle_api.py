@@ -30,3 +30,23 @@ def test_ranged_estimates_equal_the_iteration_on_threads():
         # a range past the end is clipped
         v, cnt = o.iteration_estimates(p, td, 3, tri, bary, n - 2, n + 5)
         np.testing.assert_array_equal(v, whole[n - 2:])
+
+
+def test_water_scene_has_diffuse_next_to_specular():
+    """The subspace-selection ablation's scene: the water surface faces up,
+    lies between the pool floor and the light, and the light's paths leave
+    incomplete sub-paths ending on it (L S, u = 1)."""
+    sc = scenes.water(16, 16)
+    V, T, mats = sc["verts"].astype(np.float64), sc["tris"], sc["mats"]
+    water = np.where(mats[sc["tri_mat"], 0] == 2)[0]
+    assert len(water) == 2 * 48 * 48
+    v = V[T[water]]
+    n = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    assert np.all(n[:, 1] > 0)
+    assert 0.3 < v[..., 1].min() and v[..., 1].max() < 0.4
+    o = O.Oracle(sc)
+    p = O.params(M=2000, M_p=2000, max_depth=6)
+    tri, bary = o.light_pass(p, 1)
+    ents, _ = o.entries(p, tri, bary)
+    assert len(ents) > 100 and all(e.u == 1 for e in ents)
+    assert all(mats[sc["tri_mat"][e.y_tri], 0] == 2 for e in ents)
