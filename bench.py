@@ -139,7 +139,9 @@ def src_sha(files):
 
 EYE_SRC = ["paper_2503_23412_gb300/csrc/pb_eye.cu", "paper_2503_23412_gb300/csrc/pb_device.cuh",
            "paper_2503_23412_gb300/csrc/pb_kernels.h"]
-REC_SRC = ["paper_2503_23412_gb300/csrc/pb_light.cu", "paper_2503_23412_gb300/csrc/pb_estimator.cuh",
+REC_SRC = ["paper_2503_23412_gb300/csrc/pb_light.cu", "paper_2503_23412_gb300/csrc/pb_recip.cu",
+           "paper_2503_23412_gb300/csrc/pb_recip_long.cuh", "paper_2503_23412_gb300/csrc/pb_wavefront.cu",
+           "paper_2503_23412_gb300/csrc/pb_entry.cuh", "paper_2503_23412_gb300/csrc/pb_estimator.cuh",
            "paper_2503_23412_gb300/csrc/pb_device.cuh", "paper_2503_23412_gb300/csrc/pb_kernels.h"]
 
 

@@ -165,6 +165,22 @@ void launch_pool_build(const DScene &S, const DTables &T, const KParams &P, cons
                        cudaStream_t st);
 void launch_recip(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
                   uint32_t iter_base, int num_sms, cudaStream_t st, const WfBufs *wf = nullptr);
+// the estimator's per-entry bound B (the pilot, or the table values when the
+// pilot is off) and its warp/block schedule (estimator = 1)
+void launch_recip_bounds(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
+                         uint32_t iter_base, int num_sms, cudaStream_t st, bool count);
+void launch_recip_phases(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
+                         uint32_t iter_base, int num_sms, cudaStream_t st);
+// phase 2 of that schedule, without and with traversal counting
+void launch_recip_long_plain(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
+                             uint32_t iter_base, int num_sms, cudaStream_t st);
+void launch_recip_long_counting(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
+                                uint32_t iter_base, int num_sms, cudaStream_t st);
+// the wavefront schedule of the estimator (pilot rounds when P.pilot_max > 0,
+// node rounds, finisher); launch_recip brackets it with the offsets, the
+// table-bound kernel when there is no pilot, and the repeat averages
+void launch_recip_wavefront(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
+                            uint32_t iter_base, int num_sms, cudaStream_t st, const WfBufs &W);
 void launch_eye(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                 float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st);
 void launch_eye_feat(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,

@@ -1,0 +1,673 @@
+// The reciprocal estimator's wavefront schedule (Sec. 4.2, App. Alg. I~, and
+// App. "Optimal value for B" for the per-entry pilot):
+//   k_wfp_*          the pilot of B as wavefront rounds
+//   k_wf_init/plan   windows of pre-order nodes per chain and round
+//   k_wf_nodes       the (chain, node) list of a round
+//   k_wf_step        replay of each node's draw up to its next ray query
+//   k_wf_trace       traversal-only answers to the recorded queries
+//   k_wf_walk        the paper's RRS walk per chain (warp scans)
+//   k_wf_walk_booth  Booth's roulette per chain (the RR ablation's baseline)
+//   k_wf_finish_rest chains still open after the last round
+#include <cstdio>
+
+#include <cooperative_groups.h>
+
+#include "pb_entry.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Wavefront estimator. Every (entry, repeat) of the wave is a chain. Each
+// round gives every unfinished chain a window of consecutive pre-order nodes
+// (sized from the entry's expected chain length, doubling while the chain
+// lasts), then evaluates all nodes of all windows in stages: a step kernel
+// replays a node's draw (entry_ratio with the replay tracer) up to its next
+// ray query, a traversal-only kernel answers the queries, and so on until
+// every node has its f/q. A walk per chain then consumes its window in
+// pre-order exactly as the sequential definition does. Node values depend
+// only on (entry, repeat, node), so the estimates are those of the warp and
+// block phases.
+enum { WF_CTL_ITEMS = 0, WF_CTL_NODES, WF_CTL_ACTIVE, WF_CTL_ERR, WF_CTL_CNT0 };   // CNT0 .. CNT0 + WF_MAXQ + 1
+constexpr int WF_WIN_MAX = 16384;
+
+__global__ void k_wf_init(KParams P, Pool B, WfBufs W, int slots) {
+    const int32_t *offs = B.work + 1;
+    int total = offs[slots];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        W.ctl[WF_CTL_ITEMS] = min(total, B.chain_cap);
+        W.ctl[WF_CTL_ACTIVE] = min(total, B.chain_cap);
+        W.ctl[WF_CTL_ERR] = total > B.chain_cap ? 1 : 0;
+    }
+    int items = min(total, B.chain_cap);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < items; c += gridDim.x * blockDim.x) {
+        int slot = 0;
+        while (c >= offs[slot + 1]) ++slot;
+        int local = c - offs[slot];
+        ChainState st;
+        st.slot = slot;
+        st.k = local / P.repeats;
+        st.rep = local % P.repeats;
+        st.next = 0;
+        st.sum_t = 0.0;
+        st.cur_sign = 1.0f;
+        st.sp = 0;
+        st.prod = 1.0;
+        st.surv = 1.0;
+        B.chains[c] = st;
+        W.ch_done[c] = 0;
+        // first window: about half the expected chain length, 64 .. 2048 nodes
+        float mu = B.eMu[(size_t)slot * B.ML + st.k];
+        int win = 256;
+        if (mu > 0.0f) {
+            win = 64;
+            while (win < 2048 && (float)win < 0.5f * mu) win <<= 1;
+        }
+        W.ch_win[c] = win;
+    }
+}
+
+// one block: windows of this round and their node offsets (exclusive scan)
+__global__ void __launch_bounds__(1024) k_wf_plan(KParams P, Pool B, WfBufs W) {
+    __shared__ int part[1024];
+    const int items = W.ctl[WF_CTL_ITEMS];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid <= WF_MAXQ + 1) W.ctl[WF_CTL_CNT0 + tid] = 0;
+    if (W.ctl[WF_CTL_ACTIVE] == 0) {
+        if (tid == 0) W.ctl[WF_CTL_NODES] = 0;
+        return;
+    }
+    const int per = (items + nt - 1) / nt;
+    const int c0 = tid * per, c1 = min(items, c0 + per);
+    int acc = 0;
+    for (int c = c0; c < c1; ++c) {
+        int w = 0;
+        if (!W.ch_done[c]) w = max(0, min(W.ch_win[c], P.trial_cap - B.chains[c].next));
+        W.ch_w[c] = w;
+        acc += w;
+    }
+    part[tid] = acc;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int x = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += x;
+        __syncthreads();
+    }
+    int run = part[tid] - acc;
+    for (int c = c0; c < c1; ++c) {
+        int w = W.ch_w[c];
+        if (run + w > W.node_cap) w = 0;   // no room this round: the chain waits
+        W.ch_w[c] = w;
+        W.ch_off[c] = run;
+        run += w;
+    }
+    __syncthreads();
+    if (tid == nt - 1) W.ctl[WF_CTL_NODES] = min(part[nt - 1], W.node_cap);
+}
+
+template <bool PILOT>
+__global__ void k_wf_nodes(Pool B, WfBufs W) {
+    const int items = W.ctl[WF_CTL_ITEMS], nodes = W.ctl[WF_CTL_NODES];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += gridDim.x * blockDim.x) {
+        // the last chain whose window starts at or before i (chains with an
+        // empty window share the offset of the next one and come before it)
+        int lo = 0, hi = items - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (W.ch_off[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        W.node_chain[i] = lo;
+        W.node_v[i] = (PILOT ? W.pil_next[lo] : B.chains[lo].next) + (i - W.ch_off[lo]);
+        W.node_nq[i] = 0;
+        W.list[0][i] = i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) W.ctl[WF_CTL_CNT0] = nodes;
+}
+
+// the (slot, entry) of the e-th entry of the wave
+__device__ __forceinline__ void wave_entry(const Pool &B, const KParams &P, int slots, int e, int &slot, int &k) {
+    const int32_t *offs = B.work + 1;   // per slot: first (entry, repeat) item
+    slot = 0;
+    while (e * P.repeats >= offs[slot + 1] && slot < slots - 1) ++slot;
+    k = e - offs[slot] / P.repeats;
+}
+
+// stage s: replay each listed node up to its next query (or to its f/q).
+// PILOT: the node is draw v of the pilot of entry node_chain (stream PILOT),
+// and its result is f/q itself.
+template <bool PILOT>
+__global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, WfBufs W, int s, uint32_t iter_base,
+                                                 int slots) {
+    iter_base = eff_iter(P, iter_base);
+    const int n = W.ctl[WF_CTL_CNT0 + s];
+    const int32_t *in = W.list[s & 1];
+    int32_t *out = W.list[(s + 1) & 1];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int i = in[idx];
+        int slot, k, rep = 0;
+        if (PILOT) {
+            wave_entry(B, P, slots, W.node_chain[i], slot, k);
+        } else {
+            const ChainState &st = B.chains[W.node_chain[i]];
+            slot = st.slot;
+            k = st.k;
+            rep = st.rep;
+        }
+        int Sp, C;
+        Entry E = load_entry(S, P, B, slot, k, Sp, C);
+        const float invB = PILOT ? 0.0f : 1.0f / B.eB[(size_t)slot * B.ML + k];
+        const int v = W.node_v[i];
+        Rng R;
+        if (PILOT) R.init(P.seed, K_PILOT, iter_base + slot, (uint32_t)k, (uint32_t)v);
+        else R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
+        ReplayTracer T;
+        T.res = W.node_res + (size_t)WF_MAXQ * i;
+        T.nres = W.node_nq[i];
+        T.next = 0;
+        T.susp = false;
+        float ratio = entry_ratio_t<false>(S, E, R, T);
+        if (T.susp && s == WF_MAXQ) {   // cannot happen (u <= 4): keep the walk defined and report
+            atomicExch(&W.ctl[WF_CTL_ERR], 2);
+            W.node_g[i] = 1.0f;
+            W.node_n[i] = 0;
+        } else if (T.susp) {
+            W.node_q[i] = T.q;
+            cg::coalesced_group g = cg::coalesced_threads();
+            int base = 0;
+            if (g.thread_rank() == 0) base = atomicAdd(&W.ctl[WF_CTL_CNT0 + s + 1], (int)g.size());
+            out[g.shfl(base, 0) + g.thread_rank()] = i;
+        } else if (PILOT) {
+            W.node_g[i] = ratio;
+        } else {
+            float gv = 1.0f - ratio * invB;
+            float r = fabsf(gv);
+            int nch = (int)floorf(r);
+            if (R.u(18) < r - (float)nch) nch += 1;
+            W.node_g[i] = gv;
+            W.node_n[i] = nch;
+        }
+    }
+}
+
+// pilot: entries of the wave, first window pilot_min draws
+__global__ void k_wfp_init(KParams P, Pool B, WfBufs W, int slots) {
+    const int32_t *offs = B.work + 1;
+    const int ents = min(offs[slots] / P.repeats, B.chain_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        W.ctl[WF_CTL_ITEMS] = ents;
+        W.ctl[WF_CTL_ACTIVE] = ents;
+    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ents; e += gridDim.x * blockDim.x) {
+        W.pil_next[e] = 0;
+        W.pil_best[e] = 0.0f;
+        W.pil_sum[e] = 0.0f;
+        W.pil_draws[e] = 0;
+        W.ch_done[e] = 0;
+        W.ch_win[e] = P.pilot_min;
+    }
+}
+
+// one block: pilot windows of this round and their node offsets
+__global__ void __launch_bounds__(1024) k_wfp_plan(KParams P, WfBufs W) {
+    __shared__ int part[1024];
+    const int items = W.ctl[WF_CTL_ITEMS];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid <= WF_MAXQ + 1) W.ctl[WF_CTL_CNT0 + tid] = 0;
+    const int per = (items + nt - 1) / nt;
+    const int c0 = tid * per, c1 = min(items, c0 + per);
+    int acc = 0;
+    for (int c = c0; c < c1; ++c) {
+        int w = W.ch_done[c] ? 0 : max(0, min(W.ch_win[c], P.pilot_max - W.pil_next[c]));
+        W.ch_w[c] = w;
+        acc += w;
+    }
+    part[tid] = acc;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int x = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += x;
+        __syncthreads();
+    }
+    int run = part[tid] - acc;
+    for (int c = c0; c < c1; ++c) {
+        int w = W.ch_w[c];
+        if (run + w > W.node_cap) w = 0;   // no room this round
+        W.ch_w[c] = w;
+        W.ch_off[c] = run;
+        run += w;
+    }
+    __syncthreads();
+    if (tid == nt - 1) W.ctl[WF_CTL_NODES] = min(part[nt - 1], W.node_cap);
+}
+
+// one warp per entry: the pilot's stopping rule over this round's draws, in
+// blocks of 32 (stop at the first block boundary >= pilot_min once some
+// draw had f > 0; draws evaluated past the stop are not counted)
+__global__ void __launch_bounds__(128) k_wfp_reduce(DScene S, KParams P, Pool B, DTables T, WfBufs W, int slots,
+                                                    int last_round) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int items = W.ctl[WF_CTL_ITEMS];
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < items; e += warps) {
+        if (W.ch_done[e]) continue;
+        const int w = W.ch_w[e], off = W.ch_off[e];
+        int next = W.pil_next[e];
+        float best = W.pil_best[e], sum = W.pil_sum[e];
+        int draws = W.pil_draws[e];
+        bool stop = false;
+        for (int b = 0; b < w; b += 32) {
+            if (next + b >= P.pilot_min && best > 0.0f) {
+                stop = true;
+                break;
+            }
+            float x = W.node_g[off + b + lane];
+            float m = x, t = x;
+            for (int o = 16; o > 0; o >>= 1) {
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                t += __shfl_xor_sync(0xffffffffu, t, o);
+            }
+            best = fmaxf(best, m);
+            sum += t;
+            draws += 32;
+        }
+        next += w;
+        if (!stop && next >= P.pilot_min && best > 0.0f) stop = true;
+        if (!stop && (next >= P.pilot_max || last_round)) stop = true;
+        if (lane == 0) {
+            W.pil_next[e] = next;
+            W.pil_best[e] = best;
+            W.pil_sum[e] = sum;
+            W.pil_draws[e] = draws;
+            if (stop) {
+                int slot, k;
+                wave_entry(B, P, slots, e, slot, k);
+                int Sp, C;
+                Entry E = load_entry(S, P, B, slot, k, Sp, C);
+                float Bv = best > 0.0f ? best : T.Bt[((E.u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
+                B.eB[(size_t)slot * B.ML + k] = Bv;
+                B.eMu[(size_t)slot * B.ML + k] = sum > 0.0f ? Bv * (float)draws / sum : 0.0f;
+                W.ch_done[e] = 1;
+            } else {
+                W.ch_win[e] = 2 * W.ch_win[e];
+            }
+        }
+    }
+}
+
+// stage s: answer the queries the step kernel recorded
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_wf_trace(DScene S, KParams P, Pool B, WfBufs W, int s) {
+    TravCount tc{0, 0, 0};
+    const int n = W.ctl[WF_CTL_CNT0 + s + 1];
+    const int32_t *lst = W.list[(s + 1) & 1];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int i = lst[idx];
+        const WfQuery q = W.node_q[i];
+        WfResult res;
+        if (q.kind == 2) {
+            res.tri = occluded<COUNT>(S, q.o, q.d, q.skip, q.skip2, &tc) ? 1 : 0;
+            res.b1 = res.b2 = 0.0f;
+        } else {
+            Hit h = (q.kind == 1 && S.ne <= PB_EMITTER_LIST_MAX) ? closest_emitter_hit<COUNT>(S, q.o, q.d, q.skip, &tc)
+                                                                  : closest_hit<COUNT>(S, q.o, q.d, q.skip, &tc);
+            res.tri = h.tri;
+            res.b1 = h.b1;
+            res.b2 = h.b2;
+        }
+        int nq = W.node_nq[i];
+        if (nq < WF_MAXQ) {
+            W.node_res[(size_t)WF_MAXQ * i + nq] = res;
+            W.node_nq[i] = nq + 1;
+        }
+    }
+    if (COUNT) {
+        atomicAdd(&B.counters[CNT_REC_NODES], (unsigned long long)tc.nodes);
+        atomicAdd(&B.counters[CNT_REC_TRIS], (unsigned long long)tc.tris);
+        atomicAdd(&B.counters[CNT_REC_RAYS], (unsigned long long)tc.rays);
+    }
+}
+
+// one warp per chain: the walk over this round's window in chunks of 32
+// nodes. While every pending node has sign +1 and the chunk has no negative
+// g, the walk reduces to counts (pending_v = pending - 1 + n_v; the chain
+// ends at the first node where pending reaches 0), a warp scan; otherwise
+// lane 0 replays the exact sequential walk over the chunk.
+__global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int items = W.ctl[WF_CTL_ITEMS];
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < items; c += warps) {
+        const int w = W.ch_w[c];
+        if (W.ch_done[c] || w == 0) continue;
+        ChainState &gst = B.chains[c];
+        const int slot = gst.slot, k = gst.k, rep = gst.rep;
+        const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
+        const int off = W.ch_off[c];
+        int next = gst.next;
+        double sum_t = gst.sum_t;
+        // pending-count form of the walk state while all signs are +1
+        bool pos = gst.cur_sign > 0.0f;
+        int pend = 1;
+        for (int f = 0; f < gst.sp; ++f) {
+            pos = pos && gst.fr_sign[f] > 0.0f;
+            pend += gst.fr_rem[f];
+        }
+        bool stack_form = !pos;   // gst holds the authoritative stack
+        int done = 0, trunc = 0;
+        // four chunks are loaded ahead of their walk (128 nodes per trip)
+        float gq[4];
+        int nq4[4];
+        for (int j0 = 0; j0 < w && !done; j0 += 32) {
+            const int qi = (j0 >> 5) & 3;
+            if (qi == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int jj = j0 + 32 * q + lane;
+                    gq[q] = jj < w ? W.node_g[off + jj] : 1.0f;
+                    nq4[q] = jj < w ? W.node_n[off + jj] : 1;
+                }
+            }
+            const int j = j0 + lane;
+            const bool in = j < w;
+            float g = gq[0];
+            int n = nq4[0];
+#pragma unroll
+            for (int q = 1; q < 4; ++q)
+                if (qi == q) {
+                    g = gq[q];
+                    n = nq4[q];
+                }
+            const bool anyneg = __any_sync(0xffffffffu, in && g < 0.0f);
+            if (!stack_form && !anyneg) {
+                // inclusive scan of (n - 1) over the chunk
+                int x = in ? n - 1 : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const unsigned endm = __ballot_sync(0xffffffffu, in && pend + x <= 0);
+                const int cnt = min(32, w - j0);
+                const int last = endm ? __ffs(endm) - 1 : cnt - 1;   // last node processed
+                double t = (in && lane <= last) ? (double)(g * invB) : 0.0;
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                sum_t += t;
+                next += last + 1;
+                pend += __shfl_sync(0xffffffffu, x, last);
+                if (endm) done = 1;
+                continue;
+            }
+            // exact sequential walk of this chunk by lane 0, on the stack form
+            if (!stack_form) {
+                if (lane == 0) {
+                    gst.cur_sign = 1.0f;
+                    gst.sp = 0;
+                    if (pend - 1 > 0) {
+                        gst.fr_sign[0] = 1.0f;
+                        gst.fr_rem[0] = pend - 1;
+                        gst.sp = 1;
+                    }
+                }
+                stack_form = true;
+            }
+            if (lane == 0) {
+                const int cnt = min(32, w - j0);
+                for (int q = 0; q < cnt; ++q) {
+                    const float gj = W.node_g[off + j0 + q];
+                    const int nj = W.node_n[off + j0 + q];
+                    sum_t += (double)(gst.cur_sign * gj * invB);
+                    next += 1;
+                    if (nj >= 1) {
+                        if (gst.sp >= PB_MAXF) {
+                            done = 1;
+                            trunc = 1;
+                            break;
+                        }
+                        gst.fr_sign[gst.sp] = gst.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                        gst.fr_rem[gst.sp] = nj;
+                        gst.sp++;
+                    }
+                    if (gst.sp == 0) {
+                        done = 1;
+                        break;
+                    }
+                    gst.cur_sign = gst.fr_sign[gst.sp - 1];
+                    if (--gst.fr_rem[gst.sp - 1] == 0) gst.sp--;
+                }
+            }
+            done = __shfl_sync(0xffffffffu, done, 0);
+            trunc = __shfl_sync(0xffffffffu, trunc, 0);
+            next = __shfl_sync(0xffffffffu, next, 0);
+            sum_t = __shfl_sync(0xffffffffu, sum_t, 0);
+            __syncwarp();
+            // back to the count form when the stack turned all-positive again
+            bool p2 = gst.cur_sign > 0.0f;
+            int pe = 1;
+            for (int f = 0; f < gst.sp; ++f) {
+                p2 = p2 && gst.fr_sign[f] > 0.0f;
+                pe += gst.fr_rem[f];
+            }
+            if (p2) {
+                stack_form = false;
+                pend = pe;
+            }
+            __syncwarp();
+        }
+        if (!done && next >= P.trial_cap) {
+            done = 1;
+            trunc = 1;
+        }
+        if (lane == 0) {
+            if (!stack_form) {   // store the count form as a one-frame stack
+                gst.cur_sign = 1.0f;
+                gst.sp = 0;
+                if (pend - 1 > 0) {
+                    gst.fr_sign[0] = 1.0f;
+                    gst.fr_rem[0] = pend - 1;
+                    gst.sp = 1;
+                }
+            }
+            gst.next = next;
+            gst.sum_t = sum_t;
+            if (done) {
+                size_t o = ((size_t)slot * B.ML + k) * P.repeats + rep;
+                B.rep[o] = (float)((double)invB + sum_t);
+                B.repn[o] = (float)next;
+                B.reptr[o] = trunc;
+                W.ch_done[c] = 1;
+                atomicSub(&W.ctl[WF_CTL_ACTIVE], 1);
+            } else {
+                W.ch_win[c] = min(2 * W.ch_win[c], WF_WIN_MAX);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Booth's roulette (one chain, no splitting; Sec. 4.2's RR ablation): node j
+// of a chain adds prod_{i<=j} g_i over the product of the continuation
+// probabilities taken before it, and the chain continues past j with
+// probability rho_j = min(1, c |prod_{i<=j} g_i|), drawn with the node's RRS
+// uniform. A warp takes 32 consecutive nodes at a time: product scans give
+// each lane its prefix product and survival, and a ballot finds the first
+// node whose roulette ends the chain.
+__global__ void __launch_bounds__(128) k_wf_walk_booth(KParams P, Pool B, WfBufs W, uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int items = W.ctl[WF_CTL_ITEMS];
+    const double cb = (double)P.booth;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < items; c += warps) {
+        const int w = W.ch_w[c];
+        if (W.ch_done[c] || w == 0) continue;
+        ChainState &gst = B.chains[c];
+        const int slot = gst.slot, k = gst.k, rep = gst.rep;
+        const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
+        const int off = W.ch_off[c];
+        int next = gst.next;
+        double sum_t = gst.sum_t, prod = gst.prod, surv = gst.surv;
+        int done = 0, trunc = 0;
+        for (int j0 = 0; j0 < w && !done; j0 += 32) {
+            const bool in = j0 + lane < w;
+            double pg = in ? (double)W.node_g[off + j0 + lane] : 1.0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const double y = __shfl_up_sync(FULL, pg, o);
+                if (lane >= o) pg *= y;
+            }
+            const double pr = prod * pg;   // product of g through this node
+            const double rho = fmin(1.0, cb * fabs(pr));
+            bool stop = false;
+            if (in) {
+                Rng R;
+                R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)(next + lane));
+                stop = !((double)R.u(18) < rho);
+            }
+            double rs = in ? rho : 1.0;    // survival through this node
+            for (int o = 1; o < 32; o <<= 1) {
+                const double y = __shfl_up_sync(FULL, rs, o);
+                if (lane >= o) rs *= y;
+            }
+            double before = __shfl_up_sync(FULL, rs, 1);
+            if (lane == 0) before = 1.0;
+            const unsigned stopm = __ballot_sync(FULL, stop);
+            const int cnt = min(32, w - j0);
+            const int last = stopm ? __ffs(stopm) - 1 : cnt - 1;
+            double t = (in && lane <= last) ? pr / (surv * before) * (double)invB : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+            sum_t += t;
+            next += last + 1;
+            prod = __shfl_sync(FULL, pr, last);
+            surv *= __shfl_sync(FULL, rs, last);
+            if (stopm) done = 1;
+        }
+        if (!done && next >= P.trial_cap) {
+            done = 1;
+            trunc = 1;
+        }
+        if (lane == 0) {
+            gst.next = next;
+            gst.sum_t = sum_t;
+            gst.prod = prod;
+            gst.surv = surv;
+            if (done) {
+                size_t o = ((size_t)slot * B.ML + k) * P.repeats + rep;
+                B.rep[o] = (float)((double)invB + sum_t);
+                B.repn[o] = (float)next;
+                B.reptr[o] = trunc;
+                W.ch_done[c] = 1;
+                atomicSub(&W.ctl[WF_CTL_ACTIVE], 1);
+            } else {
+                W.ch_win[c] = min(2 * W.ch_win[c], WF_WIN_MAX);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// chains the rounds left unfinished (deferred by the node capacity): one
+// thread each, inline draws, the same walk; counted in WF_CTL_ERR's high bits
+__global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t iter_base) {
+    iter_base = eff_iter(P, iter_base);
+    const int items = W.ctl[WF_CTL_ITEMS];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < items; c += gridDim.x * blockDim.x) {
+        if (W.ch_done[c]) continue;
+        atomicAdd(&W.ctl[WF_CTL_ERR], 1 << 8);
+        ChainState st = B.chains[c];
+        int Sp, C;
+        Entry E = load_entry(S, P, B, st.slot, st.k, Sp, C);
+        const float invB = 1.0f / B.eB[(size_t)st.slot * B.ML + st.k];
+        int done = 0, trunc = 0;
+        while (!done && P.booth > 0.0f) {   // Booth's roulette, as k_wf_walk_booth
+            if (st.next >= P.trial_cap) {
+                done = trunc = 1;
+                break;
+            }
+            Rng R;
+            R.init(P.seed, K_RECIP, iter_base + st.slot, (uint32_t)(st.k * 8 + st.rep), (uint32_t)st.next);
+            float ratio = entry_ratio<false>(S, E, R, nullptr);
+            float gj = 1.0f - ratio * invB;
+            st.prod *= (double)gj;
+            st.sum_t += st.prod / st.surv * (double)invB;
+            st.next += 1;
+            const double rho = fmin(1.0, (double)P.booth * fabs(st.prod));
+            if (!((double)R.u(18) < rho)) done = 1;
+            else st.surv *= rho;
+        }
+        while (!done) {
+            if (st.next >= P.trial_cap) {
+                done = trunc = 1;
+                break;
+            }
+            Rng R;
+            R.init(P.seed, K_RECIP, iter_base + st.slot, (uint32_t)(st.k * 8 + st.rep), (uint32_t)st.next);
+            float ratio = entry_ratio<false>(S, E, R, nullptr);
+            float gj = 1.0f - ratio * invB;
+            float r = fabsf(gj);
+            int nj = (int)floorf(r);
+            if (R.u(18) < r - (float)nj) nj += 1;
+            st.sum_t += (double)(st.cur_sign * gj * invB);
+            st.next += 1;
+            if (nj >= 1) {
+                if (st.sp >= PB_MAXF) {
+                    done = trunc = 1;
+                    break;
+                }
+                st.fr_sign[st.sp] = st.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                st.fr_rem[st.sp] = nj;
+                st.sp++;
+            }
+            if (st.sp == 0) {
+                done = 1;
+                break;
+            }
+            st.cur_sign = st.fr_sign[st.sp - 1];
+            if (--st.fr_rem[st.sp - 1] == 0) st.sp--;
+        }
+        size_t o = ((size_t)st.slot * B.ML + st.k) * P.repeats + st.rep;
+        B.rep[o] = (float)((double)invB + st.sum_t);
+        B.repn[o] = (float)st.next;
+        B.reptr[o] = trunc;
+        W.ch_done[c] = 1;
+        B.chains[c] = st;
+    }
+}
+
+}  // namespace
+
+void launch_recip_wavefront(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
+                            uint32_t iter_base, int num_sms, cudaStream_t st, const WfBufs &W) {
+    if (P.pilot_max > 0) {
+        // the pilot as wavefront rounds: windows pilot_min, then doubling up to pilot_max
+        k_wfp_init<<<num_sms * 2, 256, 0, st>>>(P, B, W, slots);
+        const int nr = wf_pilot_rounds(P);
+        for (int round = 0; round < nr; ++round) {
+            k_wfp_plan<<<1, 1024, 0, st>>>(P, W);
+            k_wf_nodes<true><<<num_sms * 8, 256, 0, st>>>(B, W);
+            for (int s = 0; s <= WF_MAXQ; ++s) {
+                k_wf_step<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s, iter_base, slots);
+                if (s == WF_MAXQ) break;
+                if (P.count) k_wf_trace<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+                else k_wf_trace<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+            }
+            k_wfp_reduce<<<num_sms * 16, 128, 0, st>>>(S, P, B, T, W, slots, round == nr - 1 ? 1 : 0);
+        }
+    }
+    k_wf_init<<<num_sms * 2, 256, 0, st>>>(P, B, W, slots);
+    for (int round = 0; round < WF_ROUNDS; ++round) {
+        k_wf_plan<<<1, 1024, 0, st>>>(P, B, W);
+        k_wf_nodes<false><<<num_sms * 8, 256, 0, st>>>(B, W);
+        for (int s = 0; s <= WF_MAXQ; ++s) {
+            k_wf_step<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s, iter_base, slots);
+            if (s == WF_MAXQ) break;
+            if (P.count) k_wf_trace<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+            else k_wf_trace<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+        }
+        if (P.booth > 0.0f) k_wf_walk_booth<<<num_sms * 16, 128, 0, st>>>(P, B, W, iter_base);
+        else k_wf_walk<<<num_sms * 16, 128, 0, st>>>(P, B, W);
+    }
+    k_wf_finish_rest<<<num_sms * 2, 128, 0, st>>>(S, P, B, W, iter_base);
+}
