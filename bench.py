@@ -508,6 +508,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom, sha),
                      "algorithmic_bytes_per_launch": b, "launch_ms": ms, "src_sha": sha},
+        # both traversal-bound stages against the same denominator (the dominant one is "roofline")
+        "roofline_stages": {
+            name: {"achieved": bb / (mm * 1e-3) / 1e9, "frac": bb / (mm * 1e-3) / 1e9 / peak, "unit": "GB/s",
+                   "algorithmic_bytes_per_wave": bb, "ms_per_wave": mm}
+            for name, bb, mm in (("k_recip", rec_bytes, rec_ms), ("k_eye", eye_bytes, eye_ms)) if mm > 0},
         "cpu_baseline": {"value": cpu_v, "unit": "Mpaths/s", "cores": cpu_nt, "kind": "oracle", "sample": cpu_desc},
         "e2e": {"value": e2e, "unit": "Mpaths/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
