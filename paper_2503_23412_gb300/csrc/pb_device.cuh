@@ -575,14 +575,9 @@ __device__ __forceinline__ Hit closest_hit(const DScene &S, float3 o, float3 d, 
     return closest_hit_from<COUNT>(S, o, d, skip, h, cnt);
 }
 
-// Closest hit of a ray that only matters if it ends on an emitter: the
-// emitter triangles are tested first (same predicate as the traversal); if
-// none is hit the answer "no emitter is the closest hit" needs no traversal,
-// else the traversal is bounded by the nearest emitter hit. Returns the
-// closest hit when it lies on an emitter, otherwise tri = -1.
-template <bool COUNT>
-__device__ __forceinline__ Hit closest_emitter_hit(const DScene &S, float3 o, float3 d, int skip,
-                                                   TravCount *cnt = nullptr) {
+// the nearest emitter triangle the ray meets (tri = -1 if none), with the
+// traversal's triangle predicate: the start candidate of closest_emitter_hit
+__device__ __forceinline__ Hit emitter_candidate(const DScene &S, float3 o, float3 d, int skip) {
     Hit e;
     e.tri = -1;
     e.t = INFINITY;
@@ -611,6 +606,18 @@ __device__ __forceinline__ Hit closest_emitter_hit(const DScene &S, float3 o, fl
             e.b2 = v;
         }
     }
+    return e;
+}
+
+// Closest hit of a ray that only matters if it ends on an emitter: the
+// emitter triangles are tested first (same predicate as the traversal); if
+// none is hit the answer "no emitter is the closest hit" needs no traversal,
+// else the traversal is bounded by the nearest emitter hit. Returns the
+// closest hit when it lies on an emitter, otherwise tri = -1.
+template <bool COUNT>
+__device__ __forceinline__ Hit closest_emitter_hit(const DScene &S, float3 o, float3 d, int skip,
+                                                   TravCount *cnt = nullptr) {
+    Hit e = emitter_candidate(S, o, d, skip);
     if (e.tri < 0) return e;
     Hit h = closest_hit_from<COUNT>(S, o, d, skip, e, cnt);
     int em = __float_as_int(S.stri[4 * (size_t)h.tri + 3].w);

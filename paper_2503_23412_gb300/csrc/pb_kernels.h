@@ -89,6 +89,7 @@ struct KParams {
     float side_in;              // cosine draws at a dielectric y_{s-1} on the side of y_{s-2}
     int estimator;              // 0: wavefront; 1: warp and block phases
     float booth;                // > 0: Booth's roulette of this scale (wavefront only); 0: the paper's RRS
+    int trace;                  // wavefront trace stages: 0 a query per thread; 1 persistent warps, lane refill
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
     SampleSink smp;         // raw != nullptr: record proposal training samples

@@ -5,6 +5,7 @@
 //   k_wf_nodes       the (chain, node) list of a round
 //   k_wf_step        replay of each node's draw up to its next ray query
 //   k_wf_trace       traversal-only answers to the recorded queries
+//   k_wf_trace_pt    the same with persistent warps that refill idle lanes
 //   k_wf_walk        the paper's RRS walk per chain (warp scans)
 //   k_wf_walk_booth  Booth's roulette per chain (the RR ablation's baseline)
 //   k_wf_finish_rest chains still open after the last round
@@ -331,6 +332,195 @@ __global__ void __launch_bounds__(128) k_wf_trace(DScene S, KParams P, Pool B, W
     }
 }
 
+// Persistent variant of k_wf_trace (KParams.trace = 1). A warp keeps its 32
+// lanes busy: whenever a lane's traversal ends, the lane takes the next query
+// of the stage from a counter (ray replacement), and each trip advances every
+// busy lane by up to PT_STEPS node visits. Each query runs the same
+// traversal as in k_wf_trace, node for node, so the answers are identical;
+// only the assignment of queries to lanes changes. The loop ends: every trip
+// advances a traversal (each is capped at 2^22 node visits, as in
+// trav_closest / trav_occluded) or takes or refuses a query (at most n plus
+// 32 per warp).
+constexpr int PT_STEPS = 8;
+constexpr int WF_CTL_FETCH0 = WF_CTL_CNT0 + WF_MAXQ + 2;   // per trace stage: queries taken
+static_assert(WF_CTL_FETCH0 + WF_MAXQ <= 16, "ctl holds 16 counters");
+
+struct PtRay {
+    float3 o, d, inv;   // occlusion: d = b - a
+    Hit h;              // closest: best so far; occlusion: tri = 1 once blocked
+    uint64_t trail;
+    int node, kind, s1, s2, steps;   // kind 0 closest, 2 occlusion, 3 closest that must end on an emitter
+};
+
+// starts query q; true if it is answered without a traversal
+template <bool COUNT>
+__device__ __forceinline__ bool pt_start(const DScene &S, const WfQuery &q, PtRay &r, TravCount *tc) {
+    r.o = q.o;
+    r.s1 = q.skip;
+    r.s2 = q.skip2;
+    r.node = 0;
+    r.trail = 0ull;
+    r.steps = 0;
+    r.h.tri = -1;
+    r.h.t = INFINITY;
+    r.h.b1 = r.h.b2 = 0.0f;
+    if (q.kind == 2) {
+        r.kind = 2;
+        r.d = q.d - q.o;
+    } else {
+        r.d = q.d;
+        r.kind = 0;
+        if (q.kind == 1 && S.ne <= PB_EMITTER_LIST_MAX) {
+            r.kind = 3;
+            r.h = emitter_candidate(S, q.o, q.d, q.skip);
+            if (r.h.tri < 0) return true;
+        }
+    }
+    r.inv = safe_inv(r.d);
+    if (COUNT) tc->rays++;
+    return false;
+}
+
+// one node visit of r's traversal (the loop body of trav_closest or
+// trav_occluded); true when the traversal has ended
+template <bool COUNT>
+__device__ __forceinline__ bool pt_step(const TravView &S, PtRay &r, TravCount *tc) {
+    if (r.steps++ >= (1 << 22)) return true;
+    const bool occl = r.kind == 2;
+    bool hL, hR;
+    float tl, tr;
+    int cl, cr;
+    child_boxes(S, r.node, r.o, r.inv, occl ? 1.0f : r.h.t, hL, hR, tl, tr, cl, cr);
+    if (COUNT) tc->nodes++;
+    if (hL && cl < 0) {
+        int v = -cl - 1, first = v >> 4, n = v & 15;
+        if (occl) {
+            for (int i = 0; i < n; ++i) {
+                if (COUNT) tc->tris++;
+                if (seg_test(S, first + i, r.o, r.d, r.s1, r.s2)) {
+                    r.h.tri = 1;
+                    return true;
+                }
+            }
+        } else {
+            for (int i = 0; i < n; ++i) tri_test(S, first + i, r.o, r.d, r.s1, r.h);
+            if (COUNT) tc->tris += n;
+        }
+        hL = false;
+    }
+    if (hR && cr < 0) {
+        int v = -cr - 1, first = v >> 4, n = v & 15;
+        if (occl) {
+            for (int i = 0; i < n; ++i) {
+                if (COUNT) tc->tris++;
+                if (seg_test(S, first + i, r.o, r.d, r.s1, r.s2)) {
+                    r.h.tri = 1;
+                    return true;
+                }
+            }
+        } else {
+            for (int i = 0; i < n; ++i) tri_test(S, first + i, r.o, r.d, r.s1, r.h);
+            if (COUNT) tc->tris += n;
+        }
+        hR = false;
+    }
+    if (!occl) {
+        hL = hL && tl <= r.h.t;
+        hR = hR && tr <= r.h.t;
+    }
+    if (hL && hR) {
+        r.trail = (r.trail << 1) | 1ull;
+        r.node = tl <= tr ? cl : cr;
+        return false;
+    }
+    if (hL || hR) {
+        r.trail <<= 1;
+        r.node = hL ? cl : cr;
+        return false;
+    }
+    while ((r.trail & 1ull) == 0ull) {
+        if (r.trail == 0ull) return true;
+        r.trail >>= 1;
+        r.node = __ldg(S.parent + r.node);
+    }
+    r.trail ^= 1ull;
+    r.node = __ldg(S.sibling + r.node);
+    return false;
+}
+
+// the answer of node i's pending query, stored as k_wf_trace stores it
+__device__ __forceinline__ void pt_finish(const DScene &S, const WfBufs &W, int i, const PtRay &r) {
+    WfResult res;
+    if (r.kind == 2) {
+        res.tri = r.h.tri >= 0 ? 1 : 0;
+        res.b1 = res.b2 = 0.0f;
+    } else {
+        res.tri = r.h.tri;
+        res.b1 = r.h.b1;
+        res.b2 = r.h.b2;
+        if (r.kind == 3 && r.h.tri >= 0 && __float_as_int(S.stri[4 * (size_t)r.h.tri + 3].w) < 0) res.tri = -1;
+    }
+    int nq = W.node_nq[i];
+    if (nq < WF_MAXQ) {
+        W.node_res[(size_t)WF_MAXQ * i + nq] = res;
+        W.node_nq[i] = nq + 1;
+    }
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_wf_trace_pt(DScene S, KParams P, Pool B, WfBufs W, int s) {
+    const unsigned FULL = 0xffffffffu;
+    TravCount tc{0, 0, 0};
+    const TravView V = trav_view(S);
+    const int n = W.ctl[WF_CTL_CNT0 + s + 1];
+    const int32_t *lst = W.list[(s + 1) & 1];
+    int32_t *fetch = W.ctl + WF_CTL_FETCH0 + s;
+    const int lane = threadIdx.x & 31;
+    int i = -1;
+    bool drained = false;
+    PtRay r;
+    for (;;) {
+        const bool need = i < 0 && !drained;
+        const unsigned m = __ballot_sync(FULL, need);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(fetch, __popc(m));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+                const int k = base + __popc(m & ((1u << lane) - 1u));
+                if (k < n) {
+                    i = lst[k];
+                    if (pt_start<COUNT>(S, W.node_q[i], r, &tc)) {
+                        pt_finish(S, W, i, r);
+                        i = -1;
+                    }
+                } else {
+                    drained = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, i >= 0)) {
+            if (__all_sync(FULL, drained)) break;
+            continue;
+        }
+        if (i >= 0) {
+            for (int st = 0; st < PT_STEPS; ++st) {
+                if (pt_step<COUNT>(V, r, &tc)) {
+                    pt_finish(S, W, i, r);
+                    i = -1;
+                    break;
+                }
+            }
+        }
+    }
+    if (COUNT) {
+        atomicAdd(&B.counters[CNT_REC_NODES], (unsigned long long)tc.nodes);
+        atomicAdd(&B.counters[CNT_REC_TRIS], (unsigned long long)tc.tris);
+        atomicAdd(&B.counters[CNT_REC_RAYS], (unsigned long long)tc.rays);
+    }
+}
+
 // one warp per chain: the walk over this round's window in chunks of 32
 // nodes. While every pending node has sign +1 and the chunk has no negative
 // g, the walk reduces to counts (pending_v = pending - 1 + n_v; the chain
@@ -636,6 +826,20 @@ __global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t
     }
 }
 
+// one trace stage: a query per thread, or persistent warps that refill lanes
+void launch_trace(const DScene &S, const KParams &P, const Pool &B, const WfBufs &W, int s, int num_sms,
+                  cudaStream_t st) {
+    if (P.trace) {
+        cudaMemsetAsync(W.ctl + WF_CTL_FETCH0 + s, 0, sizeof(int32_t), st);
+        if (P.count) k_wf_trace_pt<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+        else k_wf_trace_pt<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+    } else if (P.count) {
+        k_wf_trace<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+    } else {
+        k_wf_trace<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+    }
+}
+
 }  // namespace
 
 void launch_recip_wavefront(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
@@ -650,8 +854,7 @@ void launch_recip_wavefront(const DScene &S, const DTables &T, const KParams &P,
             for (int s = 0; s <= WF_MAXQ; ++s) {
                 k_wf_step<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s, iter_base, slots);
                 if (s == WF_MAXQ) break;
-                if (P.count) k_wf_trace<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
-                else k_wf_trace<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+                launch_trace(S, P, B, W, s, num_sms, st);
             }
             k_wfp_reduce<<<num_sms * 16, 128, 0, st>>>(S, P, B, T, W, slots, round == nr - 1 ? 1 : 0);
         }
@@ -663,8 +866,7 @@ void launch_recip_wavefront(const DScene &S, const DTables &T, const KParams &P,
         for (int s = 0; s <= WF_MAXQ; ++s) {
             k_wf_step<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s, iter_base, slots);
             if (s == WF_MAXQ) break;
-            if (P.count) k_wf_trace<true><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
-            else k_wf_trace<false><<<num_sms * 8, 128, 0, st>>>(S, P, B, W, s);
+            launch_trace(S, P, B, W, s, num_sms, st);
         }
         if (P.booth > 0.0f) k_wf_walk_booth<<<num_sms * 16, 128, 0, st>>>(P, B, W, iter_base);
         else k_wf_walk<<<num_sms * 16, 128, 0, st>>>(P, B, W);
