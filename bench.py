@@ -34,6 +34,7 @@ METRIC = "Mpaths/s and equal-time MAPE vs CPU oracle; learned vs plain proposal,
 W, H, SPP, DEPTH, M = 256, 256, 64, 8, 10000   # projector workload; --workload small shrinks it
 ENTRY_TARGET = 400          # incomplete light sub-paths estimated per iteration (paper: up to 400)
 BOOTH = 0.0                 # --booth: Booth's Russian roulette scale in the estimator (0: the paper's RRS)
+TRACE = 0                   # --trace: 1 = the estimator's trace stages on persistent warps with lane refill
 WORKLOAD = ("projector 256x256, 64 spp, max depth 8: textured 0.1x0.1 emitter in an absorbing box, "
             "biconvex GGX dielectric lens (IOR 1.5, ~19.5k triangles), diffuse room; M=10000 light "
             "sub-paths/iteration, 5 reciprocal repeats, 300 eye / 300 light / 100 specular / 10 control subspaces")
@@ -416,7 +417,7 @@ def run_ours(args):
     M_p = int(min(M, max(1, round(ENTRY_TARGET / max(frac, 1e-9)))))
     tables = r.tables_readback()
     base_iter = rank_iter_base(rank)
-    cfg = N.config(M=M, M_p=M_p, max_depth=DEPTH, spp=SPP, seed=7, booth=BOOTH)
+    cfg = N.config(M=M, M_p=M_p, max_depth=DEPTH, spp=SPP, seed=7, booth=BOOTH, trace=TRACE)
     trained = None
     if args.proposal == "learned":
         # the network is trained before timing, like the tables
@@ -504,7 +505,8 @@ def run_ours(args):
                    "stage_ms_per_step": mean, "entries_per_iteration": stats[-1]["n_entries"] / SPP,
                    "truncated_estimates_per_step": stats[-1]["n_truncated"],
                    "estimator_nodes_per_step": stats[-1]["n_nodes"], "parallelism": "replicas" if ws > 1 else "1 GPU",
-                   "proposal": args.proposal, "roulette": roulette_name()},
+                   "proposal": args.proposal, "roulette": roulette_name(),
+                   "trace_stages": "persistent warps, lane refill" if TRACE else "one query per thread"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom, sha),
                      "algorithmic_bytes_per_launch": b, "launch_ms": ms, "src_sha": sha},
@@ -528,7 +530,7 @@ def run_ours(args):
 
 
 def main():
-    global W, H, SPP, M, WORKLOAD, BOOTH
+    global W, H, SPP, M, WORKLOAD, BOOTH, TRACE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -543,8 +545,11 @@ def main():
     ap.add_argument("--booth", type=float, default=0.0,
                     help="Booth's Russian roulette of this scale in the reciprocal estimator (the RR ablation's "
                          "baseline; 0: the paper's RRS function)")
+    ap.add_argument("--trace", type=int, default=0, choices=[0, 1],
+                    help="1: the estimator's trace stages on persistent warps that refill idle lanes")
     args = ap.parse_args()
     BOOTH = max(0.0, args.booth)
+    TRACE = args.trace
     if args.workload == "small":
         W, H, SPP, M = 64, 64, 4, 2000
         WORKLOAD = WORKLOAD.replace("256x256, 64 spp", "64x64, 4 spp").replace("M=10000", "M=2000")
