@@ -146,6 +146,12 @@ typedef struct {
      * query as soon as theirs is answered (ray replacement). The answers are
      * the same either way. */
     int trace;
+    /* Strategies whose weighted contributions reach the film: 0 = all; 1 =
+     * only the proxy strategy (the paper's subspace-selection comparison
+     * renders these paths alone); 2 = all but the proxy strategy. Sampling
+     * and MIS weights are the same in every mode, so the modes' films add up
+     * to the full one. */
+    int film;
 } pb_config;
 
 typedef struct {

@@ -136,6 +136,7 @@ pb_status check_cfg(pb_ctx *ctx, const pb_config *c) {
     if (c->estimator < 0 || c->estimator > 1) return fail(ctx, PB_ERR_ARG, "estimator must be 0 or 1");
     if (!(c->booth >= 0.0f && c->booth < 3.0e38f)) return fail(ctx, PB_ERR_ARG, "booth must be finite and >= 0");
     if (c->trace < 0 || c->trace > 1) return fail(ctx, PB_ERR_ARG, "trace must be 0 or 1");
+    if (c->film < 0 || c->film > 2) return fail(ctx, PB_ERR_ARG, "film must be 0, 1 or 2");
     if (c->booth > 0.0f && c->estimator != 0)
         return fail(ctx, PB_ERR_ARG, "Booth's roulette runs on the wavefront estimator (estimator 0) only");
     return PB_OK;
@@ -168,6 +169,7 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
     P.estimator = c->estimator;
     P.booth = c->booth;
     P.trace = c->trace;
+    P.film = c->film;
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
     P.smp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};

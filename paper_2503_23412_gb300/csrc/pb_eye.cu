@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                     }
                     w = 1.0f / (1.0f + Epr + pt);
                 }
-                L = L + mul(beta, Le) * w;
+                if (P.film != 1) L = L + mul(beta, Le) * w;
                 if (P.acc.tile_all) atomicAdd(&P.acc.tile_all[tile], lum(mul(beta, Le)) * w);
             }
         }
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                             }
                         }
                         float w = 1.0f / (1.0f + Lsum0 + Ea + pt);
-                        L = L + c * w;
+                        if (P.film != 1) L = L + c * w;
                         if (P.acc.tile_all) atomicAdd(&P.acc.tile_all[tile], lum(c) * w);
                     }
                 }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                                     Ea = rev_a > 0.0f ? (fz / rev_a) * (av1 + Em1) : 0.0f;
                                 }
                                 float w = 1.0f / (1.0f + Ls + Ea);
-                                L = L + c * w;
+                                if (P.film != 1) L = L + c * w;
                                 if (P.smp.raw) {
                                     unsigned int idx = atomicAdd(P.smp.count, 1u);
                                     if (idx < (unsigned int)P.smp.cap) {
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                                     }
                                     w = 1.0f / (1.0f + p0r + p1r);
                                 }
-                                L = L + c * w;
+                                if (P.film != 2) L = L + c * w;
                                 n_proxy_ok++;
                                 if (P.acc.proxy) {
                                     atomicAdd(&P.acc.tile_all[tile], lum(c) * w);

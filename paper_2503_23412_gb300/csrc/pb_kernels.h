@@ -90,6 +90,7 @@ struct KParams {
     int estimator;              // 0: wavefront; 1: warp and block phases
     float booth;                // > 0: Booth's roulette of this scale (wavefront only); 0: the paper's RRS
     int trace;                  // wavefront trace stages: 0 a query per thread; 1 persistent warps, lane refill
+    int film;                   // strategies reaching the film: 0 all, 1 the proxy strategy only, 2 all but it
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
     SampleSink smp;         // raw != nullptr: record proposal training samples
