@@ -329,6 +329,48 @@ def equal_time_study(N, r, M_p, base_iter, table_ms):
     }
 
 
+def run_subspace_ablation(args):
+    """The paper's subspace-selection comparison on the water-pool scene:
+    only the proxy strategy's paths are rendered (film mode 1), at equal
+    iterations, with the learned selection rows Gamma' and with uniform rows,
+    against a reference rendered with the learned rows on disjoint
+    iterations. Prints one JSON line with both MAPEs. 1 GPU, rank 0 only."""
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_2503_23412_gb300 import native as N
+    from paper_2503_23412_gb300 import scenes
+    Wa = Ha = 128
+    spp, ref_spp, depth, Ma = 128, 2048, 8, 10000
+    sc = scenes.water(Wa, Ha)
+    r = N.Renderer(sc, None, device=local)
+    r.prepare(N.config(M=Ma, M_p=Ma, max_depth=depth), n_iter=4, iter0=1 << 22, n_bsamples=32, lloyd_iters=8,
+              KT=64, KS=64, KSp=32, KC=4)
+    learned = r.tables_readback()
+    uniform = dict(learned, gamma_proxy=np.full_like(learned["gamma_proxy"], 1.0 / learned["gamma_proxy"].shape[1]))
+    base = dict(M=Ma, M_p=Ma, max_depth=depth, seed=7, film=1)
+
+    def render(tables, n, iter0):
+        r.upload_tables(tables)
+        r.clear()
+        st = r.render(N.config(spp=n, iter0=iter0, **base), allow_truncated=True)
+        return r.film().astype(np.float64), st
+
+    ref, _ = render(learned, ref_spp, 1 << 24)
+    img_l, st_l = render(learned, spp, 0)
+    img_u, st_u = render(uniform, spp, 0)
+    out = {"metric": "proxy-only MAPE at equal iterations, importance vs uniform subspace selection",
+           "unit": "MAPE", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "water pool %dx%d, depth %d, M=%d, %d iterations each, reference %d iterations"
+                      % (Wa, Ha, depth, Ma, spp, ref_spp), "film": "proxy strategy only"},
+           "mape": {"importance": mape(img_l, ref), "uniform": mape(img_u, ref)},
+           "proxy_ok": {"importance": st_l["n_proxy_ok"], "uniform": st_u["n_proxy_ok"]},
+           "ms": {"importance": st_l["ms"], "uniform": st_u["ms"]}}
+    print(json.dumps(out))
+
+
 def run_batch(args):
     """Batched workload: procedural glass / GGX / diffuse scenes of uneven
     size rendered by one graph launch (pb_render_batch), each with its
@@ -538,9 +580,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--proposal", default="table", choices=["table", "learned"],
                     help="light-subspace proposal of the timed steps (learned: trained before timing)")
-    ap.add_argument("--workload", default="projector", choices=["projector", "small", "batch"],
+    ap.add_argument("--workload", default="projector", choices=["projector", "small", "batch", "subspace"],
                     help="small: the same scene and pipeline at 64x64, 4 spp, M=2000 (profiling captures); "
-                         "batch: procedural scenes of uneven size in one graph launch")
+                         "batch: procedural scenes of uneven size in one graph launch; "
+                         "subspace: the proxy-only selection comparison on the water scene")
     ap.add_argument("--scenes", type=int, default=16, help="scenes of the batch workload")
     ap.add_argument("--booth", type=float, default=0.0,
                     help="Booth's Russian roulette of this scale in the reciprocal estimator (the RR ablation's "
@@ -557,6 +600,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "subspace":
+        run_subspace_ablation(args)
     else:
         run_ours(args)
 
