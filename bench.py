@@ -371,6 +371,50 @@ def run_subspace_ablation(args):
     print(json.dumps(out))
 
 
+def run_rr_ablation(args):
+    """The paper's RR ablation on the projector workload: MAPE at equal time
+    of the paper's RRS function and of Booth's roulette at scales 10 ... 10^4,
+    against a reference rendered with the paper's function on disjoint
+    iterations. The time budget is one 64-iteration render with the paper's
+    function. Prints one JSON line. 1 GPU, rank 0 only."""
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    from paper_2503_23412_gb300 import native as N
+    from paper_2503_23412_gb300 import scenes
+    sc = scenes.projector(W, H)
+    r = N.Renderer(sc, None, device=local)
+    st = r.prepare(N.config(M=M, M_p=M, max_depth=DEPTH, spp=1, seed=7), n_iter=4, iter0=1 << 22, n_bsamples=32,
+                   lloyd_iters=8, KT=300, KS=300, KSp=100, KC=10, tile=10)
+    frac = st["n_entries"] / float(4 * M)
+    M_p = int(min(M, max(1, round(ENTRY_TARGET / max(frac, 1e-9)))))
+    base = dict(M=M, M_p=M_p, max_depth=DEPTH, seed=7)
+
+    def render(n, iter0, booth):
+        r.clear()
+        s_ = r.render(N.config(spp=n, iter0=iter0, booth=booth, **base), allow_truncated=True)
+        return r.film().astype(np.float64), s_
+
+    ref, _ = render(REF_SPP, 1 << 24, 0.0)
+    img, st0 = render(SPP, 0, 0.0)
+    budget = st0["ms"]
+    rows = {"paper_rrs": {"spp": SPP, "ms": budget, "mape": mape(img, ref), "nodes": st0["n_nodes"]}}
+    for c in (10.0, 100.0, 1000.0, 10000.0):
+        _, probe = render(8, 1 << 23, c)                       # time per iteration with this scale
+        n = max(1, int(round(8 * budget / max(probe["ms"], 1e-6))))
+        img_c, st_c = render(n, 0, c)
+        rows["booth_%g" % c] = {"spp": n, "ms": st_c["ms"], "mape": mape(img_c, ref), "nodes": st_c["n_nodes"],
+                                "truncated": st_c["n_truncated"]}
+    out = {"metric": "equal-time MAPE of the reciprocal estimator's Russian roulette: paper's RRS vs Booth",
+           "unit": "MAPE", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": WORKLOAD, "M_p": M_p, "reference": "%d iterations, paper's RRS" % REF_SPP,
+                      "budget_ms": budget},
+           "rows": rows}
+    print(json.dumps(out))
+
+
 def run_batch(args):
     """Batched workload: procedural glass / GGX / diffuse scenes of uneven
     size rendered by one graph launch (pb_render_batch), each with its
@@ -580,10 +624,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--proposal", default="table", choices=["table", "learned"],
                     help="light-subspace proposal of the timed steps (learned: trained before timing)")
-    ap.add_argument("--workload", default="projector", choices=["projector", "small", "batch", "subspace"],
+    ap.add_argument("--workload", default="projector", choices=["projector", "small", "batch", "subspace", "rr"],
                     help="small: the same scene and pipeline at 64x64, 4 spp, M=2000 (profiling captures); "
                          "batch: procedural scenes of uneven size in one graph launch; "
-                         "subspace: the proxy-only selection comparison on the water scene")
+                         "subspace: the proxy-only selection comparison on the water scene; "
+                         "rr: equal-time MAPE of the paper's RRS against Booth's roulette")
     ap.add_argument("--scenes", type=int, default=16, help="scenes of the batch workload")
     ap.add_argument("--booth", type=float, default=0.0,
                     help="Booth's Russian roulette of this scale in the reciprocal estimator (the RR ablation's "
@@ -602,6 +647,8 @@ def main():
         run_batch(args)
     elif args.workload == "subspace":
         run_subspace_ablation(args)
+    elif args.workload == "rr":
+        run_rr_ablation(args)
     else:
         run_ours(args)
 
