@@ -564,6 +564,42 @@ def pin_visible_light(W=32, H=24, vfov=40.0, x=(0.1, 0.5), y=(0.05, 0.3), z=2.0,
     return b.build(np.zeros((1, 1, 3)) if tex is None else tex, cam)
 
 
+def pin_two_targets(a=0.2, light_y=1.0, targets=((-0.1, 0.5), (0.1, 0.2)), half=0.03, rough=0.1):
+    """A square emitter (half-size a, Le=1) at height light_y facing down,
+    and two small square GGX conductors (half-size `half`) facing up at
+    (x, y) = targets[i], z = 0, each wholly inside the emitter's footprint;
+    nothing else. Light reaches each target directly (L S entries)."""
+    b = _Builder()
+    light = b.add_material(material(LAMBERT, (0, 0, 0), Le=(1.0, 1.0, 1.0)))
+    spec = b.add_material(material(CONDUCTOR, (0.9, 0.9, 0.9), rough=rough))
+    b.add_quad((0.0, light_y, 0.0), (a, 0, 0), (0, 0, a), (0, -1, 0), light)
+    for (x, y) in targets:
+        b.add_quad((x, y, 0.0), (half, 0, 0), (0, 0, half), (0, 1, 0), spec)
+    cam = [0, 2, -2, 0, 0, 0, 0, 1, 0, 40.0, 4, 4]
+    return b.build(np.zeros((1, 1, 3)), cam)
+
+
+def pin_albedo_walls(W=24, H=24, left=0.8, right=0.2, floor=0.5, a=0.2):
+    """Mirror-symmetric open box about x = 0: a diffuse floor (albedo
+    `floor`) at y = 0 over [-1, 1]^2 in x, z, a left wall at x = -1 (albedo
+    `left`) and a right wall at x = +1 (albedo `right`), both up to y = 1
+    and facing inward, and a square emitter (half-size a, Le = 5) facing
+    down at (0, 1, 0.7). The pinhole camera sits on the symmetry plane at
+    (0, 3, -0.5) looking at (0, 0, -0.2) with a 24 degree field, so it sees
+    only the floor."""
+    b = _Builder()
+    fl = b.add_material(material(LAMBERT, (floor, floor, floor)))
+    lw = b.add_material(material(LAMBERT, (left, left, left)))
+    rw = b.add_material(material(LAMBERT, (right, right, right)))
+    light = b.add_material(material(LAMBERT, (0, 0, 0), Le=(5.0, 5.0, 5.0)))
+    b.add_quad((0.0, 0.0, 0.0), (1.0, 0, 0), (0, 0, 1.0), (0, 1, 0), fl)
+    b.add_quad((-1.0, 0.5, 0.0), (0, 0.5, 0), (0, 0, 1.0), (1, 0, 0), lw)
+    b.add_quad((1.0, 0.5, 0.0), (0, 0.5, 0), (0, 0, 1.0), (-1, 0, 0), rw)
+    b.add_quad((0.0, 1.0, 0.7), (a, 0, 0), (0, 0, a), (0, -1, 0), light)
+    cam = [0.0, 3.0, -0.5, 0.0, 0.0, -0.2, 0, 0, 1, 24.0, W, H]
+    return b.build(np.zeros((1, 1, 3)), cam)
+
+
 def caustic_mini(W=16, H=16, rough=0.1):
     """Small open caustic scene: a 0.1 x 0.1 light above a diffuse floor and a
     tilted GGX mirror that focuses part of its light onto the floor (L S D E

@@ -664,6 +664,112 @@ def test_pilot_bound_stopping_rule():
         assert b256 >= b32
 
 
+def _sup_fq_square(a_area, h):
+    """Supremum of f/q for an L S entry (u = 1, y_0 on a parallel square
+    light of area a_area at height h above y_{s-1}, whose footprint covers
+    y_{s-1}). With c = cos0 cos1 / (pi d^2), f = c / A and q = (1/A + c) / 2
+    (Sec. 5.3: the even mixture of light sampling and the cosine lobe at
+    y_{s-1}), so f/q = 2c / (1 + A c), increasing in c; c peaks at 1/(pi h^2)
+    with y_0 straight above."""
+    c = 1.0 / (math.pi * h * h)
+    return 2.0 * c / (1.0 + a_area * c)
+
+
+def test_pilot_bound_is_the_largest_ratio_seen_below_the_supremum():
+    """The pilot's B (App. "Optimal value for B": B = max f/q) for the square
+    light entry: never above the analytic supremum, and within 5 % of it,
+    because about a third of the light's area gives f/q within 3 % of the
+    peak and 64 draws miss it with negligible probability. A target turned
+    away from the light has f = 0 on every draw, and the pilot returns 0."""
+    sc = scenes.pin_square_light(a=0.1, h=0.5)
+    o = O.Oracle(sc)
+    e = O.Entry(2, 1 / 3, 1 / 3, 1, 0, -1, 0.0, 0.0)
+    sup = _sup_fq_square(0.04, 0.5)
+    for b in range(12):
+        B = o.entry_pilot(e, seed=3, a=1, b=b, min_draws=64, max_draws=1024)
+        assert 0.95 * sup <= B <= sup * (1 + 1e-9), (B, sup)
+    dark = O.Oracle(scenes.pin_square_light(a=0.1, h=0.5, flip=True))
+    assert dark.entry_pilot(e, seed=3, a=1, b=0, min_draws=64, max_draws=256) == 0.0
+
+
+def _pin_tables_two_targets(sc):
+    """Specular-subspace centroids on the two targets of pin_two_targets:
+    S' = 1 on the upper target, S' = 2 on the lower one (the smaller bound,
+    so that an index moved to an empty cell meets the larger fallback), and
+    S' = 0 far outside the box."""
+    tab = scenes.random_tables(sc, KT=2, KS=2, KSp=3, KC=2, seed=2)
+    lo, hi = scenes.scene_bbox(sc)
+    tab["cent_Sp"][0] = [9, 9, 9, 0, 1, 0]
+    tab["cent_Sp"][1] = list((np.array([-0.1, 0.5, 0.0]) - lo) / (hi - lo)) + [0, 1, 0]
+    tab["cent_Sp"][2] = list((np.array([0.1, 0.2, 0.0]) - lo) / (hi - lo)) + [0, 1, 0]
+    return tab
+
+
+def test_learned_bound_and_mis_cells_hold_their_targets_values():
+    """Values of the learned (u, S', C) cells (Sec. 5.4-5.5, App. "Optimal
+    value for B") on two glossy targets under a square light, at heights
+    0.5 (upper, S' = 1) and 0.8 (lower, S' = 2) below it. Every entry is
+    L S (u = 1, no control vertex: C = KC).
+    - B of each target's cell is the largest f/q of its draws: at most the
+      closed-form supremum 2c/(1 + A c) of that height and within 5 % of it.
+      The two suprema differ by 2.3x, so a transposed or shifted cell index
+      fails; cells no entry reaches take the larger one.
+    - MIS scale mean(R)/mean(R^2) = 1/(E[R^2] Pbar) is 1/(1 + relvar(R)) of
+      the density P (Eq. MIS_1), so it lies in [0.6, 1.02] P of the target,
+      P by the offset point-to-rectangle form factor. The two P differ by
+      2.2x."""
+    sc = scenes.pin_two_targets()
+    o = O.Oracle(sc)
+    L = o.learn(O.params(M=4000, M_p=4000, max_depth=3), _pin_tables_two_targets(sc), 100, 3, n_bsamples=64)
+    B, mis = L["B_tab"], L["mis_tab"]
+    KC = 2
+    for sp, h in ((1, 0.5), (2, 0.8)):
+        sup = _sup_fq_square(0.16, h)
+        assert 0.95 * sup <= B[0, sp, KC] <= sup * (1 + 1e-6), (sp, B[0, sp, KC], sup)
+        # density of an L S vertex 0.1 off the centre of the 0.4 x 0.4 light
+        P = 2 * (_corner(0.3, 0.2, h) + _corner(0.1, 0.2, h)) / (math.pi * 0.16)
+        assert 0.6 * P <= mis[0, sp, KC] <= 1.02 * P, (sp, mis[0, sp, KC], P)
+    occupied = np.zeros(B.shape, bool)
+    occupied[0, 1:, KC] = True
+    np.testing.assert_array_equal(B[~occupied], max(B[0, 1, KC], B[0, 2, KC]))
+
+
+def test_learned_selection_row_follows_contribution_shares():
+    """Gamma (Sec. 5.5: proportional to expected contribution, plus the 0.1
+    defensive uniform part) on a mirror-symmetric open box: the camera sees
+    only the floor, paths have at most 3 segments, so every subspace
+    connection joins a floor eye vertex to a light vertex y_1. Mirror images
+    on the left (albedo 0.8) and right (0.2) walls carry identical terms but
+    for the light vertex's albedo, so the expected shares are 4 : 1, and
+    floor light vertices (coplanar with every eye vertex) carry none: the
+    row is 0.9 x (0.8, 0.2, 0) + 0.1/4. The light subspaces are listed as
+    (floor, right wall, far away, left wall); eye subspace 0 never occurs.
+    The share ratio's spread over 60 learning iterations is about 0.11."""
+    sc = scenes.pin_albedo_walls()
+    o = O.Oracle(sc)
+    tab = scenes.random_tables(sc, KT=2, KS=4, KSp=2, KC=2, seed=2)
+    lo, hi = scenes.scene_bbox(sc)
+
+    def pos(p):
+        return list((np.array(p, np.float64) - lo) / (hi - lo))
+
+    tab["cent_T"][0] = [9, 9, 9, 0, 1, 0, 0, 0, 0]
+    tab["cent_T"][1] = pos((0, 0, 0)) + [0, 1, 0, 0, 0, 0]
+    tab["cent_S"][0] = pos((0, 0, 0)) + [0, 1, 0, 0, 0, 0]
+    tab["cent_S"][1] = pos((1, 0.5, 0)) + [-1, 0, 0, 0, 0, 0]
+    tab["cent_S"][2] = [9, 9, 9, 0, 1, 0, 0, 0, 0]
+    tab["cent_S"][3] = pos((-1, 0.5, 0)) + [1, 0, 0, 0, 0, 0]
+    L = o.learn(O.params(M=2000, M_p=2000, max_depth=3), tab, 100, 60, n_bsamples=4)
+    g = L["gamma_conn"]
+    np.testing.assert_array_equal(g[0], np.float32(0.25))
+    np.testing.assert_array_equal(g[1, [0, 2]], np.float32(0.025))
+    ratio = (g[1, 3] - 0.025) / (g[1, 1] - 0.025)
+    assert abs(ratio - 4.0) < 0.45, ratio
+    assert abs(g[1, 3] - (0.72 + 0.025)) < 0.02 and abs(g[1, 1] - (0.18 + 0.025)) < 0.02, g[1]
+    # no specular vertex: the proxy rows stay uniform
+    np.testing.assert_array_equal(L["gamma_proxy"], np.float32(0.5))
+
+
 def test_learned_tables_obey_their_definitions():
     """Properties fixed by the learning rules (Sec. 5.4-5.5, Sec. 6.1.1),
     checked on subspaces that no vertex can be labelled with (centroids moved
