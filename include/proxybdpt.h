@@ -82,7 +82,7 @@ typedef struct {
     const float *gamma_conn;          /* KT*KS, rows positive */
     const float *gamma_proxy;         /* KT*KSp */
     const float *B_tab;               /* 4*KSp*(KC+1), > 0 */
-    const float *mis_tab;             /* 4*KSp*(KC+1), >= 0 */
+    const float *mis_tab;             /* 4*KSp*(KC+1), >= 0; 0 leaves the cell's sub-paths out of the proxy pool */
     int tile, grid_w, grid_h;
     const float *pi_grid;             /* grid_h*grid_w, in [0,1] */
 } pb_tables_desc;
@@ -164,10 +164,18 @@ typedef struct {
     double ms_light, ms_pool, ms_recip, ms_eye;   /* device time per stage (pb_render) */
     int64_t n_launches;                           /* kernels launched by the call */
     int64_t n_waves;                              /* launch waves (iterations in flight per wave) */
-    /* traversal work when count_traversal = 1: eye kernel and estimator kernel */
+    /* traversal work when count_traversal = 1: the eye shading pass (proxy
+     * retrace) and the estimator */
     int64_t eye_nodes, eye_tris, eye_rays, rec_nodes, rec_tris, rec_rays;
     double ms_mlp;             /* device time of the proposal's feature pass and network (proposal = 1) */
     double batch_ms;           /* pb_render_batch: device time of the whole batch (first entry only) */
+    /* the eye side's stages (pb_render): camera sub-paths traced by the
+     * feature pass (its time is in ms_mlp with the learned proposal, in
+     * ms_eye otherwise) and the traversal-only occlusion answers (in ms_eye);
+     * with count_traversal = 1 their traversal work (the eye_* counts above
+     * keep the shading pass's own: the proxy retrace) */
+    double ms_eye_feat, ms_eye_occ;
+    int64_t cam_nodes, cam_tris, cam_rays, shd_nodes, shd_tris, shd_rays;
 } pb_stats;
 
 /* Creates a context on CUDA device `device`. cuda_stream: a cudaStream_t
@@ -227,7 +235,15 @@ void pb_autotune_cache_clear(void);
  *  - the MIS scale mean(R)/mean(R^2) per cell (Sec. 5.4, Eq. MIS_1);
  *  - Gamma rows proportional to the accumulated unweighted contribution
  *    (0.9 x normalised + 0.1 uniform) and the 10x10-tile proxy probability
- *    (1.0 where the proxy share is >= 5 %, else 0.2; Sec. 6.1.1).
+ *    (1.0 where the proxy share is >= 5 %, else 0.2; Sec. 6.1.1);
+ *  - a cost bound on the proxy strategy's sub-path types, extending the
+ *    paper's own limits (Sec. 6.1.1: only L S^u and L D S^u with u <= 4 are
+ *    estimated, the rest is left to the subspace connections): a cell whose
+ *    learning estimates average more than max_chain estimator nodes each
+ *    (0: 4096; negative: no bound), or in which one entry's estimates took
+ *    trial_cap nodes or more in total, gets MIS scale 0. Its sub-paths then
+ *    never enter the proxy pool, and every strategy's weight already gives
+ *    the proxy no share of such paths, so the image stays unbiased.
  * The learned tables replace the current ones. Table sizes KT, KS, KSp, KC
  * and tile apply when the centroids are learned (KS, KSp <= 1023). */
 typedef struct {
@@ -238,6 +254,7 @@ typedef struct {
     int lloyd_iters;
     int keep_centroids;
     float b_safety;
+    float max_chain;
 } pb_learn_desc;
 pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_learn_desc *learn, pb_stats *stats_or_null);
 
@@ -291,13 +308,16 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
  * It computes the averaged reciprocal estimate of n incomplete light
  * sub-paths on the context's scene -- the same values pb_iteration computes
  * for its pool when given the same entries in (light path, vertex) order,
- * the same iteration, seed, repeats, trial_cap and B -- and allocates nothing:
- * its scratch is a file-scope device array of PB_NOALLOC_MAX_ESTIMATES
- * (entry, repeat) slots that every GPU loading the library keeps until exit.
- * Calls with n * cfg->repeats above that maximum return PB_ERR_ARG.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture. All calls share the array and it
- * keeps the last call's contents: calls whose work overlaps on the GPU (two
+ * the same iteration, seed, repeats, trial_cap, side_in and B -- and
+ * allocates nothing: its scratch is a file-scope device array of
+ * PB_NOALLOC_MAX_ESTIMATES (entry, repeat) slots (about 200 KB) that a device
+ * keeps from the library's first use on it until the process exits.
+ * pb_create looks up the array's device address for its context (that
+ * set-up may load the library's device code and place the array on the
+ * device); this call then only launches kernels and copies 12 bytes back.
+ * Calls with n * cfg->repeats above that maximum return PB_ERR_ARG. All
+ * calls share the array and it keeps the last call's contents (each call
+ * clears its counters first): calls whose work overlaps on the GPU (two
  * contexts or streams at once) race on it. The call is synchronous.
  *
  * Device inputs (caller-owned): d_tri[2n] (y_{s-1} triangle, h_c triangle),
@@ -305,9 +325,11 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
  * L D S^u, back 1 when y_{s-2} lies behind y_{s-1}'s normal),
  * d_B[n] (bound B > 0 per entry). Device outputs: d_rhat[n], d_nodes[n] (total
  * estimator nodes over the repeats, may be NULL). *n_truncated (may be NULL)
- * counts entries with a repeat that hit trial_cap. Only cfg->seed, repeats
- * and trial_cap are read from cfg (the roulette is always the paper's RRS
- * function). */
+ * counts entries with a repeat that hit trial_cap or its split stack. From
+ * cfg only seed, repeats (1..8), trial_cap (> 0) and side_in ([0, 1), 0 for
+ * an even split) are read; the roulette is always the paper's RRS function.
+ * An entry whose B is not positive (or NaN) gets a NaN estimate and the call
+ * returns PB_ERR_ARG after writing the other entries' estimates. */
 #define PB_NOALLOC_MAX_ESTIMATES 16384
 pb_status pb_recip_estimates_noalloc(pb_ctx *ctx, const pb_config *cfg, int iteration, int n,
                                      const int32_t *d_tri, const float *d_bary, const int32_t *d_info,
@@ -374,6 +396,16 @@ pb_status pb_train_proposal(pb_ctx *ctx, const pb_config *cfg, const pb_train_de
  * out[1] / out[0] agrees between them up to noise, and the proposal with the
  * smaller out[2] / out[0] is the better one. */
 pb_status pb_connection_moments(pb_ctx *ctx, const pb_config *cfg, double *out);
+
+/* ---- memory read bandwidth (measurement) -----------------------------------
+ * The paper has no counterpart; this gives the roofline denominators of the
+ * traversal kernels on the machine at hand. Allocates `bytes` on `device`,
+ * reads it once to warm up, then `reps` times with loads cached in L2 only,
+ * and writes the read rate in GB/s (10^9 bytes/s) to *gbs. Below the L2
+ * size this is the L2 read rate, far above it the HBM read rate. Synchronous;
+ * frees everything it allocates. PB_ERR_ARG for bytes < 4096, reps < 1 or a
+ * NULL gbs; PB_ERR_OOM when the buffer cannot be allocated. */
+pb_status pb_read_bandwidth(int device, size_t bytes, int reps, double *gbs);
 
 #ifdef __cplusplus
 }

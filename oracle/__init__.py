@@ -35,6 +35,10 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+# default bound on a cell's mean estimator nodes per estimate in learning
+MAX_CHAIN = 4096.0
+
+
 class SceneDesc(C.Structure):
     _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("nm", C.c_int),
                 ("verts", C.c_void_p), ("uvs", C.c_void_p), ("tris", C.c_void_p),
@@ -128,7 +132,7 @@ def lib():
         L.or_render.argtypes = [vp, C.POINTER(Params), C.POINTER(TablesDesc), C.c_int, C.c_int, C.c_int,
                                 C.c_int, vp, C.POINTER(Stats)]
         L.or_learn.argtypes = [vp, C.POINTER(Params), C.POINTER(TablesDesc), C.c_int, C.c_int, C.c_int,
-                               vp, vp, vp, vp, vp]
+                               C.c_double, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -245,7 +249,10 @@ class Oracle:
                          _p(film), C.byref(st))
         return film, st.as_dict()
 
-    def learn(self, params, tables_np, iter0, n_iter, n_bsamples=16):
+    def learn(self, params, tables_np, iter0, n_iter, n_bsamples=16, max_chain=MAX_CHAIN):
+        """Learned tables (see or_learn). max_chain: cells whose learning
+        estimates average more estimator nodes than this (or truncated) get
+        MIS scale 0 and leave the proxy pool; 0 turns the rule off."""
         t = dict(tables_np)
         KT, KS = t["cent_T"].shape[0], t["cent_S"].shape[0]
         KSp, KC = t["cent_Sp"].shape[0], t["cent_C"].shape[0]
@@ -255,7 +262,7 @@ class Oracle:
         gp = np.zeros((KT, KSp), np.float32)
         pi = np.zeros_like(t["pi_grid"], np.float32)
         td = self.tables(t)
-        self.L.or_learn(self.h, C.byref(params), C.byref(td), iter0, n_iter, n_bsamples,
+        self.L.or_learn(self.h, C.byref(params), C.byref(td), iter0, n_iter, n_bsamples, float(max_chain),
                         _p(B), _p(mis), _p(gc), _p(gp), _p(pi))
         t.update(B_tab=B, mis_tab=mis, gamma_conn=gc, gamma_proxy=gp, pi_grid=pi)
         return t

@@ -300,10 +300,24 @@ static void build_iter(const or_scene_t *s, const or_params *p, const or_tab *T,
     it->ent_C = (int *)malloc(sizeof(int) * (size_t)(ne + 1));
     it->rhat = (double *)malloc(sizeof(double) * (size_t)(ne + 1));
     collect_entries(s, p, it->lp, ne, it->ent, it->ent_l, it->ent_e);
+    /* labels; entries of cells whose MIS scale is 0 (left to the other
+     * strategies by the learned cost rule) leave the pool, order kept */
+    int kept = 0;
     for (int k = 0; k < ne; ++k) {
         const or_lpath *lp = &it->lp[it->ent_l[k]];
-        it->ent_Sp[k] = label_spec(T, &lp->v[it->ent_e[k]]);
-        it->ent_C[k] = it->ent[k].type ? label_ctrl(T, &lp->v[0]) : T->KC;
+        int Sp = label_spec(T, &lp->v[it->ent_e[k]]);
+        int C = it->ent[k].type ? label_ctrl(T, &lp->v[0]) : T->KC;
+        if (!(T->mis[table_cell(T, it->ent[k].u, Sp, C)] > 0.0f)) continue;
+        it->ent[kept] = it->ent[k];
+        it->ent_l[kept] = it->ent_l[k];
+        it->ent_e[kept] = it->ent_e[k];
+        it->ent_Sp[kept] = Sp;
+        it->ent_C[kept] = C;
+        ++kept;
+    }
+    ne = kept;
+    it->nent = ne;
+    for (int k = 0; k < ne; ++k) {
         if (rhat_override) {
             it->rhat[k] = rhat_override[k];
             continue;
@@ -832,7 +846,7 @@ void or_render(void *hs, const or_params *p, const or_tables_desc *td, int iter0
  * frozen). Grid: proxy share of the weighted contribution per tile; >= 5%
  * -> probability 1.0, else 0.2 (Sec. 6.1.1). */
 void or_learn(void *hs, const or_params *p_in, const or_tables_desc *td, int iter0, int n_iter, int n_bsamples,
-              float *B_out, float *mis_out, float *gconn_out, float *gproxy_out, float *pi_out) {
+              double max_chain, float *B_out, float *mis_out, float *gconn_out, float *gproxy_out, float *pi_out) {
     const or_scene_t *s = (const or_scene_t *)hs;
     or_params p_learn = *p_in;
     p_learn.booth = 0.0;   /* statistics are learned with the paper's RRS function */
@@ -878,29 +892,42 @@ void or_learn(void *hs, const or_params *p_in, const or_tables_desc *td, int ite
     }
     if (gmax <= 0.0) gmax = 1.0;
     for (int c = 0; c < ncell; ++c) B_out[c] = (float)(B_SAFETY * (Bmax[c] > 0.0 ? Bmax[c] : gmax));
-    /* pass 2: reciprocal statistics with the learned B */
+    /* pass 2: reciprocal statistics with the learned B, over every entry
+     * (MIS scale 1 everywhere while learning) */
     or_tables_desc t2 = *td;
     t2.mlp_w = NULL;   /* statistics are learned with the table proposal */
     t2.B_tab = B_out;
+    for (int c = 0; c < ncell; ++c) mis_out[c] = 1.0f;
+    t2.mis_tab = mis_out;
     or_tab T2;
     tab_init(&T2, &t2);
     double s1 = 0, s2 = 0;
+    double *nsum = (double *)calloc((size_t)ncell, sizeof(double));
+    double *enodes = (double *)malloc(sizeof(double) * (size_t)p->M * (size_t)(L > 0 ? L : 1));
     for (int k = 0; k < n_iter; ++k) {
         int iteration = iter0 + k;
         or_light_pass(hs, p, iteration, tri, bary);
         or_iter it;
-        build_iter(s, p, &T2, (uint32_t)iteration, tri, bary, NULL, &it, NULL, NULL, NULL);
+        build_iter(s, p, &T2, (uint32_t)iteration, tri, bary, NULL, &it, enodes, NULL, NULL);
         for (int q = 0; q < it.nent; ++q) {
             int cell = table_cell(&T2, it.ent[q].u, it.ent_Sp[q], it.ent_C[q]);
             double R = it.rhat[q];
             r1[cell] += R; r2[cell] += R * R; rn[cell] += 1;
             s1 += R; s2 += R * R;
+            /* a truncated estimate counts as over the bound */
+            nsum[cell] += enodes[q] >= (double)p->trial_cap ? 1e30 : enodes[q];
         }
         free_iter(&it);
     }
     double pooled = (s1 > 0.0 && s2 > 0.0) ? s1 / s2 : 1.0;
-    for (int c = 0; c < ncell; ++c)
+    for (int c = 0; c < ncell; ++c) {
         mis_out[c] = (float)((rn[c] > 0 && r1[c] > 0.0 && r2[c] > 0.0) ? r1[c] / r2[c] : pooled);
+        /* learned cost rule: cells whose estimates are too long leave the
+         * proxy strategy (MIS scale 0 keeps every weight consistent) */
+        if (max_chain > 0.0 && rn[c] > 0 && nsum[c] > max_chain * rn[c] * (double)p->repeats) mis_out[c] = 0.0f;
+    }
+    free(nsum);
+    free(enodes);
     /* pass 3: selection matrices and grid from eye passes with uniform rows */
     float *gu = (float *)malloc(sizeof(float) * (size_t)T.KT * T.KS);
     float *gpu_ = (float *)malloc(sizeof(float) * (size_t)T.KT * T.KSp);

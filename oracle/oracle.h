@@ -180,10 +180,13 @@ void or_mlp_adam(int np, double *w, const double *g, double *m1, double *m2, int
 
 /* Statistics / selection learning (Sec. 5.4-5.5 as read in the design notes).
  * Inputs: centroids in t (gamma/B/mis/pi entries are ignored and rebuilt).
- * Outputs written to the caller's arrays. */
+ * Outputs written to the caller's arrays. A (u, S', C) cell whose learning
+ * estimates average more than max_chain estimator nodes each, or of which
+ * one was truncated, gets MIS scale 0: its sub-paths are left to the other
+ * strategies (max_chain <= 0: no such rule). */
 void or_learn(void *h, const or_params *p, const or_tables_desc *t, int iter0, int n_iter,
-              int n_bsamples, float *B_out, float *mis_out, float *gconn_out, float *gproxy_out,
-              float *pi_out);
+              int n_bsamples, double max_chain, float *B_out, float *mis_out, float *gconn_out,
+              float *gproxy_out, float *pi_out);
 
 #ifdef __cplusplus
 }

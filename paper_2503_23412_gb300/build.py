@@ -21,7 +21,7 @@ HEADERS = [os.path.join(ROOT, "include", "proxybdpt.h")] + [
     os.path.join(CSRC, f) for f in ("pb_device.cuh", "pb_kernels.h", "pb_bvh.h", "pb_ctx.h", "pb_estimator.cuh",
                                     "pb_mlp.cuh", "pb_entry.cuh", "pb_recip_long.cuh")]
 UNITS = ["pb_api.cu", "pb_light.cu", "pb_recip.cu", "pb_recip_long.cu", "pb_recip_long_count.cu", "pb_wavefront.cu",
-         "pb_eye.cu", "pb_learn.cu", "pb_noalloc.cu", "pb_mlp.cu", "pb_bvh.cpp"]
+         "pb_eye.cu", "pb_learn.cu", "pb_noalloc.cu", "pb_mlp.cu", "pb_probe.cu", "pb_bvh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -182,9 +182,8 @@ pb_status run_wave(pb_ctx *ctx, const KParams &P, int slots, uint32_t iter_base,
     if (with_light) launch_light_pass(ctx->S, P, ctx->B, slots, iter_base, ctx->stream);
     launch_pool_build(ctx->S, ctx->T, P, ctx->B, slots, ctx->stream);
     if (with_recip) launch_recip(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->num_sms, ctx->stream, &ctx->wf);
-    launch_eye(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->Lbuf, sig, ctx->stream);
     CK(cudaGetLastError());
-    return PB_OK;
+    return pb_eye_stages(ctx, P, slots, iter_base, sig, ctx->stream);
 }
 
 // Structural check of a built hierarchy before any kernel walks it: every
@@ -243,6 +242,12 @@ void read_counters(pb_ctx *ctx, pb_stats *st) {
     st->rec_nodes = (int64_t)c[CNT_REC_NODES];
     st->rec_tris = (int64_t)c[CNT_REC_TRIS];
     st->rec_rays = (int64_t)c[CNT_REC_RAYS];
+    st->cam_nodes = (int64_t)c[CNT_CAM_NODES];
+    st->cam_tris = (int64_t)c[CNT_CAM_TRIS];
+    st->cam_rays = (int64_t)c[CNT_CAM_RAYS];
+    st->shd_nodes = (int64_t)c[CNT_SHD_NODES];
+    st->shd_tris = (int64_t)c[CNT_SHD_TRIS];
+    st->shd_rays = (int64_t)c[CNT_SHD_RAYS];
 }
 
 // ---- debug kernels --------------------------------------------------------
@@ -314,6 +319,7 @@ pb_status pb_create(pb_ctx **out, int device, void *cuda_stream) {
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     cudaEventCreate(&ctx->ev0);
     cudaEventCreate(&ctx->ev1);
+    pb_noalloc_setup(ctx);
     *out = ctx;
     return PB_OK;
 }
@@ -327,6 +333,7 @@ void pb_destroy(pb_ctx *ctx) {
     free_graphs(ctx);
     free_all(ctx->pool_mem);
     free_all(ctx->wf_mem);
+    free_all(ctx->eye_mem);
     mlp_free(ctx);
     if (ctx->d_iter0) cudaFree(ctx->d_iter0);
     if (ctx->film) cudaFree(ctx->film);
@@ -578,8 +585,8 @@ pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t
         if (s != PB_OK) return s;
     }
     P.smp = sink;
-    launch_eye(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->Lbuf, nullptr, ctx->stream);
-    CK(cudaGetLastError());
+    s = pb_eye_stages(ctx, P, slots, iter_base, nullptr, ctx->stream);
+    if (s != PB_OK) return s;
     if (cfg->proposal) return mlp_check_err(ctx);
     return PB_OK;
 }
@@ -634,11 +641,67 @@ pb_status wf_check(pb_ctx *ctx) {
     return PB_OK;
 }
 
+// ---- camera-side wavefront of the eye pass -----------------------------------------
+pb_status pb_eye_ensure(pb_ctx *ctx, int slots, int depth) {
+    const size_t npix = (size_t)ctx->S.W * ctx->S.H;
+    const size_t px = (size_t)slots * depth * npix;           // dense vertices
+    const size_t nq = (size_t)slots * npix * (2 * depth + 1);   // at most NEE + connection per vertex, one proxy
+    if (px * 4 + 3 > (size_t)INT32_MAX || nq > (size_t)INT32_MAX)
+        return fail(ctx, PB_ERR_ARG, "eye pass: too many pixels x iterations in flight x depth");
+    if (ctx->eye_cap_px >= px && ctx->eye_cap_q >= nq) return PB_OK;
+    free_graphs(ctx);   // captured renders point into the buffers replaced here
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_all(ctx->eye_mem);
+    auto &o = ctx->eye_mem;
+    CK(dalloc(o, &ctx->eye_hits, px));
+    CK(dalloc(o, &ctx->eye_vis, 3 * px));
+    CK(dalloc(o, &ctx->eye_qa, nq));
+    CK(dalloc(o, &ctx->eye_qb, nq));
+    CK(dalloc(o, &ctx->eye_dst, nq));
+    CK(dalloc(o, &ctx->eye_count, (size_t)1));
+    ctx->eye_cap_px = px;
+    ctx->eye_cap_q = nq;
+    return PB_OK;
+}
+
+pb_status pb_eye_stages(pb_ctx *ctx, const KParams &P0, int slots, uint32_t iter_base, uint32_t *sig,
+                        cudaStream_t st, const EyeEvents *ev) {
+    pb_status s = pb_eye_ensure(ctx, slots, P0.max_depth);
+    if (s != PB_OK) return s;
+    KParams P = P0;
+    if (!P.mlp.hits) {   // the table proposal: store the hits, no network rows
+        P.mlp.hits = ctx->eye_hits;
+        P.mlp.rows = nullptr;
+        P.mlp.sel = nullptr;
+        P.mlp.selq = nullptr;
+        launch_eye_feat(ctx->S, ctx->T, P, ctx->B, slots, iter_base, st);
+        if (ev && ev->feat_end) CK(cudaEventRecordWithFlags(ev->feat_end, st, ev->flags));
+    }
+    const size_t npix = (size_t)ctx->S.W * ctx->S.H;
+    P.q = EyeQueries{ctx->eye_qa, ctx->eye_qb, ctx->eye_dst, ctx->eye_count,
+                     (int)((size_t)slots * npix * (2 * P.max_depth + 1)), ctx->eye_vis,
+                     (size_t)slots * P.max_depth * npix};
+    CK(cudaMemsetAsync(ctx->eye_count, 0, sizeof(unsigned int), st));
+    launch_eye(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->Lbuf, nullptr, st, EYE_EMIT);
+    if (ev && ev->emit_end) CK(cudaEventRecordWithFlags(ev->emit_end, st, ev->flags));
+    launch_eye_occ(ctx->S, P, ctx->B, ctx->num_sms, st);
+    if (ev && ev->occ_end) CK(cudaEventRecordWithFlags(ev->occ_end, st, ev->flags));
+    launch_eye(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->Lbuf, sig, st, EYE_READ);
+    CK(cudaGetLastError());
+    return PB_OK;
+}
+
 // ---- render: prepare, enqueue (eager or captured), finish ---------------------
-constexpr int NEV = 6;   // per wave: light | pool | estimator | proposal | eye | end
+// per wave: light | pool | estimator | proposal | eye | end, then the ends of
+// the feature pass, the query pass and the occlusion answers
+constexpr int NEV = 9;
 
 static int render_slots(const pb_config *cfg, const KParams &P) {
-    int slots = cfg->batch > 0 ? cfg->batch : std::max(1, std::min(32, (1 << 20) / std::max(1, P.npix)));
+    // iterations in flight: up to 32, and about 8M eye paths per wave, so that
+    // even a 1024^2 image puts 8 iterations' estimates (thousands of chains)
+    // in one estimator wavefront; the per-wave eye buffers (about 1.3 GB per
+    // 1024^2 iteration) fit HBM with room to spare
+    int slots = cfg->batch > 0 ? cfg->batch : std::max(1, std::min(32, (1 << 23) / std::max(1, P.npix)));
     return std::max(1, std::min(slots, std::max(1, cfg->spp)));
 }
 
@@ -658,6 +721,8 @@ static pb_status prepare_render(pb_ctx *ctx, const pb_config *cfg, KParams &P, i
         s = wf_ensure(ctx);
         if (s != PB_OK) return s;
     }
+    s = pb_eye_ensure(ctx, slots, P.max_depth);
+    if (s != PB_OK) return s;
     if (!ctx->d_iter0) CK(cudaMalloc(&ctx->d_iter0, sizeof(uint32_t)));
     return PB_OK;
 }
@@ -685,12 +750,18 @@ static pb_status enqueue_render(pb_ctx *ctx, const pb_config *cfg, const KParams
         launch_recip(ctx->S, ctx->T, P, ctx->B, ns, base, ctx->num_sms, st, &ctx->wf);
         CK(cudaEventRecordWithFlags(e[3], st, evf));
         KParams Pw = P;
+        EyeEvents eev;
+        eev.feat_end = e[6];
+        eev.emit_end = e[7];
+        eev.occ_end = e[8];
+        eev.flags = evf;
         if (cfg->proposal) {
-            pb_status s = mlp_wave(ctx, Pw, ns, base);
+            pb_status s = mlp_wave(ctx, Pw, ns, base, &eev);
             if (s != PB_OK) return s;
         }
         CK(cudaEventRecordWithFlags(e[4], st, evf));
-        launch_eye(ctx->S, ctx->T, Pw, ctx->B, ns, base, ctx->Lbuf, nullptr, st);
+        pb_status s = pb_eye_stages(ctx, Pw, ns, base, nullptr, st, &eev);
+        if (s != PB_OK) return s;
         CK(cudaEventRecordWithFlags(e[5], st, evf));
         if (film) launch_film_add(P, ns, ctx->Lbuf, ctx->film, st);
         CK(cudaGetLastError());
@@ -731,6 +802,11 @@ static pb_status finish_render(pb_ctx *ctx, const pb_config *cfg, const KParams 
         st.ms_recip += c;
         st.ms_mlp += m;
         st.ms_eye += d;
+        float f = 0, oc = 0;
+        cudaEventElapsedTime(&f, cfg->proposal ? e[3] : e[4], e[6]);   // the feature pass
+        cudaEventElapsedTime(&oc, e[7], e[8]);                           // the occlusion answers
+        st.ms_eye_feat += f;
+        st.ms_eye_occ += oc;
     }
     st.n_waves = waves;
     // per wave: light, pool build, bucket, cdf, eye, film (6); the estimator:
@@ -744,7 +820,9 @@ static pb_status finish_render(pb_ctx *ctx, const pb_config *cfg, const KParams 
     const int64_t est = cfg->estimator == 1 ? 5
                                             : 4 + (pr > 0 ? 1 + (int64_t)pr * per_round : 1) +
                                                   (int64_t)WF_ROUNDS * per_round;
-    st.n_launches = (6 + est + (cfg->proposal ? 2 : 0)) * (int64_t)waves;
+    // the eye side: feature pass (the network's select kernel too with the
+    // learned proposal), query pass, occlusion answers, shading pass
+    st.n_launches = (5 + est + 3 + (cfg->proposal ? 2 : 1)) * (int64_t)waves;
     if (cfg->proposal) {
         pb_status s = mlp_check_err(ctx);
         if (s != PB_OK) return s;
@@ -1168,7 +1246,10 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
         s = mlp_wave(ctx, P, 1, (uint32_t)iteration);
         if (s != PB_OK) return s;
     }
-    launch_eye(ctx->S, ctx->T, P, ctx->B, 1, (uint32_t)iteration, ctx->Lbuf, ctx->sigbuf, ctx->stream);
+    {
+        pb_status se = pb_eye_stages(ctx, P, 1, (uint32_t)iteration, ctx->sigbuf, ctx->stream);
+        if (se != PB_OK) return se;
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
     if (cfg->proposal) {

@@ -71,6 +71,19 @@ struct pb_ctx {
     WfBufs wf{};
     std::vector<void *> wf_mem;
     int wf_chain_cap = 0;
+    // camera-side wavefront of the eye pass: stored hits (table proposal; the
+    // learned proposal's feature pass has its own), occlusion queries, answers
+    int4 *eye_hits = nullptr;
+    float4 *eye_qa = nullptr, *eye_qb = nullptr;
+    int32_t *eye_dst = nullptr;
+    unsigned int *eye_count = nullptr;
+    uint8_t *eye_vis = nullptr;
+    size_t eye_cap_q = 0, eye_cap_px = 0;   // queries, slot-vertex-pixels
+    std::vector<void *> eye_mem;
+    // device address of the allocation-free estimator's scratch array on this
+    // context's device (looked up once in pb_create), or null with the reason
+    void *na_scratch = nullptr;
+    std::string na_err;
 };
 
 // shared by the host translation units
@@ -80,13 +93,27 @@ pb_status pb_run_wave(pb_ctx *ctx, const KParams &P, int slots, uint32_t iter_ba
                       bool with_recip, uint32_t *sig);
 KParams pb_kparams(const pb_ctx *ctx, const pb_config *c);
 pb_status pb_check_cfg(pb_ctx *ctx, const pb_config *c);
+// the eye pass of one wave as the camera-side wavefront (pb_api.cu): the
+// feature pass (unless P.mlp.hits is already filled), the query pass, the
+// traversal-only answers and the shading pass into ctx->Lbuf
+// events recorded between the eye stages (null: none); flags as for cudaEventRecordWithFlags
+struct EyeEvents {
+    cudaEvent_t feat_end = nullptr, emit_end = nullptr, occ_end = nullptr;
+    unsigned int flags = 0;
+};
+pb_status pb_eye_stages(pb_ctx *ctx, const KParams &P, int slots, uint32_t iter_base, uint32_t *sig, cudaStream_t st,
+                        const EyeEvents *ev = nullptr);
+pb_status pb_eye_ensure(pb_ctx *ctx, int slots, int depth);
+// allocation-free estimator (pb_noalloc.cu): looks up the device address of
+// its scratch array with ctx's device current; called once by pb_create
+void pb_noalloc_setup(pb_ctx *ctx);
 // learned proposal (pb_mlp.cu)
 void mlp_free(pb_ctx *ctx);
 pb_status mlp_prepare(pb_ctx *ctx, int slots, int depth);
 void free_graphs(pb_ctx *ctx);
 pb_status wf_ensure(pb_ctx *ctx);
 pb_status wf_check(pb_ctx *ctx);
-pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base);
+pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base, const EyeEvents *ev = nullptr);
 pb_status mlp_check_err(pb_ctx *ctx);
 // one wave of iterations that records proposal training samples and leaves the film alone (pb_api.cu)
 pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t iter_base, const SampleSink &sink);

@@ -21,6 +21,16 @@
 // connection and are finished at connection time. The proxy term enters PT
 // and NEE weights of paths with the proxy shape; connections (s >= 2) can
 // never produce such paths (both joined vertices must be non-specular).
+//
+// Camera-side wavefront: the feature pass traces every camera sub-path and
+// stores its hits; an EYE_EMIT pass replays them with exactly the control
+// flow of the shading pass and appends each NEE, connection and proxy-entry
+// occlusion query to a queue (warp-aggregated appends); k_eye_occ answers
+// the queue with a traversal-only kernel; the EYE_READ pass replays again,
+// reads the answers and shades. Each query is the same segment the inline
+// pass would test, so the images are identical; the traversal runs at the
+// occupancy of a small kernel instead of the shading kernel's.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "pb_kernels.h"
@@ -67,9 +77,30 @@ __device__ __forceinline__ float mis_cell(const DTables &T, int u, int Sp, int C
     return T.mis[((u - 1) * T.KSp + Sp) * (T.KC + 1) + C];
 }
 
-template <bool COUNT>
+// visibility of the segment a -> b (kind 0 NEE, 1 connection, 2 the proxy's
+// first segment) at dense vertex index `dv`: traced here, appended to the
+// query queue (answer unknown yet: false), or read from the answers
+template <bool COUNT, int MODE>
+__device__ __forceinline__ bool eye_visible(const DScene &S, const KParams &P, size_t dv, int kind, float3 a,
+                                            float3 b, int sa, int sb, TravCount *tc) {
+    if (MODE == EYE_INLINE) return !occluded<COUNT>(S, a, b, sa, sb, tc);
+    if (MODE == EYE_READ) return P.q.vis[(size_t)kind * P.q.plane + dv] != 0;
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned int base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(P.q.count, (unsigned int)g.size());
+    const unsigned int idx = g.shfl(base, 0) + g.thread_rank();
+    if (idx < (unsigned int)P.q.cap) {   // the capacity covers every vertex's queries
+        P.q.qa[idx] = make_float4(a.x, a.y, a.z, __int_as_float(sa));
+        P.q.qb[idx] = make_float4(b.x, b.y, b.z, __int_as_float(sb));
+        P.q.dst[idx] = (int32_t)(dv * 4 + (size_t)kind);
+    }
+    return false;
+}
+
+template <bool COUNT, int MODE>
 __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base,
                                              float4 *Lbuf, uint32_t *sigbuf) {
+    constexpr bool SHADE = MODE != EYE_EMIT;   // the emit pass only walks the paths and appends queries
     iter_base = eff_iter(P, iter_base);
     TravCount tc{0, 0, 0};
     int pix = blockIdx.x * blockDim.x + threadIdx.x;
@@ -123,9 +154,10 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
         bool nonS = !mz.specular;
         Rng R;
         R.init(P.seed, K_CAMERA, it, (uint32_t)pix, (uint32_t)a);
+        const size_t dv = ((size_t)slot * P.max_depth + (a - 1)) * P.npix + pix;
 
         // ---- (s = 0) emitter hit
-        if (mz.emitter && dot(z.n, we) > 0.0f) {
+        if (SHADE && mz.emitter && dot(z.n, we) > 0.0f) {
             float3 Le = emitted(S, z, we);
             if (maxc(Le) > 0.0f) {
                 float w = 1.0f;
@@ -166,7 +198,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                 float b1, b2;
                 sample_light(S, R.u(3), R.u(4), R.u(5), lt, b1, b2);
                 Vtx y = vertex_at(S, lt, b1, b2);
-                bool vis = !occluded<COUNT>(S, z.p, y.p, z.tri, y.tri, &tc);
+                bool vis = eye_visible<COUNT, MODE>(S, P, dv, 0, z.p, y.p, z.tri, y.tri, &tc);
                 sig = sig_upd(sig, 0xA0000000u | (uint32_t)lt);
                 sig = sig_upd(sig, vis ? 1u : 0u);
                 if (vis) {
@@ -240,7 +272,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                         float4 va = B.valpha[so + fixed], vm = B.vmis[so + fixed];
                         float3 yp = xyz(vp), yn = xyz(vn), ywl = xyz(vw);
                         int ymat = __float_as_int(vp.w), ytri = __float_as_int(vn.w);
-                        bool vis = !occluded<COUNT>(S, z.p, yp, z.tri, ytri, &tc);
+                        bool vis = eye_visible<COUNT, MODE>(S, P, dv, 1, z.p, yp, z.tri, ytri, &tc);
                         sig = sig_upd(sig, vis ? 1u : 0u);
                         if (vis) {
                             float3 dd = yp - z.p;
@@ -318,7 +350,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                         int sl = u + (type ? 2 : 1);
                         int status = 0;
                         if (sl + a > P.max_depth) status = 1;
-                        else if (occluded<COUNT>(S, z.p, gs[0].p, z.tri, gs[0].tri, &tc)) status = 2;
+                        else if (!eye_visible<COUNT, MODE>(S, P, dv, 2, z.p, gs[0].p, z.tri, gs[0].tri, &tc)) status = 2;
                         else {
                             float3 prev = z.p;
                             for (int r = 1; r <= u && !status; ++r) {
@@ -454,6 +486,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
         h = replay ? stored_hit(P, slot, a + 1, pix) : closest_hit<COUNT>(S, z.p, d, z.tri, &tc);
         ++a;
     }
+    if (!SHADE) return;
     size_t o = (size_t)slot * P.npix + pix;
     Lbuf[o] = make_float4(L.x, L.y, L.z, 0.0f);
     if (sigbuf) sigbuf[o] = sig;
@@ -473,8 +506,10 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
 // network's input row, eye subspace and dense index of every vertex where
 // k_eye makes a subspace connection (row order is arbitrary; each row's
 // result depends on its own content only).
+template <bool COUNT>
 __global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base) {
     iter_base = eff_iter(P, iter_base);
+    TravCount tc{0, 0, 0};
     int pix = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = blockIdx.y;
     if (pix >= P.npix) return;
@@ -485,7 +520,7 @@ __global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P
     float j0 = r0.u(0), j1 = r0.u(1);
     float sx = 2.0f * ((float)px + j0) / (float)S.W - 1.0f, sy = 1.0f - 2.0f * ((float)py + j1) / (float)S.H;
     float3 d = normalize(S.cfwd + (S.cright * (sx * S.tanh_ * S.aspect) + S.cup * (sy * S.tanh_)));
-    Hit h = closest_hit<false>(S, S.cpos, d, -1, nullptr);
+    Hit h = closest_hit<COUNT>(S, S.cpos, d, -1, &tc);
     int a = 1;
     bool conn = P.conn && B.npool[slot] > 0;
     while (true) {
@@ -496,7 +531,7 @@ __global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P
         const DMat &mz = S.mats[z.mat];
         float3 we = -d;
         if (absorbing(S, z, we)) break;
-        if (conn && !mz.specular && a + 2 <= P.max_depth) {
+        if (conn && P.mlp.rows && !mz.specular && a + 2 <= P.max_depth) {
             int Tl = label_dir(S, z, we, T.KT, T.cT);
             cg::coalesced_group g = cg::coalesced_threads();
             unsigned int base = 0;
@@ -518,8 +553,32 @@ __global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P
         float pw = bsdf_pdf(mz, z.n, we, wl);
         if (!(pw > 0.0f)) break;
         d = wl;
-        h = closest_hit<false>(S, z.p, d, z.tri, nullptr);
+        h = closest_hit<COUNT>(S, z.p, d, z.tri, &tc);
         ++a;
+    }
+    if (COUNT) {
+        atomicAdd(&B.counters[CNT_CAM_NODES], (unsigned long long)tc.nodes);
+        atomicAdd(&B.counters[CNT_CAM_TRIS], (unsigned long long)tc.tris);
+        atomicAdd(&B.counters[CNT_CAM_RAYS], (unsigned long long)tc.rays);
+    }
+}
+
+// answers of the eye pass's occlusion queries: one query per thread, the
+// same traversal as the inline test, nothing else in the kernel
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_eye_occ(DScene S, KParams P, unsigned long long *counters) {
+    const unsigned int n = min(*P.q.count, (unsigned int)P.q.cap);
+    TravCount tc{0, 0, 0};
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 a = P.q.qa[i], b = P.q.qb[i];
+        const bool occ = occluded<COUNT>(S, xyz(a), xyz(b), __float_as_int(a.w), __float_as_int(b.w), &tc);
+        const int32_t d = P.q.dst[i];
+        P.q.vis[(size_t)(d & 3) * P.q.plane + (size_t)(d >> 2)] = occ ? 0 : 1;
+    }
+    if (COUNT) {
+        atomicAdd(&counters[CNT_SHD_NODES], (unsigned long long)tc.nodes);
+        atomicAdd(&counters[CNT_SHD_TRIS], (unsigned long long)tc.tris);
+        atomicAdd(&counters[CNT_SHD_RAYS], (unsigned long long)tc.rays);
     }
 }
 
@@ -541,16 +600,30 @@ __global__ void k_film_add(KParams P, int slots, const float4 *Lbuf, float *film
 }  // namespace
 
 void launch_eye(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
-                float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st) {
+                float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st, int mode) {
     dim3 grid((P.npix + 127) / 128, slots);
-    if (P.count) k_eye<true><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
-    else k_eye<false><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
+    if (mode == EYE_EMIT) {   // traversal counts come from k_eye_occ
+        k_eye<false, EYE_EMIT><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
+    } else if (mode == EYE_READ) {
+        if (P.count) k_eye<true, EYE_READ><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
+        else k_eye<false, EYE_READ><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
+    } else {
+        if (P.count) k_eye<true, EYE_INLINE><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
+        else k_eye<false, EYE_INLINE><<<grid, 128, 0, st>>>(S, T, P, B, iter_base, Lbuf, sigbuf);
+    }
+}
+
+void launch_eye_occ(const DScene &S, const KParams &P, const Pool &B, int num_sms, cudaStream_t st) {
+    const int blocks = std::max(1, std::min(num_sms * 16, (P.q.cap + 127) / 128));
+    if (P.count) k_eye_occ<true><<<blocks, 128, 0, st>>>(S, P, B.counters);
+    else k_eye_occ<false><<<blocks, 128, 0, st>>>(S, P, B.counters);
 }
 
 void launch_eye_feat(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                      cudaStream_t st) {
     dim3 grid((P.npix + 127) / 128, slots);
-    k_eye_feat<<<grid, 128, 0, st>>>(S, T, P, B, iter_base);
+    if (P.count) k_eye_feat<true><<<grid, 128, 0, st>>>(S, T, P, B, iter_base);
+    else k_eye_feat<false><<<grid, 128, 0, st>>>(S, T, P, B, iter_base);
 }
 
 void launch_film_add(const KParams &P, int slots, const float4 *Lbuf, float *film, cudaStream_t st) {

@@ -78,6 +78,22 @@ struct WfBufs {
     int32_t *pil_draws;                // draws counted (whole blocks of 32 before the stop)
 };
 
+// Occlusion queries of the eye pass (the camera-side wavefront): one pass
+// replays the camera sub-paths and appends every NEE, connection and
+// proxy-entry visibility query (warp-aggregated), a traversal-only kernel
+// answers them, and the shading pass reads the answers. Dense vertex index:
+// ((slot * max_depth) + a - 1) * npix + pix; kinds 0 NEE, 1 connection,
+// 2 the proxy's first segment z -> y_{s-1}.
+struct EyeQueries {
+    float4 *qa, *qb;        // segment a -> b: a.xyz and a's skip triangle, b.xyz and b's (int bits in .w)
+    int32_t *dst;           // per query: dense vertex index * 4 + kind
+    unsigned int *count;    // queries appended this wave
+    int cap;                // queries the arrays hold (every vertex's at most: no overflow)
+    uint8_t *vis;           // [kind][dense]: 1 the segment is unoccluded
+    size_t plane;           // bytes per kind: slots * max_depth * npix
+};
+constexpr int EYE_INLINE = 0, EYE_EMIT = 1, EYE_READ = 2;
+
 struct KParams {
     uint32_t seed;
     int max_depth, M, M_p, repeats, proxy, conn, trial_cap;
@@ -94,6 +110,7 @@ struct KParams {
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
     SampleSink smp;         // raw != nullptr: record proposal training samples
+    EyeQueries q;           // the eye pass's occlusion queries and answers (vis == nullptr: traced inline)
     const uint32_t *iter_dev;   // non-null (graph replay): iteration numbers are *iter_dev + the launch's base
 };
 
@@ -158,7 +175,8 @@ struct Pool {
 
 enum {
     CNT_ENTRIES = 0, CNT_TRUNC, CNT_NODES, CNT_CONN, CNT_PROXY, CNT_PROXY_OK, CNT_NFETCH, CNT_TTEST,
-    CNT_EYE_NODES, CNT_EYE_TRIS, CNT_EYE_RAYS, CNT_REC_NODES, CNT_REC_TRIS, CNT_REC_RAYS, CNT_N
+    CNT_EYE_NODES, CNT_EYE_TRIS, CNT_EYE_RAYS, CNT_REC_NODES, CNT_REC_TRIS, CNT_REC_RAYS,
+    CNT_CAM_NODES, CNT_CAM_TRIS, CNT_CAM_RAYS, CNT_SHD_NODES, CNT_SHD_TRIS, CNT_SHD_RAYS, CNT_N
 };
 
 void launch_light_pass(const DScene &S, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
@@ -183,8 +201,13 @@ void launch_recip_long_counting(const DScene &S, const DTables &T, const KParams
 // table-bound kernel when there is no pilot, and the repeat averages
 void launch_recip_wavefront(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots,
                             uint32_t iter_base, int num_sms, cudaStream_t st, const WfBufs &W);
+// the eye pass: mode EYE_INLINE traces its occlusion queries itself;
+// EYE_EMIT appends them to P.q and writes nothing else; EYE_READ reads
+// their answers from P.q.vis
 void launch_eye(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
-                float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st);
+                float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st, int mode = EYE_INLINE);
+// traversal-only answers of the queries the EYE_EMIT pass appended
+void launch_eye_occ(const DScene &S, const KParams &P, const Pool &B, int num_sms, cudaStream_t st);
 void launch_eye_feat(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                      cudaStream_t st);
 void launch_film_add(const KParams &P, int slots, const float4 *Lbuf, float *film, cudaStream_t st);

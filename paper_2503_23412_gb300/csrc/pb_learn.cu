@@ -189,7 +189,7 @@ __global__ void k_bsample(DScene S, DTables T, KParams P, Pool B, int slots, uin
     }
 }
 
-__global__ void k_recip_stats(DTables T, KParams P, Pool B, double *s1, double *s2, int32_t *cn) {
+__global__ void k_recip_stats(DTables T, KParams P, Pool B, double *s1, double *s2, double *s3, int32_t *cn) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = blockIdx.y;
     if (k >= B.nent[slot]) return;
@@ -200,8 +200,13 @@ __global__ void k_recip_stats(DTables T, KParams P, Pool B, double *s1, double *
     int Sp = B.elabel[o + fixed];
     int cell = ((u - 1) * T.KSp + Sp) * (T.KC + 1) + C;
     double R = (double)B.rhat[o + k];
+    // estimator nodes of the entry over its repeats; reaching trial_cap in
+    // total counts as over any bound
+    double nodes = 0.0;
+    for (int r = 0; r < P.repeats; ++r) nodes += (double)B.repn[(o + k) * P.repeats + r];
     atomicAdd(&s1[cell], R);
     atomicAdd(&s2[cell], R * R);
+    atomicAdd(&s3[cell], nodes >= (double)P.trial_cap ? 1e30 : nodes);
     atomicAdd(&cn[cell], 1);
 }
 
@@ -290,7 +295,8 @@ extern "C" pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_lear
     int gw = (W + tile - 1) / tile, gh = (H + tile - 1) / tile;
     int ncell = 4 * KSp * (KC + 1);
     std::vector<float> gC((size_t)KT * KS, 1.0f / KS), gP((size_t)KT * KSp, 1.0f / KSp);
-    std::vector<float> Bt(ncell, 1.0f), mis(ncell, 0.0f), pi((size_t)gw * gh, 1.0f);
+    // MIS scale 1 everywhere while learning: every entry stays in the pool
+    std::vector<float> Bt(ncell, 1.0f), mis(ncell, 1.0f), pi((size_t)gw * gh, 1.0f);
     auto upload_tables = [&]() -> pb_status {
         pb_tables_desc d{KT, KS, KSp, KC, lo.data(), hi.data(), cT.data(), cS.data(), cSp.data(), cC.data(),
                          gC.data(), gP.data(), Bt.data(), mis.data(), tile, gw, gh, pi.data()};
@@ -300,7 +306,7 @@ extern "C" pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_lear
     if (s != PB_OK) return s;
     KParams P = pb_kparams(ctx, cfg);
     P.booth = 0.0f;   // statistics are learned with the paper's RRS function
-    int slots = std::max(1, std::min(ld->n_iter, std::max(1, (1 << 20) / std::max(1, P.npix))));
+    int slots = std::max(1, std::min(ld->n_iter, std::max(1, (1 << 23) / std::max(1, P.npix))));
     s = pb_ensure_pool(ctx, slots, P.M * P.L, P.repeats);
     if (s != PB_OK) return s;
     DevBuf tmp;
@@ -374,20 +380,22 @@ extern "C" pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_lear
     if (s != PB_OK) return s;
     CK(cudaMemsetAsync(ctx->B.counters, 0, sizeof(unsigned long long) * CNT_N, ctx->stream));
     // ---- 3. MIS scale from reciprocal estimates
-    double *s1, *s2;
+    double *s1, *s2, *s3;
     int32_t *cn;
     CK(tmp.get(&s1, (size_t)ncell));
     CK(tmp.get(&s2, (size_t)ncell));
+    CK(tmp.get(&s3, (size_t)ncell));
     CK(tmp.get(&cn, (size_t)ncell));
     CK(cudaMemsetAsync(s1, 0, 8 * (size_t)ncell, ctx->stream));
     CK(cudaMemsetAsync(s2, 0, 8 * (size_t)ncell, ctx->stream));
+    CK(cudaMemsetAsync(s3, 0, 8 * (size_t)ncell, ctx->stream));
     CK(cudaMemsetAsync(cn, 0, 4 * (size_t)ncell, ctx->stream));
     for (int done = 0; done < ld->n_iter;) {
         int ns = std::min(slots, ld->n_iter - done);
         launch_light_pass(ctx->S, P, ctx->B, ns, it0 + done, ctx->stream);
         launch_pool_build(ctx->S, ctx->T, P, ctx->B, ns, ctx->stream);
         launch_recip(ctx->S, ctx->T, P, ctx->B, ns, it0 + done, ctx->num_sms, ctx->stream);
-        k_recip_stats<<<dim3((unsigned)((ML + 127) / 128), ns), 128, 0, ctx->stream>>>(ctx->T, P, ctx->B, s1, s2, cn);
+        k_recip_stats<<<dim3((unsigned)((ML + 127) / 128), ns), 128, 0, ctx->stream>>>(ctx->T, P, ctx->B, s1, s2, s3, cn);
         CK(cudaGetLastError());
         done += ns;
     }
@@ -400,16 +408,22 @@ extern "C" pb_status pb_prepare(pb_ctx *ctx, const pb_config *cfg, const pb_lear
         st.n_truncated = (int64_t)c[CNT_TRUNC];
         st.n_nodes = (int64_t)c[CNT_NODES];
     }
-    std::vector<double> h1(ncell), h2(ncell);
+    std::vector<double> h1(ncell), h2(ncell), h3(ncell);
     std::vector<int32_t> hn(ncell);
     CK(cudaMemcpyAsync(h1.data(), s1, 8 * (size_t)ncell, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(h2.data(), s2, 8 * (size_t)ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(h3.data(), s3, 8 * (size_t)ncell, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(hn.data(), cn, 4 * (size_t)ncell, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     double t1 = 0, t2 = 0;
     for (int c = 0; c < ncell; ++c) { t1 += h1[c]; t2 += h2[c]; }
     double pooled = (t1 > 0 && t2 > 0) ? t1 / t2 : 1.0;
-    for (int c = 0; c < ncell; ++c) mis[c] = (float)((hn[c] > 0 && h1[c] > 0 && h2[c] > 0) ? h1[c] / h2[c] : pooled);
+    const double max_chain = ld->max_chain == 0.0f ? 4096.0 : (double)ld->max_chain;
+    for (int c = 0; c < ncell; ++c) {
+        mis[c] = (float)((hn[c] > 0 && h1[c] > 0 && h2[c] > 0) ? h1[c] / h2[c] : pooled);
+        // learned cost bound: cells whose estimates run too long leave the proxy pool
+        if (max_chain > 0.0 && hn[c] > 0 && h3[c] > max_chain * (double)hn[c] * (double)P.repeats) mis[c] = 0.0f;
+    }
     s = upload_tables();
     if (s != PB_OK) return s;
     s = pb_ensure_pool(ctx, slots, P.M * P.L, P.repeats);

@@ -134,8 +134,12 @@ __global__ void k_pool_build(DScene S, DTables T, KParams P, Pool B) {
             if (u >= 1 && u <= 4 && j <= 1) {
                 int type = (j == 1);
                 int C = type ? label_ctrl(S, T, y[0]) : T.KC;
-                B.elabel[k] = label_spec(S, T, y[e]);
-                B.einfo[k] = u | (type << 3) | (C << 4);
+                int Sp = label_spec(S, T, y[e]);
+                // a cell with MIS scale 0 is left to the other strategies
+                if (T.mis[((u - 1) * T.KSp + Sp) * (T.KC + 1) + C] > 0.0f) {
+                    B.elabel[k] = Sp;
+                    B.einfo[k] = u | (type << 3) | (C << 4);
+                }
             }
         }
         // shift

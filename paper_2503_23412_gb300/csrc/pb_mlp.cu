@@ -826,7 +826,7 @@ pb_status mlp_prepare(pb_ctx *ctx, int slots, int depth) {
 }
 
 // feature pass, network and selection for one wave of iterations; sets P.mlp
-pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base) {
+pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base, const EyeEvents *ev) {
     MlpState &M = ctx->mlp;
     if (!M.ready) return pb_fail(ctx, PB_ERR_STATE, "learned proposal requested but no network is loaded");
     if (slots > MAX_SLOTS) return pb_fail(ctx, PB_ERR_ARG, "mlp: too many iterations in flight");
@@ -839,6 +839,7 @@ pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base) {
     P.mlp = MlpRows{M.rows, M.rowT, M.rowPos, M.rcount, (int)n, M.hits, nullptr, nullptr, M.emb, A};
     launch_eye_feat(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->stream);
     CK(cudaGetLastError());
+    if (ev && ev->feat_end) CK(cudaEventRecordWithFlags(ev->feat_end, ctx->stream, ev->flags));
     SelArgs a = sel_base(ctx);
     a.rows = M.rows;
     a.rowT = M.rowT;

@@ -6,18 +6,19 @@
 // process whose allocations are capped or pooled by another runtime, or code
 // on a path where cudaMalloc's implicit synchronisation is not acceptable.
 // This entry point serves them. Its inputs and outputs are the caller's
-// device buffers; its scratch -- one estimate, node count and truncation flag
+// device buffers; its scratch -- one estimate, node count and status flag
 // per (entry, repeat), plus a work counter -- lives in the file-scope array
-// below, sized for PB_NOALLOC_MAX_ESTIMATES estimates. Every GPU that loads
-// the library holds that array until the process exits.
+// below, sized for PB_NOALLOC_MAX_ESTIMATES estimates. A device holds that
+// array from the library's first use on it until the process exits;
+// pb_create looks up its address once per context (pb_noalloc_setup), so the
+// entry point itself never allocates or loads anything.
 //
 // The kernel is a one-phase form of the estimator (Sec. 4.2, App. Alg. I~):
 // one warp per (entry, repeat) draws 32 pre-order nodes at a time and
-// replays the sequential walk with a 48-frame stack. It uses the same
+// replays the sequential walk with a stack of 48 sign frames (children whose
+// sign matches the top frame join it). It uses the same
 // streams as the pooled estimator in pb_light.cu, so both produce the same
 // estimates.
-#include <mutex>
-
 #include "pb_ctx.h"
 #include "pb_estimator.cuh"
 
@@ -27,18 +28,18 @@ constexpr int NA_MAXF = 48;
 
 struct NAScratch {
     int work;        // next (entry, repeat) to claim; cleared at the start of each call
-    int pad[63];
+    int ntrunc;      // entries with a truncated repeat; cleared at the start of each call
+    int nbad;        // entries whose bound B is not positive; cleared at the start of each call
+    int pad[61];
     float est[PB_NOALLOC_MAX_ESTIMATES];
     float nodes[PB_NOALLOC_MAX_ESTIMATES];
-    int trunc[PB_NOALLOC_MAX_ESTIMATES];
+    int flag[PB_NOALLOC_MAX_ESTIMATES];   // 1 truncated, 2 bound not positive
 };
 
 // In host code `g_na_scratch` names a host-side stand-in, not device memory:
-// kernels get the address obtained from cudaGetSymbolAddress below.
+// kernels get the address obtained from cudaGetSymbolAddress in
+// pb_noalloc_setup.
 static __device__ __align__(256) NAScratch g_na_scratch;
-
-std::mutex g_na_mutex;
-void *g_na_ptr[256] = {nullptr};   // per device ordinal
 
 __global__ void __launch_bounds__(128) k_na_recip(DScene S, KParams P, uint32_t iteration, int n,
                                                   const int32_t *tri, const float *bary, const int32_t *info,
@@ -58,7 +59,16 @@ __global__ void __launch_bounds__(128) k_na_recip(DScene S, KParams P, uint32_t 
         E.type = (info[k] >> 3) & 1;
         E.back = (info[k] >> 30) & 1;
         E.pin = P.side_in;
-        float invB = 1.0f / Bv[k];
+        const float Bk = Bv[k];
+        if (!(Bk > 0.0f)) {   // not a valid bound (zero, negative or NaN): no estimate
+            if (lane == 0) {
+                sc->est[item] = __int_as_float(0x7fc00000);
+                sc->nodes[item] = 0.0f;
+                sc->flag[item] = 2;
+            }
+            continue;
+        }
+        float invB = 1.0f / Bk;
         double sum_t = 0.0;
         int nodes = 0;
         bool done = false, trunc = false;
@@ -91,14 +101,20 @@ __global__ void __launch_bounds__(128) k_na_recip(DScene S, KParams P, uint32_t 
                 sum_t += (double)(cur_sign * gj * invB);
                 nodes++;
                 if (nj >= 1) {
-                    if (sp >= NA_MAXF) {
-                        done = true;
-                        trunc = true;
-                        continue;
+                    // children whose sign matches the pending frame on top join it
+                    const float cs = cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                    if (sp > 0 && fr_sign[sp - 1] == cs) {
+                        fr_rem[sp - 1] += nj;
+                    } else {
+                        if (sp >= NA_MAXF) {
+                            done = true;
+                            trunc = true;
+                            continue;
+                        }
+                        fr_sign[sp] = cs;
+                        fr_rem[sp] = nj;
+                        ++sp;
                     }
-                    fr_sign[sp] = cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
-                    fr_rem[sp] = nj;
-                    ++sp;
                 }
                 if (sp == 0) {
                     done = true;
@@ -111,28 +127,44 @@ __global__ void __launch_bounds__(128) k_na_recip(DScene S, KParams P, uint32_t 
         if (lane == 0) {
             sc->est[item] = (float)((double)invB + sum_t);
             sc->nodes[item] = (float)nodes;
-            sc->trunc[item] = trunc ? 1 : 0;
+            sc->flag[item] = trunc ? 1 : 0;
         }
     }
 }
 
-__global__ void k_na_finish(KParams P, int n, const NAScratch *sc, float *rhat, float *nodes_out, int *ntrunc) {
+__global__ void k_na_finish(KParams P, int n, NAScratch *sc, float *rhat, float *nodes_out) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     double acc = 0.0;
     float nn = 0.0f;
-    int tr = 0;
+    int fl = 0;
     for (int r = 0; r < P.repeats; ++r) {
         acc += (double)sc->est[k * P.repeats + r];
         nn += sc->nodes[k * P.repeats + r];
-        tr |= sc->trunc[k * P.repeats + r];
+        fl |= sc->flag[k * P.repeats + r];
     }
     rhat[k] = (float)(acc / (double)P.repeats);
     if (nodes_out) nodes_out[k] = nn;
-    if (tr) atomicAdd(ntrunc, 1);
+    if (fl & 2) atomicAdd(&sc->nbad, 1);
+    else if (fl & 1) atomicAdd(&sc->ntrunc, 1);
 }
 
 }  // namespace
+
+void pb_noalloc_setup(pb_ctx *ctx) {
+    // called by pb_create with ctx's device current: the lookup may load the
+    // library's device code and place the array on this device, so it
+    // belongs to set-up, not to the allocation-free call
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e == cudaSuccess && p) {
+        ctx->na_scratch = p;
+    } else {
+        ctx->na_scratch = nullptr;
+        ctx->na_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+    }
+}
 
 extern "C" pb_status pb_recip_estimates_noalloc(pb_ctx *ctx, const pb_config *cfg, int iteration, int n,
                                                 const int32_t *d_tri, const float *d_bary, const int32_t *d_info,
@@ -141,44 +173,35 @@ extern "C" pb_status pb_recip_estimates_noalloc(pb_ctx *ctx, const pb_config *cf
     if (!ctx->has_scene) return pb_fail(ctx, PB_ERR_STATE, "no scene uploaded");
     if (!cfg || cfg->repeats < 1 || cfg->repeats > 8 || cfg->trial_cap < 1)
         return pb_fail(ctx, PB_ERR_ARG, "noalloc: repeats must be in [1, 8] and trial_cap positive");
+    if (!(cfg->side_in >= 0.0f && cfg->side_in < 1.0f))
+        return pb_fail(ctx, PB_ERR_ARG, "noalloc: side_in must lie in [0, 1)");
     if (n < 0 || (n > 0 && (!d_tri || !d_bary || !d_info || !d_B || !d_rhat)))
         return pb_fail(ctx, PB_ERR_ARG, "noalloc: null input or output");
     if ((long long)n * cfg->repeats > PB_NOALLOC_MAX_ESTIMATES)
         return pb_fail(ctx, PB_ERR_ARG,
                        "noalloc: entries x repeats exceeds PB_NOALLOC_MAX_ESTIMATES (" +
                            std::to_string(PB_NOALLOC_MAX_ESTIMATES) + ")");
-    if (ctx->device < 0 || ctx->device >= 256) return pb_fail(ctx, PB_ERR_ARG, "noalloc: device ordinal out of range");
+    if (!ctx->na_scratch) return pb_fail(ctx, PB_ERR_CUDA, "noalloc: scratch array unavailable: " + ctx->na_err);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return pb_fail(ctx, PB_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
-    NAScratch *sc;
-    {
-        std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_ptr[ctx->device]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_na_scratch);
-            if (e != cudaSuccess || !p)
-                return pb_fail(ctx, PB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_na_ptr[ctx->device] = p;
-        }
-        sc = (NAScratch *)g_na_ptr[ctx->device];
-    }
+    NAScratch *sc = (NAScratch *)ctx->na_scratch;
     if (n_truncated) *n_truncated = 0;
     if (n == 0) return PB_OK;
     KParams P = pb_kparams(ctx, cfg);
-    // the work counter and the caller's truncation count start at zero each call
-    e = cudaMemsetAsync(&sc->work, 0, sizeof(int), ctx->stream);
-    if (e != cudaSuccess) return pb_fail(ctx, PB_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-    int *d_ntr = reinterpret_cast<int *>(&sc->pad[0]);
-    e = cudaMemsetAsync(d_ntr, 0, sizeof(int), ctx->stream);
+    // the work counter and the status counts start at zero each call
+    e = cudaMemsetAsync(sc, 0, 3 * sizeof(int), ctx->stream);
     if (e != cudaSuccess) return pb_fail(ctx, PB_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     k_na_recip<<<ctx->num_sms * 8, 128, 0, ctx->stream>>>(ctx->S, P, (uint32_t)iteration, n, d_tri, d_bary, d_info,
                                                           d_B, sc);
-    k_na_finish<<<(n + 127) / 128, 128, 0, ctx->stream>>>(P, n, sc, d_rhat, d_nodes, d_ntr);
-    int ntr = 0;
-    e = cudaMemcpyAsync(&ntr, d_ntr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    k_na_finish<<<(n + 127) / 128, 128, 0, ctx->stream>>>(P, n, sc, d_rhat, d_nodes);
+    int cnt[3] = {0, 0, 0};
+    e = cudaMemcpyAsync(cnt, sc, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return pb_fail(ctx, PB_ERR_CUDA, std::string("noalloc estimator: ") + cudaGetErrorString(e));
-    if (n_truncated) *n_truncated = ntr;
+    if (n_truncated) *n_truncated = cnt[1];
+    if (cnt[2] > 0)
+        return pb_fail(ctx, PB_ERR_ARG, "noalloc: " + std::to_string(cnt[2]) +
+                                            " entries have a bound B that is not positive (their estimates are NaN)");
     return PB_OK;
 }

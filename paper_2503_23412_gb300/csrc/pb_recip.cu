@@ -151,7 +151,11 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
                     trunc = true;
                     continue;
                 }
-                if (nj >= 1 && sp >= MAXF1) {
+                // children whose sign matches the pending frame on top join it
+                // (the walk reads only the sign sequence and the pending count)
+                const float cs = cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                const bool merge = sp > 0 && fr_sign[sp - 1] == cs;
+                if (nj >= 1 && !merge && sp >= MAXF1) {
                     stop = j;
                     deep = true;
                     continue;
@@ -159,9 +163,13 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
                 sum_t += (double)(cur_sign * gj * invB);
                 nodes++;
                 if (nj >= 1) {
-                    fr_sign[sp] = cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
-                    fr_rem[sp] = nj;
-                    ++sp;
+                    if (merge) {
+                        fr_rem[sp - 1] += nj;
+                    } else {
+                        fr_sign[sp] = cs;
+                        fr_rem[sp] = nj;
+                        ++sp;
+                    }
                 }
                 if (sp == 0) {
                     done = true;

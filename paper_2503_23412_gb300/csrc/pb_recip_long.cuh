@@ -199,15 +199,21 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
                     int nj = sn[j];
                     st.sum_t += (double)(st.cur_sign * gj * invB);
                     if (nj >= 1) {
-                        if (st.sp >= PB_MAXF) {
-                            s_done = 1;
-                            trunc = true;
-                            st.next = v + 1;
-                            break;
+                        // children whose sign matches the pending frame on top join it
+                        const float cs = st.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                        if (st.sp > 0 && st.fr_sign[st.sp - 1] == cs) {
+                            st.fr_rem[st.sp - 1] += nj;
+                        } else {
+                            if (st.sp >= PB_MAXF) {
+                                s_done = 1;
+                                trunc = true;
+                                st.next = v + 1;
+                                break;
+                            }
+                            st.fr_sign[st.sp] = cs;
+                            st.fr_rem[st.sp] = nj;
+                            st.sp++;
                         }
-                        st.fr_sign[st.sp] = st.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
-                        st.fr_rem[st.sp] = nj;
-                        st.sp++;
                     }
                     if (st.sp == 0) {
                         s_done = 1;

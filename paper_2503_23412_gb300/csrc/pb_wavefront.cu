@@ -31,7 +31,7 @@ namespace {
 // only on (entry, repeat, node), so the estimates are those of the warp and
 // block phases.
 enum { WF_CTL_ITEMS = 0, WF_CTL_NODES, WF_CTL_ACTIVE, WF_CTL_ERR, WF_CTL_CNT0 };   // CNT0 .. CNT0 + WF_MAXQ + 1
-constexpr int WF_WIN_MAX = 16384;
+constexpr int WF_WIN_MAX = 1 << 18;   // a window doubles per round up to this many nodes
 
 __global__ void k_wf_init(KParams P, Pool B, WfBufs W, int slots) {
     const int32_t *offs = B.work + 1;
@@ -71,7 +71,8 @@ __global__ void k_wf_init(KParams P, Pool B, WfBufs W, int slots) {
 
 // one block: windows of this round and their node offsets (exclusive scan)
 __global__ void __launch_bounds__(1024) k_wf_plan(KParams P, Pool B, WfBufs W) {
-    __shared__ int part[1024];
+    // 64-bit sums: windows of up to WF_WIN_MAX nodes over all chains exceed int
+    __shared__ long long part[1024];
     const int items = W.ctl[WF_CTL_ITEMS];
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid <= WF_MAXQ + 1) W.ctl[WF_CTL_CNT0 + tid] = 0;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(1024) k_wf_plan(KParams P, Pool B, WfBufs W) {
     }
     const int per = (items + nt - 1) / nt;
     const int c0 = tid * per, c1 = min(items, c0 + per);
-    int acc = 0;
+    long long acc = 0;
     for (int c = c0; c < c1; ++c) {
         int w = 0;
         if (!W.ch_done[c]) w = max(0, min(W.ch_win[c], P.trial_cap - B.chains[c].next));
@@ -91,21 +92,21 @@ __global__ void __launch_bounds__(1024) k_wf_plan(KParams P, Pool B, WfBufs W) {
     part[tid] = acc;
     __syncthreads();
     for (int off = 1; off < nt; off <<= 1) {
-        int x = tid >= off ? part[tid - off] : 0;
+        long long x = tid >= off ? part[tid - off] : 0;
         __syncthreads();
         part[tid] += x;
         __syncthreads();
     }
-    int run = part[tid] - acc;
+    long long run = part[tid] - acc;
     for (int c = c0; c < c1; ++c) {
         int w = W.ch_w[c];
-        if (run + w > W.node_cap) w = 0;   // no room this round: the chain waits
+        if (run + w > (long long)W.node_cap) w = 0;   // no room this round: the chain waits
         W.ch_w[c] = w;
-        W.ch_off[c] = run;
+        W.ch_off[c] = (int)min(run, (long long)W.node_cap);
         run += w;
     }
     __syncthreads();
-    if (tid == nt - 1) W.ctl[WF_CTL_NODES] = min(part[nt - 1], W.node_cap);
+    if (tid == nt - 1) W.ctl[WF_CTL_NODES] = (int)min(part[nt - 1], (long long)W.node_cap);
 }
 
 template <bool PILOT>
@@ -611,14 +612,20 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
                     sum_t += (double)(gst.cur_sign * gj * invB);
                     next += 1;
                     if (nj >= 1) {
-                        if (gst.sp >= PB_MAXF) {
-                            done = 1;
-                            trunc = 1;
-                            break;
+                        // children whose sign matches the pending frame on top join it
+                        const float cs = gst.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                        if (gst.sp > 0 && gst.fr_sign[gst.sp - 1] == cs) {
+                            gst.fr_rem[gst.sp - 1] += nj;
+                        } else {
+                            if (gst.sp >= PB_MAXF) {
+                                done = 1;
+                                trunc = 1;
+                                break;
+                            }
+                            gst.fr_sign[gst.sp] = cs;
+                            gst.fr_rem[gst.sp] = nj;
+                            gst.sp++;
                         }
-                        gst.fr_sign[gst.sp] = gst.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
-                        gst.fr_rem[gst.sp] = nj;
-                        gst.sp++;
                     }
                     if (gst.sp == 0) {
                         done = 1;
@@ -802,13 +809,18 @@ __global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t
             st.sum_t += (double)(st.cur_sign * gj * invB);
             st.next += 1;
             if (nj >= 1) {
-                if (st.sp >= PB_MAXF) {
-                    done = trunc = 1;
-                    break;
+                const float cs = st.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                if (st.sp > 0 && st.fr_sign[st.sp - 1] == cs) {
+                    st.fr_rem[st.sp - 1] += nj;
+                } else {
+                    if (st.sp >= PB_MAXF) {
+                        done = trunc = 1;
+                        break;
+                    }
+                    st.fr_sign[st.sp] = cs;
+                    st.fr_rem[st.sp] = nj;
+                    st.sp++;
                 }
-                st.fr_sign[st.sp] = st.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
-                st.fr_rem[st.sp] = nj;
-                st.sp++;
             }
             if (st.sp == 0) {
                 done = 1;

@@ -51,7 +51,10 @@ class pb_stats(C.Structure):
                 ("ms_pool", C.c_double), ("ms_recip", C.c_double), ("ms_eye", C.c_double),
                 ("n_launches", C.c_int64), ("n_waves", C.c_int64), ("eye_nodes", C.c_int64),
                 ("eye_tris", C.c_int64), ("eye_rays", C.c_int64), ("rec_nodes", C.c_int64),
-                ("rec_tris", C.c_int64), ("rec_rays", C.c_int64), ("ms_mlp", C.c_double), ("batch_ms", C.c_double)]
+                ("rec_tris", C.c_int64), ("rec_rays", C.c_int64), ("ms_mlp", C.c_double), ("batch_ms", C.c_double),
+                ("ms_eye_feat", C.c_double), ("ms_eye_occ", C.c_double), ("cam_nodes", C.c_int64),
+                ("cam_tris", C.c_int64), ("cam_rays", C.c_int64), ("shd_nodes", C.c_int64), ("shd_tris", C.c_int64),
+                ("shd_rays", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,7 +77,7 @@ class pb_train_stats(C.Structure):
 class pb_learn_desc(C.Structure):
     _fields_ = [("KT", C.c_int), ("KS", C.c_int), ("KSp", C.c_int), ("KC", C.c_int), ("tile", C.c_int),
                 ("n_iter", C.c_int), ("iter0", C.c_uint32), ("n_bsamples", C.c_int), ("lloyd_iters", C.c_int),
-                ("keep_centroids", C.c_int), ("b_safety", C.c_float)]
+                ("keep_centroids", C.c_int), ("b_safety", C.c_float), ("max_chain", C.c_float)]
 
 
 class pb_tables_host(C.Structure):
@@ -91,7 +94,7 @@ EXPORTS = ["pb_create", "pb_destroy", "pb_last_error", "pb_scene_upload", "pb_ta
            "pb_iteration", "pb_prepare", "pb_tables_readback", "pb_recip_estimates_noalloc", "pb_mlp_nparams",
            "pb_mlp_upload", "pb_mlp_readback", "pb_mlp_logits", "pb_mlp_grad", "pb_mlp_train_batch",
            "pb_train_proposal", "pb_connection_moments", "pb_render_batch", "pb_autotune", "pb_autotune_cache_save",
-           "pb_autotune_cache_load", "pb_autotune_cache_clear"]
+           "pb_autotune_cache_load", "pb_autotune_cache_clear", "pb_read_bandwidth"]
 
 
 def lib(path=LIB):
@@ -134,6 +137,7 @@ def lib(path=LIB):
     L.pb_autotune_cache_save.argtypes = [C.c_char_p]
     L.pb_autotune_cache_load.argtypes = [C.c_char_p]
     L.pb_autotune_cache_clear.argtypes = []
+    L.pb_read_bandwidth.argtypes = [i32, C.c_size_t, i32, C.POINTER(C.c_double)]
     for n in EXPORTS:
         if n not in ("pb_destroy", "pb_last_error", "pb_autotune_cache_clear"):
             getattr(L, n).restype = i32
@@ -194,6 +198,15 @@ def autotune_cache_clear():
     lib().pb_autotune_cache_clear()
 
 
+def read_bandwidth(device, nbytes, reps):
+    """Read rate in GB/s of a buffer of nbytes read reps times (see pb_read_bandwidth)."""
+    g = C.c_double(0.0)
+    rc = lib().pb_read_bandwidth(device, nbytes, reps, C.byref(g))
+    if rc != PB_OK:
+        raise PBError(rc, "pb_read_bandwidth failed")
+    return g.value
+
+
 def train_desc(samples=1 << 20, rounds=2, steps=400, batch=4096, lr=1e-3, seed=1, iter0=1 << 23, max_iters_per_round=0,
                iters_per_wave=0, reinit=0, learned_first=0):
     return pb_train_desc(samples, rounds, steps, batch, lr, seed, iter0, max_iters_per_round, iters_per_wave, reinit,
@@ -247,10 +260,10 @@ class Renderer:
         self.tables = t
 
     def prepare(self, cfg, n_iter=8, iter0=1 << 20, n_bsamples=32, lloyd_iters=8, keep_centroids=False,
-                KT=300, KS=300, KSp=100, KC=10, tile=10, b_safety=0.0):
+                KT=300, KS=300, KSp=100, KC=10, tile=10, b_safety=0.0, max_chain=0.0):
         """Learns the subspace tables on the device (see pb_prepare)."""
         d = pb_learn_desc(KT, KS, KSp, KC, tile, n_iter, iter0, n_bsamples, lloyd_iters, 1 if keep_centroids else 0,
-                          b_safety)
+                          b_safety, max_chain)
         st = pb_stats()
         self._check(self.L.pb_prepare(self.h, C.byref(cfg), C.byref(d), C.byref(st)))
         return st.as_dict()

@@ -57,7 +57,8 @@ def test_learned_tables_are_valid_and_render(N):
         assert np.all(np.linalg.norm(c[:, 3:6], axis=1) <= 1 + 1e-4)
         assert np.all(np.linalg.norm(c[:, 6:9], axis=1) <= 1 + 1e-4)
     assert len(np.unique(t["cent_T"].round(6), axis=0)) > 12
-    assert np.all(t["B_tab"] > 0) and np.all(t["mis_tab"] > 0)
+    # MIS scale 0 marks a cell the learned cost bound leaves to the other strategies
+    assert np.all(t["B_tab"] > 0) and np.all(t["mis_tab"] >= 0) and (t["mis_tab"] > 0).mean() > 0.5
     np.testing.assert_allclose(t["gamma_conn"].sum(1), 1.0, rtol=1e-4)
     np.testing.assert_allclose(t["gamma_proxy"].sum(1), 1.0, rtol=1e-4)
     assert set(np.unique(t["pi_grid"])) <= {np.float32(0.2), np.float32(1.0)}

@@ -5,7 +5,8 @@ except where FP32 and FP64 round a decision differently (a ray passing a
 triangle edge, a label at a Voronoi boundary). Each comparison therefore
 checks: the topology signature agrees for >= 99.9 % of items (paths,
 estimator runs, rays), and where it agrees the values agree within the
-per-path relative tolerance 1e-4 (floats: FP32 device vs FP64 oracle).
+per-path relative tolerance 1e-4 (floats: FP32 device vs FP64 oracle),
+relative to the path's largest channel with no other floor.
 """
 
 import math
@@ -35,6 +36,15 @@ def rel_close(a, b, floor):
     """|a - b| <= REL * max(|a|, floor) elementwise (floor guards zeros)."""
     a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
     return np.abs(a - b) <= REL * np.maximum(np.abs(a), floor) + 1e-30
+
+
+def path_err(a, b):
+    """Per path (row): max over channels of |a - b|, relative to the path's
+    largest |a| channel; a path that is zero on one side only counts 1."""
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    mag = np.abs(a).max(1)
+    d = np.abs(a - b).max(1)
+    return np.where(mag > 0, d / np.where(mag > 0, mag, 1.0), np.where(d > 0, 1.0, 0.0))
 
 
 def learned(sc, o, M=600, M_p=300, max_depth=6, K=(16, 16, 8, 2), iters=2):
@@ -93,19 +103,13 @@ def test_light_pass_parity(N):
 
 # --- one iteration: pool, reciprocal estimates, eye pass ---------------------------
 
-# share of topology-agreeing paths that must meet REL, and a bound on all.
-# The textured projector is the exception the tolerance model allows: a
-# ~1e-6 FP32 direction error after two alpha = 0.01 refractions moves the
-# emitter hit by ~1e-5 of the 0.1-wide emitter, which the 256x256 noise
-# texture's gradient (~0.5 per texel) turns into up to ~1e-3 in radiance.
-# The same scene with a flat texture isolates geometry and BSDFs.
+# Every topology-agreeing path within REL. The textured projector's paths
+# through the lens are the one exception, bounded by its own test below.
 CASES = {
-    "cornell": dict(make=lambda: scenes.cornell(24, 20), M=800, M_p=400, max_depth=6, share=1.0, bound=REL),
+    "cornell": dict(make=lambda: scenes.cornell(24, 20), M=800, M_p=400, max_depth=6),
     "projector_flat": dict(make=lambda: scenes.projector(24, 24, lens_tris_per_cap=1500, flat=True), M=1500,
-                           M_p=1500, max_depth=8, share=0.999, bound=1e-3),
-    "projector": dict(make=lambda: scenes.projector(24, 24, lens_tris_per_cap=1500), M=1500, M_p=1500,
-                      max_depth=8, share=0.99, bound=2e-2),
-    "caustic": dict(make=lambda: scenes.caustic_mini(16, 12), M=500, M_p=500, max_depth=5, share=1.0, bound=REL),
+                           M_p=1500, max_depth=8),
+    "caustic": dict(make=lambda: scenes.caustic_mini(16, 12), M=500, M_p=500, max_depth=5),
 }
 
 
@@ -131,25 +135,69 @@ def test_iteration_parity(N, case):
         es = ref["entry_sig"] == got["entry_sig"]
         n_ent += len(es)
         n_ent_same += int(es.sum())
-        assert np.all(rel_close(ref["rhat"][es], got["rhat"][es], 1e-3))
+        assert np.all(rel_close(ref["rhat"][es], got["rhat"][es], 0.0))
         assert np.array_equal(ref["entry_nodes"][es], got["entry_nodes"][es])
         # eye pass on the oracle's estimates: isolates the per-path comparison
         got = r.iteration(cfg, it, tri, bary, rhat=ref["rhat"])
         same = ref["sig"] == got["sig"]
         n_items += len(same)
         n_same += int(same.sum())
-        a, b = ref["rgb"][same], got["rgb"][same]
-        floor = max(1e-3 * float(np.abs(ref["rgb"]).mean()), 1e-12)
-        ok = rel_close(a, b, floor)
-        assert ok.mean() >= cs["share"], (case, ok.mean())
-        err = np.abs(a - b) / np.maximum(np.abs(a), floor)
-        assert err.max() <= cs["bound"], (case, err.max())
+        err = path_err(ref["rgb"][same], got["rgb"][same])
+        assert err.max() <= REL, (case, err.max())
         proxy_live += ref["stats"]["n_proxy_ok"]
-    assert n_same / n_items >= TOPO - 0.004, n_same / n_items
-    assert n_ent == 0 or n_ent_same / n_ent >= 0.98
+    assert n_same / n_items >= TOPO, n_same / n_items
+    assert n_ent == 0 or n_ent_same / n_ent >= TOPO
     if case != "cornell":
         assert proxy_live > 0
     r.close()
+
+
+def test_textured_projector_error_is_the_texture_lookup(N):
+    """The textured projector: the emitter's radiance is a 256 x 256 noise
+    texture looked up at the hit point of paths that reach it through two
+    refractions of a lens at alpha = 0.01. An FP32 direction error of ~1e-6
+    there moves the hit by ~1e-5 of the 0.1-wide emitter, a few thousandths
+    of a texel, and the texture's texel-to-texel contrast turns that into up
+    to ~1e-3 in radiance. This test measures that model path by path: the
+    flat-textured twin draws the same paths (the texture does not enter any
+    density), every path whose textured error exceeds 1e-4 is within 1e-4 in
+    the flat twin (geometry, BSDFs, MIS and estimates agree; only the
+    texture lookup differs), and its error stays below the texel contrast
+    times 1e-2 (a hit moved by at most 1 % of a texel)."""
+    lens = dict(lens_tris_per_cap=1500)
+    runs = {}
+    sc_flat = scenes.projector(24, 24, flat=True, **lens)
+    tab = learned(sc_flat, O.Oracle(sc_flat), M=1500, M_p=1500, max_depth=8)   # one set of tables for both twins
+    for flat in (False, True):
+        sc = scenes.projector(24, 24, flat=flat, **lens)
+        o = O.Oracle(sc)
+        r = N.Renderer(sc, tab)
+        p = O.params(M=1500, M_p=1500, max_depth=8)
+        cfg = N.config(M=1500, M_p=1500, max_depth=8)
+        td = o.tables(tab)
+        out = []
+        for it in (3, 4):
+            tri, bary = o.light_pass(p, it)
+            ref = o.iteration(p, td, it, tri, bary)
+            got = r.iteration(cfg, it, tri, bary, rhat=ref["rhat"])
+            out.append((ref, got))
+        runs[flat] = (out, sc)
+        r.close()
+    tex = runs[False][1]["tex"].astype(np.float64)
+    contrast = max(np.abs(np.diff(tex, axis=0)).max(), np.abs(np.diff(tex, axis=1)).max())
+    n_big = 0
+    for (ref_t, got_t), (ref_f, got_f) in zip(runs[False][0], runs[True][0]):
+        assert (ref_t["sig"] == ref_f["sig"]).mean() >= TOPO   # the same paths in both twins
+        same = (ref_t["sig"] == got_t["sig"]) & (ref_f["sig"] == got_f["sig"])
+        assert same.mean() >= TOPO
+        e_t = path_err(ref_t["rgb"][same], got_t["rgb"][same])
+        e_f = path_err(ref_f["rgb"][same], got_f["rgb"][same])
+        big = e_t > REL
+        n_big += int(big.sum())
+        assert np.all(e_f[big] <= REL), e_f[big].max()
+        assert e_t.max() <= 1e-2 * contrast, (e_t.max(), contrast)
+        assert big.mean() <= 0.02
+    assert n_big > 0   # the model is exercised
 
 
 @pytest.mark.parametrize("handoff", [32, 96])
@@ -199,9 +247,8 @@ def test_edge_configurations_match_oracle(N, kw):
     ref = o.iteration(p, o.tables(tab), 5, tri, bary)
     got = r.iteration(cfg, 5, tri, bary, rhat=ref["rhat"])
     same = ref["sig"] == got["sig"]
-    assert same.mean() >= 0.98
-    floor = max(1e-3 * float(np.abs(ref["rgb"]).mean()), 1e-12)
-    assert rel_close(ref["rgb"][same], got["rgb"][same], floor).mean() >= 0.999
+    assert same.mean() >= TOPO
+    assert path_err(ref["rgb"][same], got["rgb"][same]).max() <= REL
     r.close()
 
 
@@ -227,10 +274,10 @@ def test_estimator_with_side_weighted_lobe_matches_oracle(N):
             es = ref["entry_sig"] == got["entry_sig"]
             n_ent += len(es)
             n_same += int(es.sum())
-            assert np.all(rel_close(ref["rhat"][es], got["rhat"][es], 1e-3))
+            assert np.all(rel_close(ref["rhat"][es], got["rhat"][es], 0.0))
             assert np.array_equal(ref["entry_nodes"][es], got["entry_nodes"][es])
             tot += float(ref["entry_nodes"].sum())
-        assert n_ent > 20 and n_same / n_ent >= 0.98
+        assert n_ent > 20 and n_same / n_ent >= TOPO
         nodes[side] = tot
     assert nodes[0.9] < nodes[0.0]
     r.close()
@@ -268,8 +315,67 @@ def test_wavefront_estimator_matches_phases_and_oracle(N, make):
         n_ent += len(es)
         n_same += int(es.sum())
         assert np.array_equal(ref["entry_nodes"][es], b["entry_nodes"][es])
-        assert np.all(rel_close(ref["rhat"][es], b["rhat"][es], 1e-3))
-    assert n_same / n_ent >= 0.98
+        assert np.all(rel_close(ref["rhat"][es], b["rhat"][es], 0.0))
+    assert n_same / n_ent >= TOPO
+    r.close()
+
+
+@pytest.mark.parametrize("film", [1, 2])
+def test_film_modes_match_oracle(N, film):
+    """The film modes of the subspace-selection comparison (1: only the
+    proxy strategy's weighted contributions; 2: all but those) give the
+    oracle's per-path values under the same mode, on a caustic scene where
+    both parts are non-zero, and the two modes add up to the full sample."""
+    sc = scenes.caustic_mini(16, 12)
+    o = O.Oracle(sc)
+    tab = learned(sc, o, M=500, M_p=500, max_depth=5)
+    r = N.Renderer(sc, tab)
+    td = o.tables(tab)
+    live = 0
+    for it in (3, 4, 5):
+        p = O.params(M=500, M_p=500, max_depth=5, film=film)
+        tri, bary = o.light_pass(p, it)
+        ref = o.iteration(p, td, it, tri, bary)
+        got = r.iteration(N.config(M=500, M_p=500, max_depth=5, film=film), it, tri, bary, rhat=ref["rhat"])
+        full = r.iteration(N.config(M=500, M_p=500, max_depth=5), it, tri, bary, rhat=ref["rhat"])
+        rest = r.iteration(N.config(M=500, M_p=500, max_depth=5, film=3 - film), it, tri, bary, rhat=ref["rhat"])
+        np.testing.assert_array_equal(got["sig"], full["sig"])
+        np.testing.assert_allclose(got["rgb"] + rest["rgb"], full["rgb"], rtol=1e-6, atol=1e-30)
+        same = ref["sig"] == got["sig"]
+        assert same.mean() >= TOPO
+        floor = max(1e-3 * float(np.abs(full["rgb"]).mean()), 1e-12)
+        assert np.all(rel_close(ref["rgb"][same], got["rgb"][same], floor))
+        live += int((np.abs(got["rgb"]).max(1) > 0).sum())
+    assert live > 0
+    r.close()
+
+
+def test_persistent_trace_stages_give_identical_estimates(N):
+    """trace = 1 runs the wavefront's trace stages on persistent warps whose
+    lanes take the next query when theirs is answered; each query is still
+    traced node by node as with one query per thread, so estimates, node
+    counts, signatures and pixels are bit-identical."""
+    sc = scenes.projector(24, 24, lens_tris_per_cap=1500, flat=True)
+    o = O.Oracle(sc)
+    tab = learned(sc, o, M=1500, M_p=1500, max_depth=8)
+    r = N.Renderer(sc, tab)
+    p = O.params(M=1500, M_p=1500, max_depth=8)
+    for it in (3, 4):
+        tri, bary = o.light_pass(p, it)
+        a = r.iteration(N.config(M=1500, M_p=1500, max_depth=8), it, tri, bary)
+        b = r.iteration(N.config(M=1500, M_p=1500, max_depth=8, trace=1), it, tri, bary)
+        assert len(a["rhat"]) > 20
+        np.testing.assert_array_equal(a["rhat"], b["rhat"])
+        np.testing.assert_array_equal(a["entry_nodes"], b["entry_nodes"])
+        np.testing.assert_array_equal(a["entry_sig"], b["entry_sig"])
+        np.testing.assert_array_equal(a["rgb"], b["rgb"])
+    r.clear()
+    s0 = r.render(N.config(M=1500, M_p=1500, max_depth=8, spp=8, iter0=50))
+    img0 = r.film()
+    r.clear()
+    s1 = r.render(N.config(M=1500, M_p=1500, max_depth=8, spp=8, iter0=50, trace=1))
+    np.testing.assert_array_equal(img0, r.film())
+    assert s0["n_nodes"] == s1["n_nodes"]
     r.close()
 
 
@@ -334,7 +440,8 @@ def test_gpu_proxy_on_off_and_pt_agree(N):
         per = []
         for k in range(8):
             r.clear()
-            r.render(N.config(M=1000, M_p=500, max_depth=5, spp=256, iter0=1000 * k, **kw), allow_truncated=True)
+            # no estimate may hit its cap: a truncated chain is a biased estimate
+            r.render(N.config(M=1000, M_p=500, max_depth=5, spp=256, iter0=1000 * k, trial_cap=1 << 20, **kw))
             per.append(r.film().mean(1))
         per = np.array(per)
         out[name] = (per.mean(0), per.var(0, ddof=1) / len(per))
@@ -345,4 +452,32 @@ def test_gpu_proxy_on_off_and_pt_agree(N):
         live = den > 0
         z = (m[live] - mp[live]) / den[live]
         assert np.abs(z).max() < 5.5 and (z * z).mean() < 2.0, (a, np.abs(z).max(), (z * z).mean())
+    r.close()
+
+
+@pytest.mark.parametrize("name", ["cornell", "caustic"])
+def test_image_mape_against_oracle_render(N, name):
+    """Whole images through the render path (waves of iterations in flight,
+    slot-ordered film accumulation, tables learned by the oracle): the GPU
+    film of iterations [0, n) against the oracle's render of the same
+    iterations, whose random numbers are the same. Image MAPE (mean over
+    pixels and channels of |x - r| / (r + 1e-2 mean r)) must be <= 1 %
+    (it is far smaller: the images are sums of paths that agree to 1e-4)."""
+    if name == "cornell":
+        sc, kw, n = scenes.cornell(16, 16), dict(M=600, M_p=300, max_depth=5), 48
+    else:
+        sc, kw, n = scenes.caustic_mini(16, 12), dict(M=500, M_p=500, max_depth=5), 96
+    o = O.Oracle(sc)
+    tab = learned(sc, o, M=kw["M"], M_p=kw["M_p"], max_depth=kw["max_depth"])
+    film, st = o.render(O.params(**kw), o.tables(tab), 0, n)
+    ref = film / n
+    r = N.Renderer(sc, tab)
+    r.clear()
+    g = r.render(N.config(spp=n, iter0=0, **kw), allow_truncated=True)
+    img = r.film().astype(np.float64)
+    eps = 1e-2 * ref.mean()
+    mape = float(np.mean(np.abs(img - ref) / (ref + eps)))
+    assert mape <= 1e-2, mape
+    assert mape <= 1e-3, mape   # the expected level: per-path parity of every sample
+    assert g["n_proxy_ok"] > 0 or name == "cornell"
     r.close()

@@ -820,6 +820,57 @@ def test_learned_tables_obey_their_definitions():
     np.testing.assert_array_equal(L0["gamma_proxy"], np.float32(1.0 / 6))
 
 
+def test_learned_cost_bound_leaves_long_cells_out_of_the_pool():
+    """The learned cost bound (an extension of the paper's sub-path type
+    limits, Sec. 6.1.1): a cell whose learning estimates average more than
+    max_chain nodes each gets MIS scale 0, and its entries leave the proxy
+    pool. With the bound off no cell is 0; with a bound of one node every
+    occupied cell is; in between, exactly the cells whose mean node count
+    (from estimates made with every entry in the pool) exceeds it."""
+    sc = scenes.caustic_mini(8, 8)
+    o = O.Oracle(sc)
+    tab = scenes.random_tables(sc, KT=8, KS=8, KSp=4, KC=2)
+    p = O.params(M=300, M_p=300, max_depth=4)
+    off = o.learn(p, tab, 1000, 2, n_bsamples=64, max_chain=-1)
+    assert np.all(off["mis_tab"] > 0)
+    # mean estimator nodes per estimate of each cell, with the learned B and
+    # every entry kept (MIS scale 1)
+    keep = dict(off, mis_tab=np.ones_like(off["mis_tab"]))
+    tot, cnt = np.zeros(off["mis_tab"].shape), np.zeros(off["mis_tab"].shape)
+    lo, hi = scenes.scene_bbox(sc)
+    for it in (1000, 1001):
+        tri, bary = o.light_pass(p, it)
+        r = o.iteration(p, o.tables(keep), it, tri, bary, pix_lo=0, pix_hi=0)
+        ents, li = o.entries(p, tri, bary)
+        assert len(ents) == len(r["rhat"])
+        for e, nn in zip(ents, r["entry_nodes"]):
+            V = sc["verts"].astype(np.float64)[sc["tris"][e.y_tri]]
+            y = V[0] + e.y_b1 * (V[1] - V[0]) + e.y_b2 * (V[2] - V[0])
+            nrm = np.cross(V[1] - V[0], V[2] - V[0])
+            f = np.concatenate([(y - lo) / (hi - lo), nrm / np.linalg.norm(nrm)])
+            Sp = int(np.argmin(((off["cent_Sp"].astype(np.float64) - f) ** 2).sum(1)))
+            C = -1
+            if e.type:
+                Vh = sc["verts"].astype(np.float64)[sc["tris"][e.h_tri]]
+                h = Vh[0] + e.h_b1 * (Vh[1] - Vh[0]) + e.h_b2 * (Vh[2] - Vh[0])
+                C = int(np.argmin(((off["cent_C"].astype(np.float64) - (h - lo) / (hi - lo)) ** 2).sum(1)))
+            tot[e.u - 1, Sp, C] += nn
+            cnt[e.u - 1, Sp, C] += 1
+    occ = cnt > 0
+    mean = np.where(occ, tot / np.maximum(cnt, 1) / p.repeats, 0)
+    assert occ.sum() >= 2 and mean[occ].min() < mean[occ].max()
+    bound = float(np.sqrt(mean[occ].min() * mean[occ].max()))
+    mid = o.learn(p, tab, 1000, 2, n_bsamples=64, max_chain=bound)
+    np.testing.assert_array_equal(mid["mis_tab"] == 0, occ & (mean > bound))
+    np.testing.assert_array_equal(mid["mis_tab"][~(occ & (mean > bound))], off["mis_tab"][~(occ & (mean > bound))])
+    one = o.learn(p, tab, 1000, 2, n_bsamples=64, max_chain=1.0)
+    np.testing.assert_array_equal(one["mis_tab"] == 0, occ)
+    # gated cells' entries are not estimated
+    tri, bary = o.light_pass(p, 1000)
+    r = o.iteration(p, o.tables(one), 1000, tri, bary, pix_lo=0, pix_hi=0)
+    assert len(r["rhat"]) == 0
+
+
 # --- whole estimator ------------------------------------------------------------
 
 def _render_mean(sc, tab, n_iter, **kw):
@@ -965,8 +1016,14 @@ def test_proxy_on_off_and_path_tracing_agree_per_pixel():
     m_off, v_off, _ = run(8, n, proxy=0)
     m_pt, v_pt, _ = run(9, n, proxy=0, conn=0)
     m_bo, v_bo, k_bo = run(10, n, proxy=1, booth=100.0)   # Booth's roulette in the proxy estimates
-    assert k_on > 500 and k_bo > 500
-    for m, v in ((m_on, v_on), (m_off, v_off), (m_bo, v_bo)):
+    # cells with MIS scale 0 leave the proxy pool (the learned cost bound):
+    # here the mirror's L D S cell (u = 1, its control subspace), keeping L S
+    gated = dict(tab, mis_tab=tab["mis_tab"].copy())
+    gated["mis_tab"][0, :, 0] = 0.0
+    td = o.tables(gated)
+    m_ga, v_ga, k_ga = run(11, n, proxy=1)
+    assert k_on > 500 and k_bo > 500 and 0 < k_ga < k_on
+    for m, v in ((m_on, v_on), (m_off, v_off), (m_bo, v_bo), (m_ga, v_ga)):
         den = np.sqrt(v + v_pt)
         live = den > 0
         z = (m[live] - m_pt[live]) / den[live]
