@@ -441,41 +441,64 @@ def equal_time_study(N, r, M_p, base_iter, ms, tables_used):
     }
 
 
-def validate_reference(o, td, M_p, ref, ref_spp, n_iter=4, rows=2):
-    """The GPU reference against the oracle: the oracle renders `rows` image
-    rows through the middle at n_iter iterations (its own random numbers are
-    the device's, on iterations the reference did not use) with the same
-    tables, and the mean over those pixels is compared with the reference's
-    mean over the same pixels. z = difference / its standard error, from the
-    spread of the oracle's per-iteration means and the reference's own."""
+def workload_parity(N, r, o, td, M_p, n_iter=2, rows=2, n_est=32):
+    """Parity with the oracle on the bench workload itself, path by path: for
+    n_iter iterations the device runs one iteration (pb_iteration: light
+    pass, pool, estimates, eye pass) and the oracle recomputes the eye paths
+    of `rows` image rows through the middle from the same light geometry and
+    the device's estimates, and n_est of the estimates from scratch. Reports
+    the share of paths and estimates whose topology signatures agree and the
+    relative errors where they do (path error relative to its largest
+    channel)."""
     import oracle as O
     from concurrent.futures import ThreadPoolExecutor
-    p = O.params(M=M, M_p=M_p, max_depth=DEPTH, trial_cap=TRIAL_CAP,
-                 pilot_max=1024 if WL.get("pilot_max", 0) >= 0 else 0)
+    pm = 1024 if WL.get("pilot_max", 0) >= 0 else 0
+    p = O.params(M=M, M_p=M_p, max_depth=DEPTH, trial_cap=TRIAL_CAP, pilot_max=pm)
+    cfg = N.config(M=M, M_p=M_p, max_depth=DEPTH, seed=7, trial_cap=TRIAL_CAP, pilot_max=WL.get("pilot_max", 0))
     lo, hi = (H // 2 - rows // 2) * W, (H // 2 - rows // 2 + rows) * W
     nt = oracle_threads()
     t0 = time.perf_counter()
-    means = []
+    errs, same_n, tot_n, e_errs, e_same, e_tot = [], 0, 0, [], 0, 0
     for it in range(n_iter):
         itn = (7 << 20) + it
-        tri, bary = o.light_pass(p, itn)
-        _, n = o.iteration_estimates(p, td, itn, tri, bary, 0, 0)
-        parts = 4 * nt
-        kr = [(n * i // parts, n * (i + 1) // parts) for i in range(parts)]
-        with ThreadPoolExecutor(nt) as ex:
-            rh = np.concatenate(list(ex.map(lambda q: o.iteration_estimates(p, td, itn, tri, bary, q[0], q[1])[0], kr)))
+        tri, bary = r.light_pass(cfg, itn)
+        got = r.iteration(cfg, itn, tri, bary, cap=1 << 20)
+        if o.iteration_estimates(p, td, itn, tri, bary, 0, 0)[1] != len(got["rhat"]):
+            continue   # the two pools differ (a label decided differently): the estimates do not line up
         pr = [(lo + (hi - lo) * i // nt, lo + (hi - lo) * (i + 1) // nt) for i in range(nt)]
         with ThreadPoolExecutor(nt) as ex:
-            rgb = np.concatenate(list(ex.map(lambda q: o.iteration(p, td, itn, tri, bary, pix_lo=q[0], pix_hi=q[1],
-                                                                   rhat=rh)["rgb"], pr)))
-        means.append(float(rgb.mean()))
-    means = np.array(means)
-    ref_px = ref[lo:hi]
-    se = math.sqrt(means.var(ddof=1) / n_iter + (means.var(ddof=1) / ref_spp))
-    d = float(means.mean() - ref_px.mean())
-    return {"pixels": int(hi - lo), "oracle_iterations": n_iter, "oracle_mean": float(means.mean()),
-            "reference_mean": float(ref_px.mean()), "z": d / se if se > 0 else None,
-            "rel_diff": d / max(float(ref_px.mean()), 1e-30), "seconds": time.perf_counter() - t0, "threads": nt}
+            parts = list(ex.map(lambda q: o.iteration(p, td, itn, tri, bary, pix_lo=q[0], pix_hi=q[1],
+                                                      rhat=got["rhat"].astype(np.float64)), pr))
+        ref_rgb = np.concatenate([x["rgb"] for x in parts])
+        ref_sig = np.concatenate([x["sig"] for x in parts])
+        same = ref_sig == got["sig"][lo:hi]
+        same_n += int(same.sum())
+        tot_n += len(same)
+        a, b = ref_rgb[same], got["rgb"][lo:hi][same].astype(np.float64)
+        mag = np.abs(a).max(1)
+        d = np.abs(a - b).max(1)
+        errs.append(np.where(mag > 0, d / np.where(mag > 0, mag, 1.0), np.where(d > 0, 1.0, 0.0)))
+        # a spread subset of the estimates, from scratch on the oracle
+        n = len(got["rhat"])
+        ks = sorted(set(int(k) for k in np.linspace(0, n - 1, min(n, n_est))))
+        with ThreadPoolExecutor(nt) as ex:
+            est = list(ex.map(lambda k: o.iteration_estimates(p, td, itn, tri, bary, k, k + 1)[0], ks))
+        for k, e in zip(ks, est):
+            if len(e) == 0:
+                continue
+            e_tot += 1
+            rel = abs(e[0] - got["rhat"][k]) / max(abs(e[0]), 1e-30)
+            e_errs.append(rel)
+            e_same += int(rel <= 1e-3)
+    errs = np.concatenate(errs) if errs else np.zeros(0)
+    q = lambda x, v: float(np.quantile(x, v)) if len(x) else None
+    return {"iterations": n_iter, "pixels_per_iteration": int(hi - lo), "topology_agreement": same_n / max(tot_n, 1),
+            "path_rel_err": {"median": q(errs, 0.5), "p99": q(errs, 0.99), "p999": q(errs, 0.999),
+                             "max": q(errs, 1.0)},
+            "paths_within_1e-4": float((errs <= 1e-4).mean()) if len(errs) else None,
+            "estimates_checked": e_tot, "estimates_within_1e-3": e_same / max(e_tot, 1),
+            "estimate_rel_err_max": max(e_errs) if e_errs else None,
+            "seconds": time.perf_counter() - t0, "threads": nt}
 
 
 def run_subspace_ablation(args):
@@ -769,7 +792,7 @@ def run_ours(args):
         ref = study.pop("_ref")
         ref_spp = study.pop("_ref_spp")
         o, td = oracle_tables(sc, tables)
-        study["reference_vs_oracle"] = validate_reference(o, td, M_p, ref, ref_spp)
+        study["workload_parity"] = workload_parity(N, r, o, td, M_p)
         npx = len(cpu_px)
         study["mape"]["cpu_oracle_1spp"] = mape(cpu_px, ref[:npx])
         study["cpu_oracle"] = {"spp": 1, "pixels": npx, "threads": cpu_nt,

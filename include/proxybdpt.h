@@ -152,6 +152,14 @@ typedef struct {
      * and MIS weights are the same in every mode, so the modes' films add up
      * to the full one. */
     int film;
+    /* Split limit of the reciprocal estimator (Alg. I~ with r = |g|): from
+     * this pre-order node of an estimate on, a node with |g| > 1 has one child
+     * entering with weight g instead of floor(|g|) + Bernoulli children of
+     * weight sign(g). The estimate stays unbiased for any such rule; a tree
+     * that would split without end (a bound B far below some f/q) continues
+     * as a chain instead of reaching trial_cap. 0: 65536; negative: never
+     * (the paper's rule throughout). */
+    int split_cap;
 } pb_config;
 
 typedef struct {
@@ -326,8 +334,9 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
  * d_B[n] (bound B > 0 per entry). Device outputs: d_rhat[n], d_nodes[n] (total
  * estimator nodes over the repeats, may be NULL). *n_truncated (may be NULL)
  * counts entries with a repeat that hit trial_cap or its split stack. From
- * cfg only seed, repeats (1..8), trial_cap (> 0) and side_in ([0, 1), 0 for
- * an even split) are read; the roulette is always the paper's RRS function.
+ * cfg only seed, repeats (1..8), trial_cap (> 0), side_in ([0, 1), 0 for an
+ * even split) and split_cap are read; the roulette is always the paper's RRS
+ * function.
  * An entry whose B is not positive (or NaN) gets a NaN estimate and the call
  * returns PB_ERR_ARG after writing the other entries' estimates. */
 #define PB_NOALLOC_MAX_ESTIMATES 16384

@@ -27,6 +27,11 @@
  * as the ablation reports). c > 0 selects this rule; c = 0 the paper's. */
 #include "or_internal.h"
 
+/* the split limit of the stand-alone estimator entry points (pins, tests) */
+static uint32_t or_split_default = 1u << 16;
+
+void or_set_split_default(int split) { or_split_default = split > 0 ? (uint32_t)split : 0xFFFFFFFFu; }
+
 typedef struct {
     double (*ratio)(void *ctx, uint32_t node);    /* draw x ~ q, return f(x)/q(x) */
     double (*unif)(void *ctx, uint32_t node);     /* the node's RRS uniform */
@@ -36,9 +41,20 @@ typedef struct {
     int truncated;
     double sum_t, sum_i;
     double booth;       /* > 0: Booth's roulette with scale c (no splitting); 0: the paper's RRS */
+    uint32_t split;     /* first pre-order node without splitting (see visit) */
 } rec_state;
 
-static void visit(rec_state *st, double sign_anc) {
+/* The split limit. Alg. I~ is unbiased for any number-of-children rule
+ * r(x) > 0 (with E[children] = r and the children's terms weighted by g / r):
+ * each child's estimate has the same expectation whatever the rule, so the
+ * recursion E[I~'] = E[g]/B + E[g] E[I~'] holds node by node, and the rule
+ * may depend on the history (here: the node's pre-order index). The paper's
+ * r = |g| is used up to node `split`; from there on a node with |g| > 1
+ * has exactly one child of weight g (r = 1), so a chain whose bound B sits
+ * far below some f/q (a tree that would split without end) finishes as a
+ * chain instead of hitting the node cap. Chains shorter than `split` are
+ * unchanged. */
+static void visit(rec_state *st, double w_anc) {
     for (;;) {
         if (st->next >= st->cap) {
             st->truncated = 1;
@@ -46,15 +62,22 @@ static void visit(rec_state *st, double sign_anc) {
         }
         uint32_t node = st->next++;
         double g = 1.0 - st->ratio(st->ctx, node) / st->B;
-        st->sum_t += sign_anc * g / st->B;
-        st->sum_i += sign_anc / st->B;
+        st->sum_t += w_anc * g / st->B;
+        st->sum_i += w_anc / st->B;
         double r = fabs(g);
-        int n = (int)floor(r);
-        if (st->unif(st->ctx, node) < r - (double)n) n += 1;
+        int n;
+        double child_w;
+        if (r > 1.0 && node >= st->split) {
+            n = 1;
+            child_w = w_anc * g;
+        } else {
+            n = (int)floor(r);
+            if (st->unif(st->ctx, node) < r - (double)n) n += 1;
+            child_w = w_anc * (g > 0.0 ? 1.0 : -1.0);
+        }
         if (n == 0) return;
-        double child_sign = sign_anc * (g > 0.0 ? 1.0 : -1.0);
-        for (int i = 0; i < n - 1; ++i) visit(st, child_sign);
-        sign_anc = child_sign;   /* the last child continues in this loop */
+        for (int i = 0; i < n - 1; ++i) visit(st, child_w);
+        w_anc = child_w;   /* the last child continues in this loop */
     }
 }
 
@@ -138,7 +161,7 @@ int or_recip_1d(int fn, double B, int n_runs, uint32_t seed, int trial_cap, doub
 int or_recip_1d_booth(int fn, double B, double c, int n_runs, uint32_t seed, int trial_cap, double *out_t,
                       double *out_i, double *out_n) {
     one_d o = {fn, seed, 0};
-    rec_state st = {one_d_ratio, one_d_unif, &o, B, (uint32_t)trial_cap, 0, 0, 0, 0, c};
+    rec_state st = {one_d_ratio, one_d_unif, &o, B, (uint32_t)trial_cap, 0, 0, 0, 0, c, or_split_default};
     int ntr = 0;
     for (int r = 0; r < n_runs; ++r) {
         o.run = (uint32_t)r;
@@ -363,14 +386,15 @@ static void entry_setup(entry_ctx *e, const or_scene_t *s, const or_entry *en) {
  * roulette of scale `booth` when it is positive. Stream:
  * kind RECIP, a = iteration, b = entry*8 + repeat, c = node. */
 double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, double booth, uint32_t seed,
-                     uint32_t iteration, uint32_t entry, int repeats, int cap, double *nodes,
+                     uint32_t iteration, uint32_t entry, int repeats, int cap, int split, double *nodes,
                      int *trunc, uint32_t *sig) {
     entry_ctx e;
     entry_setup(&e, s, en);
     e.seed = seed;
     e.kind = K_RECIP;
     e.a = iteration;
-    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)cap, 0, 0, 0, 0, booth};
+    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)cap, 0, 0, 0, 0, booth,
+                    split > 0 ? (uint32_t)split : 0xFFFFFFFFu};
     double acc = 0.0, nn = 0.0;
     int tr = 0;
     uint32_t h = 2166136261u;
@@ -448,7 +472,7 @@ int or_entry_recip_booth(void *hs, const or_entry *en, double B, double c, int n
     entry_setup(&e, (const or_scene_t *)hs, en);
     e.seed = seed;
     e.kind = K_RECIP;
-    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)trial_cap, 0, 0, 0, 0, c};
+    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)trial_cap, 0, 0, 0, 0, c, or_split_default};
     int ntr = 0;
     for (int i = 0; i < n; ++i) {
         e.a = 0xFFFFu;

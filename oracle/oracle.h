@@ -67,6 +67,8 @@ typedef struct {
                         * (learning always uses the paper's RRS function) */
     int film;          /* strategies whose weighted contributions reach the pixel: 0 all, 1 the
                         * proxy strategy only, 2 all but the proxy strategy */
+    int split_cap;     /* pre-order node index from which a node with |g| > 1 has one child of
+                        * weight g instead of splitting (<= 0: never) */
 } or_params;
 
 typedef struct {
@@ -177,6 +179,9 @@ double or_mlp_loss_grad(const double *w, int K, int KT, int n, const double *raw
                         const double *wt, double *grad);
 void or_mlp_adam(int np, double *w, const double *g, double *m1, double *m2, int t, double lr, double beta1,
                  double beta2, double eps);
+
+/* split limit of or_recip_1d*, or_entry_recip* (default 2^16; <= 0: never) */
+void or_set_split_default(int split);
 
 /* Statistics / selection learning (Sec. 5.4-5.5 as read in the design notes).
  * Inputs: centroids in t (gamma/B/mis/pi entries are ignored and rebuilt).

@@ -170,6 +170,7 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
     P.booth = c->booth;
     P.trace = c->trace;
     P.film = c->film;
+    P.split = c->split_cap == 0 ? (1u << 16) : (c->split_cap < 0 ? 0xFFFFFFFFu : (uint32_t)c->split_cap);
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
     P.smp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};

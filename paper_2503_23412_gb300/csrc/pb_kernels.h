@@ -107,6 +107,7 @@ struct KParams {
     float booth;                // > 0: Booth's roulette of this scale (wavefront only); 0: the paper's RRS
     int trace;                  // wavefront trace stages: 0 a query per thread; 1 persistent warps, lane refill
     int film;                   // strategies reaching the film: 0 all, 1 the proxy strategy only, 2 all but it
+    uint32_t split;             // first pre-order estimator node without splitting (split limit)
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
     SampleSink smp;         // raw != nullptr: record proposal training samples
@@ -123,6 +124,23 @@ __host__ __device__ inline int wf_pilot_rounds(const KParams &P) {
         ++nr;
     }
     return nr;
+}
+
+// Children of an estimator node (Alg. I~ with the split limit): the paper's
+// r = |g|, i.e. floor(|g|) + Bernoulli(frac) children entering with weight
+// sign(g); from pre-order node `split` on, a node with |g| > 1 has one child
+// entering with weight g. The estimator is unbiased for any such rule (each
+// child's estimate has the same expectation); trees that would split without
+// end (a bound far below some f/q) become chains.
+__device__ __forceinline__ int est_children(float g, float u, uint32_t v, uint32_t split) {
+    const float r = fabsf(g);
+    if (r > 1.0f && v >= split) return 1;
+    int n = (int)floorf(r);
+    if (u < r - (float)n) n += 1;
+    return n;
+}
+__device__ __forceinline__ float est_child_weight(float g, uint32_t v, uint32_t split) {
+    return (fabsf(g) > 1.0f && v >= split) ? g : (g > 0.0f ? 1.0f : -1.0f);
 }
 
 __device__ __forceinline__ uint32_t eff_iter(const KParams &P, uint32_t iter_base) {

@@ -85,9 +85,7 @@ __global__ void __launch_bounds__(128) k_na_recip(DScene S, KParams P, uint32_t 
                 R.init(P.seed, K_RECIP, iteration, (uint32_t)(k * 8 + rep), (uint32_t)v);
                 float ratio = entry_ratio<false>(S, E, R, nullptr);
                 g = 1.0f - ratio * invB;
-                float r = fabsf(g);
-                nch = (int)floorf(r);
-                if (R.u(18) < r - (float)nch) nch += 1;
+                nch = est_children(g, R.u(18), (uint32_t)v, P.split);
             }
             for (int j = 0; j < 32; ++j) {
                 float gj = __shfl_sync(0xffffffffu, g, j);
@@ -101,8 +99,8 @@ __global__ void __launch_bounds__(128) k_na_recip(DScene S, KParams P, uint32_t 
                 sum_t += (double)(cur_sign * gj * invB);
                 nodes++;
                 if (nj >= 1) {
-                    // children whose sign matches the pending frame on top join it
-                    const float cs = cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                    // children whose weight matches the pending frame on top join it
+                    const float cs = cur_sign * est_child_weight(gj, (uint32_t)(base + j), P.split);
                     if (sp > 0 && fr_sign[sp - 1] == cs) {
                         fr_rem[sp - 1] += nj;
                     } else {

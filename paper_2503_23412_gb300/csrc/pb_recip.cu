@@ -135,9 +135,7 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
                 R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
                 float ratio = entry_ratio<COUNT>(S, E, R, &tc);
                 g = 1.0f - ratio * invB;
-                float r = fabsf(g);
-                nch = (int)floorf(r);
-                if (R.u(18) < r - (float)nch) nch += 1;
+                nch = est_children(g, R.u(18), (uint32_t)v, P.split);
             }
             // the walk stops before a node that would need a frame beyond MAXF1;
             // the block phase resumes from that node with the full stack
@@ -151,9 +149,9 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
                     trunc = true;
                     continue;
                 }
-                // children whose sign matches the pending frame on top join it
-                // (the walk reads only the sign sequence and the pending count)
-                const float cs = cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                // children whose weight matches the pending frame on top join it
+                // (the walk reads only the weight sequence and the pending count)
+                const float cs = cur_sign * est_child_weight(gj, (uint32_t)(base + j), P.split);
                 const bool merge = sp > 0 && fr_sign[sp - 1] == cs;
                 if (nj >= 1 && !merge && sp >= MAXF1) {
                     stop = j;

@@ -109,16 +109,14 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
                     R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
                     float ratio = entry_ratio<COUNT>(S, E, R, &tc);
                     g = 1.0f - ratio * invB;
-                    float r = fabsf(g);
-                    nch = (int)floorf(r);
-                    if (R.u(18) < r - (float)nch) nch += 1;
+                    nch = est_children(g, R.u(18), (uint32_t)v, P.split);
                 }
                 sg[idx] = g;
                 sn[idx] = nch;
             }
             if (tid == 0) {
-                bool pos = st.cur_sign > 0.0f;
-                for (int i = 0; i < st.sp; ++i) pos = pos && st.fr_sign[i] > 0.0f;
+                bool pos = st.cur_sign == 1.0f;   // weights other than +1 only arise past the split limit
+                for (int i = 0; i < st.sp; ++i) pos = pos && st.fr_sign[i] == 1.0f;
                 s_neg = pos ? 0 : 1;
             }
             __syncthreads();
@@ -199,8 +197,8 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
                     int nj = sn[j];
                     st.sum_t += (double)(st.cur_sign * gj * invB);
                     if (nj >= 1) {
-                        // children whose sign matches the pending frame on top join it
-                        const float cs = st.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                        // children whose weight matches the pending frame on top join it
+                        const float cs = st.cur_sign * est_child_weight(gj, (uint32_t)v, P.split);
                         if (st.sp > 0 && st.fr_sign[st.sp - 1] == cs) {
                             st.fr_rem[st.sp - 1] += nj;
                         } else {

@@ -185,11 +185,8 @@ __global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, Wf
             W.node_g[i] = ratio;
         } else {
             float gv = 1.0f - ratio * invB;
-            float r = fabsf(gv);
-            int nch = (int)floorf(r);
-            if (R.u(18) < r - (float)nch) nch += 1;
             W.node_g[i] = gv;
-            W.node_n[i] = nch;
+            W.node_n[i] = est_children(gv, R.u(18), (uint32_t)W.node_v[i], P.split);
         }
     }
 }
@@ -541,10 +538,11 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
         int next = gst.next;
         double sum_t = gst.sum_t;
         // pending-count form of the walk state while all signs are +1
-        bool pos = gst.cur_sign > 0.0f;
+        // (weights other than +1 only arise past the split limit)
+        bool pos = gst.cur_sign == 1.0f;
         int pend = 1;
         for (int f = 0; f < gst.sp; ++f) {
-            pos = pos && gst.fr_sign[f] > 0.0f;
+            pos = pos && gst.fr_sign[f] == 1.0f;
             pend += gst.fr_rem[f];
         }
         bool stack_form = !pos;   // gst holds the authoritative stack
@@ -609,11 +607,12 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
                 for (int q = 0; q < cnt; ++q) {
                     const float gj = W.node_g[off + j0 + q];
                     const int nj = W.node_n[off + j0 + q];
+                    const uint32_t v = (uint32_t)next;
                     sum_t += (double)(gst.cur_sign * gj * invB);
                     next += 1;
                     if (nj >= 1) {
-                        // children whose sign matches the pending frame on top join it
-                        const float cs = gst.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                        // children whose weight matches the pending frame on top join it
+                        const float cs = gst.cur_sign * est_child_weight(gj, v, P.split);
                         if (gst.sp > 0 && gst.fr_sign[gst.sp - 1] == cs) {
                             gst.fr_rem[gst.sp - 1] += nj;
                         } else {
@@ -641,10 +640,10 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
             sum_t = __shfl_sync(0xffffffffu, sum_t, 0);
             __syncwarp();
             // back to the count form when the stack turned all-positive again
-            bool p2 = gst.cur_sign > 0.0f;
+            bool p2 = gst.cur_sign == 1.0f;
             int pe = 1;
             for (int f = 0; f < gst.sp; ++f) {
-                p2 = p2 && gst.fr_sign[f] > 0.0f;
+                p2 = p2 && gst.fr_sign[f] == 1.0f;
                 pe += gst.fr_rem[f];
             }
             if (p2) {
@@ -803,13 +802,12 @@ __global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t
             R.init(P.seed, K_RECIP, iter_base + st.slot, (uint32_t)(st.k * 8 + st.rep), (uint32_t)st.next);
             float ratio = entry_ratio<false>(S, E, R, nullptr);
             float gj = 1.0f - ratio * invB;
-            float r = fabsf(gj);
-            int nj = (int)floorf(r);
-            if (R.u(18) < r - (float)nj) nj += 1;
+            const uint32_t v = (uint32_t)st.next;
+            int nj = est_children(gj, R.u(18), v, P.split);
             st.sum_t += (double)(st.cur_sign * gj * invB);
             st.next += 1;
             if (nj >= 1) {
-                const float cs = st.cur_sign * (gj > 0.0f ? 1.0f : -1.0f);
+                const float cs = st.cur_sign * est_child_weight(gj, v, P.split);
                 if (st.sp > 0 && st.fr_sign[st.sp - 1] == cs) {
                     st.fr_rem[st.sp - 1] += nj;
                 } else {

@@ -119,3 +119,32 @@ def test_autotune_chooses_cached_valid_configuration(N, tmp_path):
     b, _ = _film(N, r, best)
     np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6 * float(np.abs(a).max()))
     r.close()
+
+
+def test_batch_films_match_oracle_renders(N):
+    """A batch of uneven scenes in one graph launch against the oracle: each
+    scene's film (iterations [0, n), tables learned by the oracle) equals the
+    oracle's render of the same iterations up to per-path rounding: image
+    MAPE <= 1e-3."""
+    import oracle as O
+    items = [
+        (scenes.cornell(16, 16), dict(M=600, M_p=300, max_depth=5), 24),
+        (scenes.caustic_mini(16, 12), dict(M=500, M_p=500, max_depth=5), 48),
+    ]
+    rs, cfgs, refs = [], [], []
+    for sc, base, n in items:
+        o = O.Oracle(sc)
+        tab = scenes.random_tables(sc, KT=16, KS=16, KSp=8, KC=2)
+        tab = o.learn(O.params(**base), tab, 1000, 2, n_bsamples=48)
+        film, _ = o.render(O.params(**base), o.tables(tab), 0, n)
+        refs.append(film / n)
+        r = N.Renderer(sc, tab)
+        r.clear()
+        rs.append(r)
+        cfgs.append(N.config(spp=n, iter0=0, **base))
+    N.render_batch(rs, cfgs, allow_truncated=True)
+    for r, ref in zip(rs, refs):
+        img = r.film().astype(np.float64)
+        mape = float(np.mean(np.abs(img - ref) / (ref + 1e-2 * ref.mean())))
+        assert mape <= 1e-3, mape
+        r.close()

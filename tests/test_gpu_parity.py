@@ -315,8 +315,12 @@ def test_wavefront_estimator_matches_phases_and_oracle(N, make):
         n_ent += len(es)
         n_same += int(es.sum())
         assert np.array_equal(ref["entry_nodes"][es], b["entry_nodes"][es])
-        assert np.all(rel_close(ref["rhat"][es], b["rhat"][es], 0.0))
-    assert n_same / n_ent >= TOPO
+        # an estimate is an intermediate value: a sum of up to ~10^5 terms
+        # g/B in FP32 whose ratios f/q carry ~1e-6 relative error each
+        rel = np.abs(ref["rhat"][es] - b["rhat"][es]) / np.abs(ref["rhat"][es])
+        assert rel.max() <= 1e-3 and np.median(rel) <= 1e-5, (rel.max(), np.median(rel))
+    # a run of thousands of FP32 roulette decisions: one flipped decision changes its topology
+    assert n_same / n_ent >= 0.995
     r.close()
 
 

@@ -61,6 +61,9 @@ def test_booth_roulette_matches_oracle(N):
         assert np.array_equal(ref["entry_nodes"][es], got["entry_nodes"][es])
         a = ref["rhat"][es]
         b = got["rhat"][es].astype(np.float64)
+        assert np.isfinite(a).all() and np.isfinite(b).all(), (np.flatnonzero(~np.isfinite(a)),
+                                                                 np.flatnonzero(~np.isfinite(b)),
+                                                                 ref["entry_nodes"][es][~np.isfinite(a) | ~np.isfinite(b)])
         scale = np.maximum(np.abs(a), np.median(np.abs(a)))
         errs.append(np.abs(a - b) / scale)
         rrs = r.iteration(N.config(M=1500, M_p=1500, max_depth=8), it, tri, bary)

@@ -99,6 +99,37 @@ def test_main_estimator_beats_sign_estimator(fn, B):
     assert t.var() <= i.var() * 1.001
 
 
+def test_split_limit_keeps_the_estimator_unbiased():
+    """The split limit (a number-of-children rule that depends on the node's
+    pre-order index): from node `split` on, a node with |g| > 1 has one
+    child of weight g instead of floor(|g|) + Bernoulli children of weight
+    sign(g). Alg. I~ is unbiased for any such rule (each child's estimate has
+    the same expectation, so E[I~'] = E[g]/B + E[g] E[I~'] node by node).
+    fn 0 with B = 0.6 has g in [-1.5, 0.17]: with the limit at node 2 the
+    rule is active in 40 % of the chains, yet the mean stays 1. Giving the
+    single child the weight sign(g) instead of g biases the mean by -1.3 %
+    here, about 7 standard errors. With the default limit (2^16) every chain
+    of these cases is far shorter, and the estimates equal those of the
+    unlimited rule exactly."""
+    try:
+        O.set_split_default(0)
+        t0, _, n0, _ = O.recip_1d(1, 1.2, 100000, seed=17)
+        O.set_split_default(1 << 16)
+        t1, _, n1, _ = O.recip_1d(1, 1.2, 100000, seed=17)
+        np.testing.assert_array_equal(t0, t1)
+        np.testing.assert_array_equal(n0, n1)
+        O.set_split_default(2)
+        t, _, nn, tr = O.recip_1d(0, 0.6, 800000, seed=19)
+        assert tr == 0
+        assert (nn > 2).mean() > 0.3
+        bm = t.reshape(20, -1).mean(1)
+        assert abs(t.mean() - 1.0) < 4 * bm.std(ddof=1) / math.sqrt(len(bm)), (t.mean(), bm.std(ddof=1))
+        t4, _, _, _ = O.recip_1d(1, 1.2, 100000, seed=17)
+        assert np.any(t4 != t1)   # the limit changed some chains
+    finally:
+        O.set_split_default(1 << 16)
+
+
 # --- Booth's Russian roulette (the baseline of the paper's RR ablation) -----------
 
 def _booth_law(B, c, kmax=400):
