@@ -398,7 +398,7 @@ def train_network(N, r, M_p, base_iter):
     tr = r.train_proposal(N.config(M=M, M_p=M_p, max_depth=DEPTH, seed=7, trial_cap=TRIAL_CAP,
                                    pilot_max=WL.get("pilot_max", 0)),
                           N.train_desc(samples=1 << 20, rounds=rounds, steps=500, batch=8192, lr=3e-3, seed=5,
-                                       iter0=(1 << 23) + base_iter))
+                                       iter0=(1 << 23) + base_iter, proxy=1))
     tr["train_s"] = time.perf_counter() - t0
     return tr
 
@@ -415,7 +415,7 @@ def equal_time_study(N, r, M_p, base_iter, ms, tables_used):
     base = dict(M=M, M_p=M_p, max_depth=DEPTH, seed=7, trial_cap=TRIAL_CAP, pilot_max=WL.get("pilot_max", 0))
     ref_spp = WL["ref_mult"] * SPP
     mt = r.connection_moments(N.config(spp=4, iter0=base_iter + (5 << 20), **base))
-    ml = r.connection_moments(N.config(spp=4, iter0=base_iter + (5 << 20), proposal=1, **base))
+    ml = r.connection_moments(N.config(spp=4, iter0=base_iter + (5 << 20), proposal=2, **base))
     t0 = time.perf_counter()
     r.clear()
     st_ref = r.render(N.config(spp=ref_spp, iter0=base_iter + (2 << 20), **base), allow_truncated=True)
@@ -426,7 +426,7 @@ def equal_time_study(N, r, M_p, base_iter, ms, tables_used):
     r.render(N.config(spp=SPP, iter0=base_iter + (3 << 20), **base), allow_truncated=True)
     img_t = r.film().astype(np.float64)
     r.clear()
-    r.render(N.config(spp=spp_l, iter0=base_iter + (4 << 20), proposal=1, **base), allow_truncated=True)
+    r.render(N.config(spp=spp_l, iter0=base_iter + (4 << 20), proposal=2, **base), allow_truncated=True)
     img_l = r.film().astype(np.float64)
     r.clear()
     return {
@@ -688,7 +688,7 @@ def run_ours(args):
     if proposal == "learned" or study_on:
         trained = train_network(N, r, M_p, base_iter)   # before timing, like the tables
     cfg = N.config(M=M, M_p=M_p, max_depth=DEPTH, spp=SPP, seed=7, booth=BOOTH, trace=TRACE, trial_cap=TRIAL_CAP,
-                   proposal=1 if proposal == "learned" else 0, pilot_max=pilot)
+                   proposal=2 if proposal == "learned" else 0, pilot_max=pilot)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step(i, count=False, prop=None):
@@ -725,7 +725,7 @@ def run_ours(args):
     # the other proposal, for the equal-time comparison (untimed with respect to the headline)
     other_ms = None
     if study_on:
-        other = 0 if cfg.proposal == 1 else 1
+        other = 0 if cfg.proposal == 2 else 2
         step(nxt, prop=other)
         ot = []
         for i in range(2):
@@ -754,9 +754,10 @@ def run_ours(args):
     sha = src_sha(REC_SRC if dom == "k_recip" else EYE_SRC)
     # end to end through the C ABI with host buffers, every step: scene upload (host BVH build included),
     # tables and network upload, render, film readback
-    w_net = r.mlp_readback() if cfg.proposal == 1 else None
+    w_net = r.mlp_readback() if cfg.proposal == 2 else None
+    w_prx = r.mlp_proxy_readback() if cfg.proposal == 2 else None
     h2d = sum(v.nbytes for v in sc.values()) + sum(v.nbytes for v in tables.values() if isinstance(v, np.ndarray))
-    h2d += 0 if w_net is None else w_net.nbytes
+    h2d += 0 if w_net is None else w_net.nbytes + w_prx.nbytes
     d2h = W * H * 3 * 4
     e2e_t = []
     for i in range(max(1, min(args.steps, 3))):
@@ -766,6 +767,7 @@ def run_ours(args):
         r.upload_tables(tables)
         if w_net is not None:
             r.mlp_upload(w_net)
+            r.mlp_proxy_upload(w_prx)
         cfg.iter0 = base_iter + (nxt + i) * SPP
         cfg.count_traversal = 0
         r.clear()
@@ -780,7 +782,7 @@ def run_ours(args):
         return
     study = None
     if study_on:
-        ms_pair = {"learned": total_ms / args.steps, "table": other_ms} if cfg.proposal == 1 else \
+        ms_pair = {"learned": total_ms / args.steps, "table": other_ms} if cfg.proposal == 2 else \
             {"table": total_ms / args.steps, "learned": other_ms}
         study = equal_time_study(N, r, M_p, base_iter, ms_pair, tables)
         study["learned_value"] = W * H * SPP / (ms_pair["learned"] * 1e-3) / 1e6
@@ -802,7 +804,11 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "proposal": proposal, "M": M, "M_p": M_p, "spp": SPP, "max_depth": DEPTH,
+        "config": {"workload": WORKLOAD,
+                   "proposal": ("learned: networks for the connection's light subspace S and the proxy's specular "
+                                "subspace S', each mixed 0.9 / 0.1 with its table row" if proposal == "learned"
+                                else "table rows Gamma and Gamma'"),
+                   "M": M, "M_p": M_p, "spp": SPP, "max_depth": DEPTH,
                    "triangles": int(len(sc["tris"])), "trial_cap": TRIAL_CAP,
                    "l2": "256 MiB buffer written before every timed step",
                    "tables": "learned on the device before timing (%.1f s, %d learning iterations); %d of %d "

@@ -115,7 +115,13 @@ typedef struct {
     /* Light-subspace proposal of the subspace connection (Sec. 3.2): 0 = the
      * table row Gamma[T, .]; 1 = the learned network mixed with the table,
      * Q(S | x) = 0.9 softmax(MLP(x))_S + 0.1 Gamma[T, S] / Z_T over occupied
-     * subspaces (needs a network: pb_mlp_upload or pb_train_proposal). */
+     * subspaces (needs a network: pb_mlp_upload or pb_train_proposal);
+     * 2 = also the proxy strategy's specular subspace S' from its own network,
+     * Q'(S' | x) = 0.9 softmax(MLP'(x))_S' + 0.1 Gamma'[T, S'] / Z'_T over the
+     * subspaces that hold incomplete sub-paths, in place of the row
+     * Gamma'[T, .] of Sec. 5.5 (needs pb_mlp_proxy_upload or training with
+     * pb_train_desc.proxy = 1). The proxy estimate divides by the drawn
+     * subspace's Q', so it stays unbiased. */
     int proposal;
     /* 1: capture the render's waves as a CUDA graph the first time this
      * configuration is seen on the context, then replay it (iter0 becomes a
@@ -360,6 +366,10 @@ size_t pb_mlp_nparams(int KS, int KT);
 /* copies the n = pb_mlp_nparams weights (host) and resets Adam's moments */
 pb_status pb_mlp_upload(pb_ctx *ctx, const float *w, size_t n);
 pb_status pb_mlp_readback(pb_ctx *ctx, float *w, size_t n);
+/* the proxy strategy's network: the same layout with KSp outputs, n =
+ * pb_mlp_nparams(KSp, KT) with the tables' KSp (<= 384) */
+pb_status pb_mlp_proxy_upload(pb_ctx *ctx, const float *w, size_t n);
+pb_status pb_mlp_proxy_readback(pb_ctx *ctx, float *w, size_t n);
 /* logits of n rows: raw features n x 10 (host), eye subspaces T (host); z is
  * n x KS (host). Runs the tensor-core kernel of the render path. */
 pb_status pb_mlp_logits(pb_ctx *ctx, int n, const float *raw, const int32_t *T, float *z);
@@ -383,11 +393,14 @@ typedef struct {
     int iters_per_wave;        /* iterations in flight while collecting (0: 8) */
     int reinit;                /* 1: start from a fresh initialisation even if a network is loaded */
     int learned_first;         /* 1: the first round already collects with the network */
+    int proxy;                 /* 1: also train the proxy strategy's network (proposal 2) */
 } pb_train_desc;
 
 typedef struct {
     int64_t iterations, samples, steps;
     double loss_first, loss_last;
+    int64_t samples_proxy;     /* the proxy network's training samples (proxy = 1) */
+    double loss_proxy_first, loss_proxy_last;
 } pb_train_stats;
 
 /* Online training: each round renders collection iterations (never added to
@@ -395,7 +408,10 @@ typedef struct {
  * learned_first -- and records one sample per connection with a non-zero
  * contribution (features, T, the chosen S, the unweighted contribution
  * luminance, which already carries the 1/Q(S) of the proposal that drew it),
- * then takes `steps` Adam steps on mini-batches of those samples. */
+ * then takes `steps` Adam steps on mini-batches of those samples. With
+ * proxy = 1 each successful proxy connection also records a sample (its S',
+ * the unweighted contribution luminance clamped at 0, since the reciprocal
+ * estimate in it is signed) and the proxy network takes its own steps. */
 pb_status pb_train_proposal(pb_ctx *ctx, const pb_config *cfg, const pb_train_desc *td, pb_train_stats *out);
 
 /* Moments of the subspace-connection estimate under cfg->proposal: renders

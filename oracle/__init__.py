@@ -53,7 +53,7 @@ class TablesDesc(C.Structure):
                 ("cent_C", C.c_void_p), ("gamma_conn", C.c_void_p), ("gamma_proxy", C.c_void_p),
                 ("B_tab", C.c_void_p), ("mis_tab", C.c_void_p),
                 ("tile", C.c_int), ("grid_w", C.c_int), ("grid_h", C.c_int), ("pi_grid", C.c_void_p),
-                ("mlp_w", C.c_void_p)]
+                ("mlp_w", C.c_void_p), ("mlp_wp", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -177,10 +177,13 @@ class Oracle:
                        _p(keep["bbox_lo"]), _p(keep["bbox_hi"]), _p(keep["cent_T"]), _p(keep["cent_S"]),
                        _p(keep["cent_Sp"]), _p(keep["cent_C"]), _p(keep["gamma_conn"]),
                        _p(keep["gamma_proxy"]), _p(keep["B_tab"]), _p(keep["mis_tab"]),
-                       int(t["tile"]), gw, gh, _p(keep["pi_grid"]), None)
+                       int(t["tile"]), gw, gh, _p(keep["pi_grid"]), None, None)
         if t.get("mlp_w") is not None:
             keep["mlp_w"] = np.ascontiguousarray(t["mlp_w"], np.float64)
             d.mlp_w = _p(keep["mlp_w"])
+        if t.get("mlp_wp") is not None:   # the proxy strategy's network (K = KSp)
+            keep["mlp_wp"] = np.ascontiguousarray(t["mlp_wp"], np.float64)
+            d.mlp_wp = _p(keep["mlp_wp"])
         d._keep = keep
         return d
 

@@ -92,7 +92,12 @@ static void walk_booth(rec_state *st) {
         }
         uint32_t node = st->next++;
         prod *= 1.0 - st->ratio(st->ctx, node) / st->B;
-        st->sum_t += prod / surv / st->B;
+        double t = prod / surv / st->B;
+        if (!isfinite(t)) {   /* the weight left the double range: a truncated chain */
+            st->truncated = 1;
+            return;
+        }
+        st->sum_t += t;
         double rho = st->booth * fabs(prod);
         if (rho > 1.0) rho = 1.0;
         if (!(st->unif(st->ctx, node) < rho)) return;

@@ -49,7 +49,7 @@ typedef struct {
     int KT, KS, KSp, KC;
     double lo[3], ext[3];
     const float *cT, *cS, *cSp, *cC, *gC, *gP, *Bt, *mis, *pi;
-    const double *mlp;
+    const double *mlp, *mlp_p;
     int tile, gw, gh;
 } or_tab;
 
@@ -87,6 +87,7 @@ static void tab_init(or_tab *T, const or_tables_desc *t) {
     T->gC = t->gamma_conn; T->gP = t->gamma_proxy; T->Bt = t->B_tab; T->mis = t->mis_tab;
     T->pi = t->pi_grid; T->tile = t->tile; T->gw = t->grid_w; T->gh = t->grid_h;
     T->mlp = t->mlp_w;
+    T->mlp_p = t->mlp_wp;
 }
 
 static int nearest(const double *f, int dim, int K, const float *cent) {
@@ -619,9 +620,25 @@ static v3 eye_path(const or_scene_t *s, const or_tab *T, const or_params *p, con
                 if (coin) {
                     if (Tl < 0) Tl = label_dir(T, z, we, T->KT, T->cT);
                     double Q;
-                    int slot = select_item(T->gP + (size_t)Tl * T->KSp, T->KSp, it->estart,
+                    int slot;
+                    if (T->mlp_p && i + 2 <= p->max_depth) {
+                        /* learned proposal of the proxy: S' ~ Q'(. | x) (the network mixed with the row
+                         * Gamma'[T, .]), then a uniform incomplete sub-path of S'; deeper than
+                         * max_depth - 2 no proxy can fit, and the table row is drawn */
+                        double raw[10], QS;
+                        feat_raw(s, T, z, we, raw);
+                        int Sel = or_mlp_select(T->mlp_p, T->KSp, raw, Tl, T->gP + (size_t)Tl * T->KSp, it->estart,
+                                                or_rnd(p->seed, K_CAMERA, iteration, pu, ci, 9), &QS);
+                        int nS = it->estart[Sel + 1] - it->estart[Sel];
+                        int jq = (int)floor(or_rnd(p->seed, K_CAMERA, iteration, pu, ci, 10) * nS);
+                        if (jq > nS - 1) jq = nS - 1;
+                        slot = it->estart[Sel] + jq;
+                        Q = QS / nS;
+                    } else {
+                        slot = select_item(T->gP + (size_t)Tl * T->KSp, T->KSp, it->estart,
                                            or_rnd(p->seed, K_CAMERA, iteration, pu, ci, 9),
                                            or_rnd(p->seed, K_CAMERA, iteration, pu, ci, 10), &Q);
+                    }
                     int jj = it->eitems[slot];
                     const or_entry *E = &it->ent[jj];
                     sig = sig_upd(sig, (uint32_t)jj);
@@ -897,6 +914,7 @@ void or_learn(void *hs, const or_params *p_in, const or_tables_desc *td, int ite
      * (MIS scale 1 everywhere while learning) */
     or_tables_desc t2 = *td;
     t2.mlp_w = NULL;   /* statistics are learned with the table proposal */
+    t2.mlp_wp = NULL;
     t2.B_tab = B_out;
     for (int c = 0; c < ncell; ++c) mis_out[c] = 1.0f;
     t2.mis_tab = mis_out;

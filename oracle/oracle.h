@@ -49,6 +49,8 @@ typedef struct {
     int tile, grid_w, grid_h;
     const float *pi_grid;             /* grid_h*grid_w proxy probability per tile */
     const double *mlp_w;              /* learned light-subspace proposal (or_mlp.c layout), NULL: table rows */
+    const double *mlp_wp;             /* learned specular-subspace proposal of the proxy strategy (or_mlp.c
+                                       * layout with K = KSp), NULL: the rows Gamma'[T, .] */
 } or_tables_desc;
 
 typedef struct {

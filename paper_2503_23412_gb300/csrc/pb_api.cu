@@ -131,7 +131,8 @@ pb_status check_cfg(pb_ctx *ctx, const pb_config *c) {
     if (c->repeats < 1 || c->repeats > 8) return fail(ctx, PB_ERR_ARG, "repeats must be in [1, 8]");
     if (c->trial_cap < 1) return fail(ctx, PB_ERR_ARG, "trial_cap must be positive");
     if (c->spp < 0) return fail(ctx, PB_ERR_ARG, "spp must be >= 0");
-    if (c->proposal < 0 || c->proposal > 1) return fail(ctx, PB_ERR_ARG, "proposal must be 0 (table) or 1 (learned)");
+    if (c->proposal < 0 || c->proposal > 2)
+        return fail(ctx, PB_ERR_ARG, "proposal must be 0 (table), 1 (learned connection) or 2 (and learned proxy)");
     if (!(c->side_in >= 0.0f && c->side_in < 1.0f)) return fail(ctx, PB_ERR_ARG, "side_in must lie in [0, 1)");
     if (c->estimator < 0 || c->estimator > 1) return fail(ctx, PB_ERR_ARG, "estimator must be 0 or 1");
     if (!(c->booth >= 0.0f && c->booth < 3.0e38f)) return fail(ctx, PB_ERR_ARG, "booth must be finite and >= 0");
@@ -170,6 +171,7 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
     P.booth = c->booth;
     P.trace = c->trace;
     P.film = c->film;
+    P.proposal = c->proposal;
     P.split = c->split_cap == 0 ? (1u << 16) : (c->split_cap < 0 ? 0xFFFFFFFFu : (uint32_t)c->split_cap);
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
@@ -573,7 +575,8 @@ pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *t) {
 
 }  // extern "C"
 
-pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t iter_base, const SampleSink &sink) {
+pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t iter_base, const SampleSink &sink,
+                          const SampleSink &sink_proxy) {
     KParams P = kparams(ctx, cfg);
     pb_status s = ensure_pool(ctx, slots, P.M * P.L, P.repeats, P.npix);
     if (s != PB_OK) return s;
@@ -586,6 +589,7 @@ pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t
         if (s != PB_OK) return s;
     }
     P.smp = sink;
+    P.smpp = sink_proxy;
     s = pb_eye_stages(ctx, P, slots, iter_base, nullptr, ctx->stream);
     if (s != PB_OK) return s;
     if (cfg->proposal) return mlp_check_err(ctx);
@@ -593,7 +597,7 @@ pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t
 }
 
 // ---- wavefront estimator buffers ------------------------------------------------
-constexpr int WF_NODE_CAP = 1 << 23;   // nodes per round (about 1 GB of state)
+constexpr int WF_NODE_CAP = 1 << 25;   // nodes per round (about 4 GB of state): long chains rarely wait
 
 pb_status wf_ensure(pb_ctx *ctx) {
     const int chains = ctx->B.chain_cap;
@@ -715,7 +719,7 @@ static pb_status prepare_render(pb_ctx *ctx, const pb_config *cfg, KParams &P, i
     s = ensure_pool(ctx, slots, P.M * P.L, P.repeats, P.npix);
     if (s != PB_OK) return s;
     if (cfg->proposal) {
-        s = mlp_prepare(ctx, slots, P.max_depth);
+        s = mlp_prepare(ctx, slots, P.max_depth, cfg->proposal);
         if (s != PB_OK) return s;
     }
     if (cfg->estimator == 0) {

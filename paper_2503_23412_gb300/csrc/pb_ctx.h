@@ -64,7 +64,8 @@ struct pb_ctx {
     float *film = nullptr;
     int64_t film_iters = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    MlpState mlp;
+    MlpState mlp;        // the connection's network (K = KS)
+    MlpState mlp_p;      // the proxy strategy's network (K = KSp), proposal = 2
     std::vector<RenderGraph *> graphs;
     uint32_t *d_iter0 = nullptr;     // iteration base of graph replays
     // wavefront estimator buffers (allocated on first use)
@@ -109,11 +110,12 @@ pb_status pb_eye_ensure(pb_ctx *ctx, int slots, int depth);
 void pb_noalloc_setup(pb_ctx *ctx);
 // learned proposal (pb_mlp.cu)
 void mlp_free(pb_ctx *ctx);
-pb_status mlp_prepare(pb_ctx *ctx, int slots, int depth);
+pb_status mlp_prepare(pb_ctx *ctx, int slots, int depth, int proposal);
 void free_graphs(pb_ctx *ctx);
 pb_status wf_ensure(pb_ctx *ctx);
 pb_status wf_check(pb_ctx *ctx);
 pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base, const EyeEvents *ev = nullptr);
 pb_status mlp_check_err(pb_ctx *ctx);
 // one wave of iterations that records proposal training samples and leaves the film alone (pb_api.cu)
-pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t iter_base, const SampleSink &sink);
+pb_status pb_collect_wave(pb_ctx *ctx, const pb_config *cfg, int slots, uint32_t iter_base, const SampleSink &sink,
+                          const SampleSink &sink_proxy = SampleSink{});

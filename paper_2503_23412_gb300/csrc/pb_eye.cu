@@ -328,14 +328,24 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                 sig = sig_upd(sig, 0xC0000000u | (coin ? 1u : 0u));
                 if (coin) {
                     if (Tl < 0) Tl = label_dir(S, z, we, T.KT, T.cT);
-                    const float *cdf = B.cdfP + (size_t)slot * T.KT * T.KSp + (size_t)Tl * T.KSp;
-                    int Ssel = select_cdf(cdf, T.KSp, R.u(9));
+                    int Ssel;
+                    float QS;   // probability of the specular subspace
+                    if (P.mlpp.sel && a + 2 <= P.max_depth) {
+                        // learned proposal of the proxy: drawn by the proxy network's kernel
+                        const size_t row = ((size_t)slot * P.mlpp.A + (a - 1)) * P.npix + pix;
+                        Ssel = P.mlpp.sel[row];
+                        QS = P.mlpp.selq[row];
+                    } else {
+                        const float *cdf = B.cdfP + (size_t)slot * T.KT * T.KSp + (size_t)Tl * T.KSp;
+                        Ssel = select_cdf(cdf, T.KSp, R.u(9));
+                        QS = T.gP[(size_t)Tl * T.KSp + Ssel] / B.ZP[(size_t)slot * T.KT + Tl];
+                    }
                     const int32_t *est = B.estart + (size_t)slot * (T.KSp + 1);
-                    int nS = est[Ssel + 1] - est[Ssel];
+                    int nS = Ssel >= 0 ? est[Ssel + 1] - est[Ssel] : 0;
                     if (nS > 0) {
                         int jj = min((int)(R.u(10) * (float)nS), nS - 1);
                         int k = B.eitems[so + est[Ssel] + jj];
-                        float Q = (T.gP[(size_t)Tl * T.KSp + Ssel] / B.ZP[(size_t)slot * T.KT + Tl]) / (float)nS;
+                        float Q = QS / (float)nS;
                         sig = sig_upd(sig, (uint32_t)k);
                         n_proxy++;
                         int fixed = B.ent_idx[so + k];
@@ -437,6 +447,16 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
                                 }
                                 if (P.film != 2) L = L + c * w;
                                 n_proxy_ok++;
+                                if (P.smpp.raw) {   // a training sample of the proxy network
+                                    unsigned int idx = atomicAdd(P.smpp.count, 1u);
+                                    if (idx < (unsigned int)P.smpp.cap) {
+                                        mlp_raw(S, z, we, P.smpp.raw + (size_t)MLP_NRAW * idx);
+                                        P.smpp.T[idx] = Tl;
+                                        P.smpp.S[idx] = Ssel;
+                                        // the estimate R is signed; the proposal's training target is not
+                                        P.smpp.w[idx] = fmaxf(lum(c), 0.0f);
+                                    }
+                                }
                                 if (P.acc.proxy) {
                                     atomicAdd(&P.acc.tile_all[tile], lum(c) * w);
                                     atomicAdd(&P.acc.tile_proxy[tile], lum(c) * w);
@@ -523,6 +543,10 @@ __global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P
     Hit h = closest_hit<COUNT>(S, S.cpos, d, -1, &tc);
     int a = 1;
     bool conn = P.conn && B.npool[slot] > 0;
+    // a row of the proxy network at the first non-specular vertex where the eye
+    // pass draws a proxy (the tile's coin, camera dimension 8)
+    bool proxy_row = P.mlpp.rows && P.proxy && B.nent[slot] > 0;
+    const float pi_pix = T.pi[(py / T.tile) * T.gw + (px / T.tile)];
     while (true) {
         P.mlp.hits[((size_t)slot * P.max_depth + (a - 1)) * P.npix + pix] =
             make_int4(h.tri, __float_as_int(h.t), __float_as_int(h.b1), __float_as_int(h.b2));
@@ -531,6 +555,25 @@ __global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P
         const DMat &mz = S.mats[z.mat];
         float3 we = -d;
         if (absorbing(S, z, we)) break;
+        if (proxy_row && !mz.specular) {
+            proxy_row = false;   // only the first non-specular vertex
+            Rng Rc;
+            Rc.init(P.seed, K_CAMERA, it, (uint32_t)pix, (uint32_t)a);
+            if (pi_pix > 0.0f && a + 2 <= P.max_depth && Rc.u(8) < pi_pix) {
+                int Tl = label_dir(S, z, we, T.KT, T.cT);
+                cg::coalesced_group g = cg::coalesced_threads();
+                unsigned int base = 0;
+                if (g.thread_rank() == 0) base = atomicAdd(P.mlpp.count, (unsigned int)g.size());
+                unsigned int idx = g.shfl(base, 0) + g.thread_rank();
+                if (idx < (unsigned int)P.mlpp.cap) {
+                    float raw[MLP_NRAW];
+                    mlp_raw(S, z, we, raw);
+                    mlp_pack_row(raw, Tl, P.mlpp.emb, P.mlpp.rows + (size_t)MLP_NX * idx);
+                    P.mlpp.rowT[idx] = Tl;
+                    P.mlpp.rowPos[idx] = (int32_t)(((size_t)slot * P.mlpp.A + (a - 1)) * P.npix + pix);
+                }
+            }
+        }
         if (conn && P.mlp.rows && !mz.specular && a + 2 <= P.max_depth) {
             int Tl = label_dir(S, z, we, T.KT, T.cT);
             cg::coalesced_group g = cg::coalesced_threads();

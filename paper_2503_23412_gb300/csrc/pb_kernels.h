@@ -59,7 +59,7 @@ struct WfResult {
     float b1, b2;
 };
 constexpr int WF_MAXQ = 5;   // at most u = 4 closest hits and one occlusion per node
-constexpr int WF_ROUNDS = 24;   // wavefront rounds launched per wave (idle rounds exit at once)
+constexpr int WF_ROUNDS = 40;   // wavefront rounds launched per wave (idle rounds exit at once)
 
 struct WfBufs {
     int32_t *ch_w, *ch_off, *ch_win;   // per chain: nodes this round, first node, window size
@@ -110,7 +110,10 @@ struct KParams {
     uint32_t split;             // first pre-order estimator node without splitting (split limit)
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
+    MlpRows mlpp;           // the proxy strategy's network: rows at the proxy's vertex, its S' selections
     SampleSink smp;         // raw != nullptr: record proposal training samples
+    SampleSink smpp;        // raw != nullptr: record the proxy network's training samples
+    int proposal;           // 0 table rows; 1 learned connection; 2 learned connection and proxy
     EyeQueries q;           // the eye pass's occlusion queries and answers (vis == nullptr: traced inline)
     const uint32_t *iter_dev;   // non-null (graph replay): iteration numbers are *iter_dev + the launch's base
 };

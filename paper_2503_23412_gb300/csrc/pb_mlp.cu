@@ -166,6 +166,7 @@ struct SelArgs {
     const float *cdfC;       // slots x KT x K
     int32_t *sel;
     float *selq;
+    int udim;                // camera dimension of the selection uniform (6 connection, 9 proxy)
     // logits mode
     float *logits;           // nrows x K
     int *err;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
                 Rng R;
                 const uint32_t ib = a.iter_dev ? a.iter_base + *a.iter_dev : a.iter_base;
                 R.init(a.seed, K_CAMERA, ib + (uint32_t)slot, (uint32_t)pix, (uint32_t)av);
-                const float u = R.u(6);
+                const float u = R.u(a.udim);
                 if (u < MLP_EPS) gpick = select_cdf_row(a.cdfC + ((size_t)slot * a.KT + T) * a.K, a.K, u / MLP_EPS);
                 else target = (u - MLP_EPS) / (1.0f - MLP_EPS) * Zg;
             }
@@ -710,16 +711,30 @@ static cudaError_t grow(T **p, size_t &cap, size_t n) {
 static pb_status mlp_check(pb_ctx *ctx) {
     if (!ctx->has_tables) return pb_fail(ctx, PB_ERR_STATE, "mlp: no tables uploaded");
     if (ctx->T.KS > MLP_KMAX) return pb_fail(ctx, PB_ERR_ARG, "mlp: more than 384 light subspaces");
+    if (ctx->T.KSp > MLP_KMAX) return pb_fail(ctx, PB_ERR_ARG, "mlp: more than 384 specular subspaces");
     return PB_OK;
 }
 
-// (re)shape the network for the current tables
-static pb_status mlp_shape(pb_ctx *ctx) {
-    MlpState &M = ctx->mlp;
-    int K = ctx->T.KS, KT = ctx->T.KT;
+static void free_state(MlpState &M) {
+    void *ps[] = {M.w, M.g, M.m1, M.m2, M.img, M.bias, M.emb, M.err, M.rows, M.rowT, M.rowPos, M.hits, M.rcount,
+                  M.sel, M.selq, M.s_raw,
+                  M.s_T, M.s_S, M.s_w, M.s_count, M.b_X, M.b_T, M.b_S, M.b_a, M.b_H1, M.b_H2, M.b_DH1, M.b_DH2,
+                  M.b_DZ, M.b_DE, M.b_loss};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    M = MlpState{};
+}
+
+// the network of the connection (K = KS) or of the proxy strategy (K = KSp)
+static MlpState &net(pb_ctx *ctx, bool proxy) { return proxy ? ctx->mlp_p : ctx->mlp; }
+
+// (re)shape a network for the current tables
+static pb_status mlp_shape(pb_ctx *ctx, bool proxy = false) {
+    MlpState &M = net(ctx, proxy);
+    int K = proxy ? ctx->T.KSp : ctx->T.KS, KT = ctx->T.KT;
     if (M.K == K && M.KT == KT && M.w) return PB_OK;
     free_graphs(ctx);
-    mlp_free(ctx);
+    free_state(M);
     M.K = K;
     M.KT = KT;
     M.Kpad = mlp_kpad(K);
@@ -741,18 +756,12 @@ static pb_status mlp_shape(pb_ctx *ctx) {
 }
 
 void mlp_free(pb_ctx *ctx) {
-    MlpState &M = ctx->mlp;
-    void *ps[] = {M.w, M.g, M.m1, M.m2, M.img, M.bias, M.emb, M.err, M.rows, M.rowT, M.rowPos, M.hits, M.rcount,
-                  M.sel, M.selq, M.s_raw,
-                  M.s_T, M.s_S, M.s_w, M.s_count, M.b_X, M.b_T, M.b_S, M.b_a, M.b_H1, M.b_H2, M.b_DH1, M.b_DH2,
-                  M.b_DZ, M.b_DE, M.b_loss};
-    for (void *p : ps)
-        if (p) cudaFree(p);
-    M = MlpState{};
+    free_state(ctx->mlp);
+    free_state(ctx->mlp_p);
 }
 
-static pb_status mlp_pack(pb_ctx *ctx) {
-    MlpState &M = ctx->mlp;
+static pb_status mlp_pack(pb_ctx *ctx, bool proxy = false) {
+    MlpState &M = net(ctx, proxy);
     int n = MLP_H * MLP_NX + MLP_H * MLP_H + M.Kpad * MLP_H + MLP_H + M.Kpad + 4 * M.KT;
     k_mlp_pack<<<(n + 255) / 256, 256, 0, ctx->stream>>>(M.w, M.K, M.KT, M.img, M.bias, M.emb);
     CK(cudaGetLastError());
@@ -787,8 +796,8 @@ static pb_status run_select(pb_ctx *ctx, SelArgs &a, bool device_count) {
     return PB_OK;
 }
 
-static SelArgs sel_base(pb_ctx *ctx) {
-    MlpState &M = ctx->mlp;
+static SelArgs sel_base(pb_ctx *ctx, bool proxy = false) {
+    MlpState &M = net(ctx, proxy);
     SelArgs a{};
     a.img = M.img;
     a.bias = M.bias;
@@ -796,32 +805,40 @@ static SelArgs sel_base(pb_ctx *ctx) {
     a.Kpad = M.Kpad;
     a.KT = M.KT;
     a.err = M.err;
+    a.udim = 6;
     return a;
 }
 
-// rows, hits and selections of `slots` iterations of the eye pass
-pb_status mlp_ensure_rows(pb_ctx *ctx, int slots, int A, int depth) {
-    MlpState &M = ctx->mlp;
+// rows, hits and selections of `slots` iterations of the eye pass (the
+// proxy network's rows and selections use the same dense layout; it stores
+// no hits)
+pb_status mlp_ensure_rows(pb_ctx *ctx, int slots, int A, int depth, bool proxy) {
+    MlpState &M = net(ctx, proxy);
     size_t npix = (size_t)ctx->S.W * ctx->S.H;
     size_t n = (size_t)slots * A * npix;
-    if (M.cap_rowT < n || M.cap_hits < (size_t)slots * depth * npix) free_graphs(ctx);
+    size_t nh = proxy ? 0 : (size_t)slots * depth * npix;
+    if (M.cap_rowT < n || M.cap_hits < nh) free_graphs(ctx);
     CK(grow(&M.rows, M.cap_rows16, MLP_NX * n));
     CK(grow(&M.rowT, M.cap_rowT, n));
     CK(grow(&M.rowPos, M.cap_rowPos, n));
     CK(grow(&M.sel, M.cap_sel, n));
     CK(grow(&M.selq, M.cap_selq, n));
-    CK(grow(&M.hits, M.cap_hits, (size_t)slots * depth * npix));
+    if (!proxy) CK(grow(&M.hits, M.cap_hits, nh));
     if (!M.rcount) CK(cudaMalloc(&M.rcount, sizeof(unsigned int)));
     return PB_OK;
 }
 
 // everything a wave of the learned proposal allocates or configures, done
-// before a render is enqueued (and possibly captured)
-pb_status mlp_prepare(pb_ctx *ctx, int slots, int depth) {
+// before a render is enqueued (and possibly captured); proposal 2 also the
+// proxy strategy's network
+pb_status mlp_prepare(pb_ctx *ctx, int slots, int depth, int proposal) {
     if (!ctx->mlp.ready) return pb_fail(ctx, PB_ERR_STATE, "learned proposal requested but no network is loaded");
+    if (proposal == 2 && !ctx->mlp_p.ready)
+        return pb_fail(ctx, PB_ERR_STATE, "learned proxy proposal requested but no proxy network is loaded");
     if (depth - 2 < 1) return PB_OK;
-    pb_status s = mlp_ensure_rows(ctx, slots, depth - 2, depth);
+    pb_status s = mlp_ensure_rows(ctx, slots, depth - 2, depth, false);
     if (s != PB_OK) return s;
+    if (proposal == 2 && (s = mlp_ensure_rows(ctx, slots, depth - 2, depth, true)) != PB_OK) return s;
     return set_select_attr(ctx);
 }
 
@@ -830,13 +847,21 @@ pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base, const
     MlpState &M = ctx->mlp;
     if (!M.ready) return pb_fail(ctx, PB_ERR_STATE, "learned proposal requested but no network is loaded");
     if (slots > MAX_SLOTS) return pb_fail(ctx, PB_ERR_ARG, "mlp: too many iterations in flight");
+    const bool prox = P.proposal == 2;
+    MlpState &MP = ctx->mlp_p;
+    if (prox && !MP.ready) return pb_fail(ctx, PB_ERR_STATE, "learned proxy proposal requested but no proxy network");
     int A = P.max_depth - 2;
     if (A < 1) return PB_OK;
-    pb_status s = mlp_ensure_rows(ctx, slots, A, P.max_depth);
+    pb_status s = mlp_ensure_rows(ctx, slots, A, P.max_depth, false);
     if (s != PB_OK) return s;
+    if (prox && (s = mlp_ensure_rows(ctx, slots, A, P.max_depth, true)) != PB_OK) return s;
     size_t n = (size_t)slots * A * P.npix;
     CK(cudaMemsetAsync(M.rcount, 0, sizeof(unsigned int), ctx->stream));
     P.mlp = MlpRows{M.rows, M.rowT, M.rowPos, M.rcount, (int)n, M.hits, nullptr, nullptr, M.emb, A};
+    if (prox) {
+        CK(cudaMemsetAsync(MP.rcount, 0, sizeof(unsigned int), ctx->stream));
+        P.mlpp = MlpRows{MP.rows, MP.rowT, MP.rowPos, MP.rcount, (int)n, nullptr, nullptr, nullptr, MP.emb, A};
+    }
     launch_eye_feat(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->stream);
     CK(cudaGetLastError());
     if (ev && ev->feat_end) CK(cudaEventRecordWithFlags(ev->feat_end, ctx->stream, ev->flags));
@@ -863,24 +888,55 @@ pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base, const
     P.mlp.rows = nullptr;
     P.mlp.sel = M.sel;
     P.mlp.selq = M.selq;
-    return PB_OK;
-}
-
-pb_status mlp_check_err(pb_ctx *ctx) {
-    MlpState &M = ctx->mlp;
-    if (!M.err) return PB_OK;
-    int e = 0;
-    CK(cudaMemcpyAsync(&e, M.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    if (e) {
-        CK(cudaMemsetAsync(M.err, 0, sizeof(int), ctx->stream));
-        return pb_fail(ctx, PB_ERR_TIMEOUT, "mlp: tensor-core wait timed out");
+    if (prox) {
+        // the proxy strategy's specular subspace S' of each proxy row: the same
+        // kernel with the proxy network, Gamma' as the defensive part, the
+        // occupancy of the incomplete sub-paths and camera dimension 9
+        SelArgs b = sel_base(ctx, true);
+        b.rows = MP.rows;
+        b.rowT = MP.rowT;
+        b.rowPos = MP.rowPos;
+        b.count = MP.rcount;
+        b.nrows = (long long)n;
+        b.A = A;
+        b.npix = P.npix;
+        b.slots = slots;
+        b.seed = P.seed;
+        b.iter_base = iter_base;
+        b.iter_dev = P.iter_dev;
+        b.bstart = ctx->B.estart;
+        b.gC = ctx->T.gP;
+        b.ZC = ctx->B.ZP;
+        b.cdfC = ctx->B.cdfP;
+        b.sel = MP.sel;
+        b.selq = MP.selq;
+        b.udim = 9;
+        s = run_select(ctx, b, true);
+        if (s != PB_OK) return s;
+        P.mlpp.rows = nullptr;
+        P.mlpp.sel = MP.sel;
+        P.mlpp.selq = MP.selq;
     }
     return PB_OK;
 }
 
-static pb_status ensure_batch(pb_ctx *ctx, int n) {
-    MlpState &M = ctx->mlp;
+pb_status mlp_check_err(pb_ctx *ctx) {
+    for (MlpState *Mp : {&ctx->mlp, &ctx->mlp_p}) {
+        MlpState &M = *Mp;
+        if (!M.err) continue;
+        int e = 0;
+        CK(cudaMemcpyAsync(&e, M.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (e) {
+            CK(cudaMemsetAsync(M.err, 0, sizeof(int), ctx->stream));
+            return pb_fail(ctx, PB_ERR_TIMEOUT, "mlp: tensor-core wait timed out");
+        }
+    }
+    return PB_OK;
+}
+
+static pb_status ensure_batch(pb_ctx *ctx, int n, bool proxy = false) {
+    MlpState &M = net(ctx, proxy);
     if (M.b_cap >= n) return PB_OK;
     void *ps[] = {M.b_X, M.b_T, M.b_S, M.b_a, M.b_H1, M.b_H2, M.b_DH1, M.b_DH2, M.b_DZ, M.b_DE, M.b_loss};
     for (void *p : ps)
@@ -905,8 +961,8 @@ static Batch batch_view(MlpState &M, int n) {
 }
 
 // gradient of the batch loss into M.g (flat layout)
-static pb_status batch_grad(pb_ctx *ctx, int n) {
-    MlpState &M = ctx->mlp;
+static pb_status batch_grad(pb_ctx *ctx, int n, bool proxy = false) {
+    MlpState &M = net(ctx, proxy);
     Batch b = batch_view(M, n);
     cudaStream_t st = ctx->stream;
     int nb = (n + 127) / 128;
@@ -924,8 +980,8 @@ static pb_status batch_grad(pb_ctx *ctx, int n) {
     return PB_OK;
 }
 
-static pb_status adam_step(pb_ctx *ctx, float lr) {
-    MlpState &M = ctx->mlp;
+static pb_status adam_step(pb_ctx *ctx, float lr, bool proxy = false) {
+    MlpState &M = net(ctx, proxy);
     M.step++;
     const float b1 = 0.9f, b2 = 0.999f;
     float c1 = (float)(1.0 - std::pow((double)b1, M.step)), c2 = (float)(1.0 - std::pow((double)b2, M.step));
@@ -964,8 +1020,8 @@ static pb_status upload_batch(pb_ctx *ctx, int n, const float *raw, const int32_
     return PB_OK;
 }
 
-static float batch_loss(pb_ctx *ctx, int n) {
-    MlpState &M = ctx->mlp;
+static float batch_loss(pb_ctx *ctx, int n, bool proxy = false) {
+    MlpState &M = net(ctx, proxy);
     int nb = (n + 127) / 128;
     std::vector<float> h(nb);
     if (cudaMemcpyAsync(h.data(), M.b_loss, 4 * (size_t)nb, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
@@ -1008,6 +1064,32 @@ pb_status pb_mlp_upload(pb_ctx *ctx, const float *w, size_t n) {
     CK(cudaMemsetAsync(ctx->mlp.m2, 0, 4 * n, ctx->stream));
     ctx->mlp.step = 0;
     if ((s = mlp_pack(ctx)) != PB_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PB_OK;
+}
+
+pb_status pb_mlp_proxy_upload(pb_ctx *ctx, const float *w, size_t n) {
+    if (!ctx) return PB_ERR_ARG;
+    pb_status s = mlp_check(ctx);
+    if (s != PB_OK) return s;
+    if ((s = mlp_shape(ctx, true)) != PB_OK) return s;
+    MlpState &M = ctx->mlp_p;
+    if (!w || n != M.np) return pb_fail(ctx, PB_ERR_ARG, "mlp: proxy weight count differs from pb_mlp_nparams(KSp, KT)");
+    CK(cudaMemcpyAsync(M.w, w, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(M.m1, 0, 4 * n, ctx->stream));
+    CK(cudaMemsetAsync(M.m2, 0, 4 * n, ctx->stream));
+    M.step = 0;
+    if ((s = mlp_pack(ctx, true)) != PB_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PB_OK;
+}
+
+pb_status pb_mlp_proxy_readback(pb_ctx *ctx, float *w, size_t n) {
+    if (!ctx) return PB_ERR_ARG;
+    MlpState &M = ctx->mlp_p;
+    if (!M.w) return pb_fail(ctx, PB_ERR_STATE, "mlp: no proxy network");
+    if (!w || n != M.np) return pb_fail(ctx, PB_ERR_ARG, "mlp: proxy weight count differs from pb_mlp_nparams(KSp, KT)");
+    CK(cudaMemcpyAsync(w, M.w, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return PB_OK;
 }
@@ -1093,74 +1175,88 @@ pb_status pb_train_proposal(pb_ctx *ctx, const pb_config *cfg, const pb_train_de
     if ((s = mlp_check(ctx)) != PB_OK) return s;
     if (!td || td->samples < 1 || td->rounds < 1 || td->steps < 0 || td->batch < 1)
         return pb_fail(ctx, PB_ERR_ARG, "train: samples, rounds and batch must be positive");
-    if ((s = mlp_shape(ctx)) != PB_OK) return s;
+    const bool prox = td->proxy != 0;
+    for (int h = 0; h < (prox ? 2 : 1); ++h) {
+        if ((s = mlp_shape(ctx, h == 1)) != PB_OK) return s;
+        MlpState &Mh = net(ctx, h == 1);
+        if (!Mh.ready || td->reinit) {
+            std::vector<float> w(Mh.np);
+            init_weights(w, Mh.K, Mh.KT, td->seed + 977u * (uint32_t)h);
+            CK(cudaMemcpyAsync(Mh.w, w.data(), 4 * Mh.np, cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemsetAsync(Mh.m1, 0, 4 * Mh.np, ctx->stream));
+            CK(cudaMemsetAsync(Mh.m2, 0, 4 * Mh.np, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            Mh.step = 0;
+            if ((s = mlp_pack(ctx, h == 1)) != PB_OK) return s;
+        }
+        // sample buffer
+        size_t cap = (size_t)td->samples;
+        if (Mh.s_cap < cap) {
+            void *ps[] = {Mh.s_raw, Mh.s_T, Mh.s_S, Mh.s_w};
+            for (void *p : ps)
+                if (p) cudaFree(p);
+            CK(cudaMalloc(&Mh.s_raw, 4 * cap * MLP_NRAW));
+            CK(cudaMalloc(&Mh.s_T, 4 * cap));
+            CK(cudaMalloc(&Mh.s_S, 4 * cap));
+            CK(cudaMalloc(&Mh.s_w, 4 * cap));
+            Mh.s_cap = cap;
+        }
+        if (!Mh.s_count) CK(cudaMalloc(&Mh.s_count, sizeof(unsigned int)));
+        if ((s = ensure_batch(ctx, td->batch, h == 1)) != PB_OK) return s;
+    }
     MlpState &M = ctx->mlp;
-    if (!M.ready || td->reinit) {
-        std::vector<float> w(M.np);
-        init_weights(w, M.K, M.KT, td->seed);
-        CK(cudaMemcpyAsync(M.w, w.data(), 4 * M.np, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemsetAsync(M.m1, 0, 4 * M.np, ctx->stream));
-        CK(cudaMemsetAsync(M.m2, 0, 4 * M.np, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-        M.step = 0;
-        if ((s = mlp_pack(ctx)) != PB_OK) return s;
-    }
-    // sample buffer
-    size_t cap = (size_t)td->samples;
-    if (M.s_cap < cap) {
-        void *ps[] = {M.s_raw, M.s_T, M.s_S, M.s_w};
-        for (void *p : ps)
-            if (p) cudaFree(p);
-        CK(cudaMalloc(&M.s_raw, 4 * cap * MLP_NRAW));
-        CK(cudaMalloc(&M.s_T, 4 * cap));
-        CK(cudaMalloc(&M.s_S, 4 * cap));
-        CK(cudaMalloc(&M.s_w, 4 * cap));
-        M.s_cap = cap;
-    }
-    if (!M.s_count) CK(cudaMalloc(&M.s_count, sizeof(unsigned int)));
-    if ((s = ensure_batch(ctx, td->batch)) != PB_OK) return s;
+    const size_t cap = (size_t)td->samples;
     pb_config c = *cfg;
     c.proposal = 0;
-    int64_t iters = 0, nsamp_total = 0;
-    double loss_first = NAN, loss_last = NAN;
+    int64_t iters = 0, nsamp_total = 0, nsamp_proxy = 0;
+    double loss_first = NAN, loss_last = NAN, lp_first = NAN, lp_last = NAN;
     uint32_t it = (uint32_t)td->iter0;
     for (int r = 0; r < td->rounds; ++r) {
         // collect: render iterations (not accumulated) with the current proposal
-        c.proposal = (r == 0 && !td->learned_first) ? 0 : 1;
+        c.proposal = (r == 0 && !td->learned_first) ? 0 : (prox ? 2 : 1);
         CK(cudaMemsetAsync(M.s_count, 0, sizeof(unsigned int), ctx->stream));
-        unsigned int cnt = 0;
+        if (prox) CK(cudaMemsetAsync(ctx->mlp_p.s_count, 0, sizeof(unsigned int), ctx->stream));
+        unsigned int cnt = 0, cntp = 0;
         int max_it = td->max_iters_per_round > 0 ? td->max_iters_per_round : 256;
         int done = 0;
         while (done < max_it) {
             int wave = std::min(td->iters_per_wave > 0 ? td->iters_per_wave : 8, max_it - done);
             SampleSink sink{M.s_raw, M.s_T, M.s_S, M.s_w, M.s_count, (int)cap};
-            if ((s = pb_collect_wave(ctx, &c, wave, it, sink)) != PB_OK) return s;
+            MlpState &MP = ctx->mlp_p;
+            SampleSink sinkp{};
+            if (prox) sinkp = SampleSink{MP.s_raw, MP.s_T, MP.s_S, MP.s_w, MP.s_count, (int)cap};
+            if ((s = pb_collect_wave(ctx, &c, wave, it, sink, sinkp)) != PB_OK) return s;
             it += (uint32_t)wave;
             done += wave;
             iters += wave;
             CK(cudaMemcpyAsync(&cnt, M.s_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+            if (prox) CK(cudaMemcpyAsync(&cntp, MP.s_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
             CK(cudaStreamSynchronize(ctx->stream));
             if (cnt >= cap) break;
         }
-        int nsrc = (int)std::min<size_t>(cnt, cap);
-        nsamp_total += nsrc;
-        if (nsrc == 0) continue;
-        // train
-        for (int k = 0; k < td->steps; ++k) {
-            Batch b = batch_view(M, td->batch);
-            k_tr_gather<<<(td->batch + 127) / 128, 128, 0, ctx->stream>>>(td->batch, nsrc, M.s_raw, M.s_T, M.s_S,
-                                                                          M.s_w, td->seed, (uint32_t)M.step, M.w,
-                                                                          M.K, b);
-            CK(cudaGetLastError());
-            if ((s = batch_grad(ctx, td->batch)) != PB_OK) return s;
-            if (k == 0 || k == td->steps - 1) {
-                float l = batch_loss(ctx, td->batch);
-                if (r == 0 && k == 0) loss_first = l;
-                loss_last = l;
+        // train each network on its own samples
+        for (int h = 0; h < (prox ? 2 : 1); ++h) {
+            MlpState &Mh = net(ctx, h == 1);
+            int nsrc = (int)std::min<size_t>(h ? cntp : cnt, cap);
+            (h ? nsamp_proxy : nsamp_total) += nsrc;
+            if (nsrc == 0) continue;
+            for (int k = 0; k < td->steps; ++k) {
+                Batch b = batch_view(Mh, td->batch);
+                k_tr_gather<<<(td->batch + 127) / 128, 128, 0, ctx->stream>>>(
+                    td->batch, nsrc, Mh.s_raw, Mh.s_T, Mh.s_S, Mh.s_w, td->seed + 977u * (uint32_t)h,
+                    (uint32_t)Mh.step, Mh.w, Mh.K, b);
+                CK(cudaGetLastError());
+                if ((s = batch_grad(ctx, td->batch, h == 1)) != PB_OK) return s;
+                if (k == 0 || k == td->steps - 1) {
+                    float l = batch_loss(ctx, td->batch, h == 1);
+                    double &lf = h ? lp_first : loss_first;
+                    if (std::isnan(lf)) lf = l;
+                    (h ? lp_last : loss_last) = l;
+                }
+                if ((s = adam_step(ctx, td->lr > 0.0f ? td->lr : 1e-3f, h == 1)) != PB_OK) return s;
             }
-            if ((s = adam_step(ctx, td->lr > 0.0f ? td->lr : 1e-3f)) != PB_OK) return s;
+            if ((s = mlp_pack(ctx, h == 1)) != PB_OK) return s;
         }
-        if ((s = mlp_pack(ctx)) != PB_OK) return s;
     }
     CK(cudaStreamSynchronize(ctx->stream));
     if (out) {
@@ -1169,6 +1265,9 @@ pb_status pb_train_proposal(pb_ctx *ctx, const pb_config *cfg, const pb_train_de
         out->steps = M.step;
         out->loss_first = loss_first;
         out->loss_last = loss_last;
+        out->samples_proxy = nsamp_proxy;
+        out->loss_proxy_first = lp_first;
+        out->loss_proxy_last = lp_last;
     }
     return PB_OK;
 }

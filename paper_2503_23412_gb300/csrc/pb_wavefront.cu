@@ -734,6 +734,11 @@ __global__ void __launch_bounds__(128) k_wf_walk_booth(KParams P, Pool B, WfBufs
             const int last = stopm ? __ffs(stopm) - 1 : cnt - 1;
             double t = (in && lane <= last) ? pr / (surv * before) * (double)invB : 0.0;
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+            if (!isfinite(t)) {   // the weight left the double range: report the chain as truncated
+                done = 1;
+                trunc = 1;
+                break;
+            }
             sum_t += t;
             next += last + 1;
             prod = __shfl_sync(FULL, pr, last);
@@ -787,7 +792,12 @@ __global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t
             float ratio = entry_ratio<false>(S, E, R, nullptr);
             float gj = 1.0f - ratio * invB;
             st.prod *= (double)gj;
-            st.sum_t += st.prod / st.surv * (double)invB;
+            const double tb = st.prod / st.surv * (double)invB;
+            if (!isfinite(tb)) {   // the weight left the double range: report the chain as truncated
+                done = trunc = 1;
+                break;
+            }
+            st.sum_t += tb;
             st.next += 1;
             const double rho = fmin(1.0, (double)P.booth * fabs(st.prod));
             if (!((double)R.u(18) < rho)) done = 1;

@@ -63,12 +63,13 @@ class pb_stats(C.Structure):
 class pb_train_desc(C.Structure):
     _fields_ = [("samples", C.c_int), ("rounds", C.c_int), ("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_float),
                 ("seed", C.c_uint32), ("iter0", C.c_int), ("max_iters_per_round", C.c_int),
-                ("iters_per_wave", C.c_int), ("reinit", C.c_int), ("learned_first", C.c_int)]
+                ("iters_per_wave", C.c_int), ("reinit", C.c_int), ("learned_first", C.c_int), ("proxy", C.c_int)]
 
 
 class pb_train_stats(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("samples", C.c_int64), ("steps", C.c_int64), ("loss_first", C.c_double),
-                ("loss_last", C.c_double)]
+                ("loss_last", C.c_double), ("samples_proxy", C.c_int64), ("loss_proxy_first", C.c_double),
+                ("loss_proxy_last", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,7 +95,8 @@ EXPORTS = ["pb_create", "pb_destroy", "pb_last_error", "pb_scene_upload", "pb_ta
            "pb_iteration", "pb_prepare", "pb_tables_readback", "pb_recip_estimates_noalloc", "pb_mlp_nparams",
            "pb_mlp_upload", "pb_mlp_readback", "pb_mlp_logits", "pb_mlp_grad", "pb_mlp_train_batch",
            "pb_train_proposal", "pb_connection_moments", "pb_render_batch", "pb_autotune", "pb_autotune_cache_save",
-           "pb_autotune_cache_load", "pb_autotune_cache_clear", "pb_read_bandwidth"]
+           "pb_autotune_cache_load", "pb_autotune_cache_clear", "pb_read_bandwidth", "pb_mlp_proxy_upload",
+           "pb_mlp_proxy_readback"]
 
 
 def lib(path=LIB):
@@ -127,6 +129,8 @@ def lib(path=LIB):
                                              C.POINTER(i32)]
     L.pb_mlp_upload.argtypes = [vp, vp, C.c_size_t]
     L.pb_mlp_readback.argtypes = [vp, vp, C.c_size_t]
+    L.pb_mlp_proxy_upload.argtypes = [vp, vp, C.c_size_t]
+    L.pb_mlp_proxy_readback.argtypes = [vp, vp, C.c_size_t]
     L.pb_mlp_logits.argtypes = [vp, i32, vp, vp, vp]
     L.pb_mlp_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, C.POINTER(C.c_float)]
     L.pb_mlp_train_batch.argtypes = [vp, i32, vp, vp, vp, vp, C.c_float, C.POINTER(C.c_float)]
@@ -210,9 +214,10 @@ def read_bandwidth(device, nbytes, reps):
 
 
 def train_desc(samples=1 << 20, rounds=2, steps=400, batch=4096, lr=1e-3, seed=1, iter0=1 << 23, max_iters_per_round=0,
-               iters_per_wave=0, reinit=0, learned_first=0):
+               iters_per_wave=0, reinit=0, learned_first=0, proxy=0):
+    """proxy = 1 also trains the proxy strategy's network (render with proposal = 2)."""
     return pb_train_desc(samples, rounds, steps, batch, lr, seed, iter0, max_iters_per_round, iters_per_wave, reinit,
-                         learned_first)
+                         learned_first, proxy)
 
 
 def tables_desc(t, W, H):
@@ -376,6 +381,20 @@ class Renderer:
     def mlp_upload(self, w):
         w = np.ascontiguousarray(w, np.float32)
         self._check(self.L.pb_mlp_upload(self.h, _p(w), w.size))
+
+    def mlp_proxy_nparams(self):
+        t = pb_tables_host()
+        self._check(self.L.pb_tables_readback(self.h, C.byref(t)))
+        return int(self.L.pb_mlp_nparams(t.KSp, t.KT))
+
+    def mlp_proxy_upload(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        self._check(self.L.pb_mlp_proxy_upload(self.h, _p(w), w.size))
+
+    def mlp_proxy_readback(self):
+        w = np.zeros(self.mlp_proxy_nparams(), np.float32)
+        self._check(self.L.pb_mlp_proxy_readback(self.h, _p(w), w.size))
+        return w
 
     def mlp_readback(self):
         w = np.zeros(self.mlp_nparams(), np.float32)

@@ -181,3 +181,45 @@ def test_trained_proposal_gains_over_table(N):
     print("connection second moment: table %.4g learned %.4g gain %.2f" % (m_tab["m2"], m_mlp["m2"], gain))
     assert gain > 1.5, (m_tab, m_mlp)
     r.close()
+
+
+def test_iteration_with_learned_proxy_proposal_matches_oracle(N):
+    """proposal = 2: the proxy strategy's specular subspace S' comes from its
+    own network (mixed with the row Gamma'[T, .]) as well. Eye passes match
+    the oracle's with the same two networks: >= 99.5 % of paths with the
+    same topology (a hidden unit may round to the neighbouring bf16 value and
+    flip a draw) and per-path radiance within 1e-4 where it agrees; the
+    proxies' choices differ from those of the table row."""
+    sc = scenes.cornell(24, 20)
+    o = O.Oracle(sc)
+    K, KT, KSp = 48, 16, 12
+    tab = scenes.random_tables(sc, KT=KT, KS=K, KSp=KSp, KC=2, seed=4)
+    p = O.params(M=800, M_p=400, max_depth=6)
+    tab = o.learn(p, tab, 1000, 2, n_bsamples=32)
+    w = _weights(K, KT, seed=11, out_scale=30.0)
+    wp = _weights(KSp, KT, seed=23, out_scale=30.0)
+    r = N.Renderer(sc, tab)
+    r.mlp_upload(w)
+    r.mlp_proxy_upload(wp)
+    np.testing.assert_array_equal(r.mlp_proxy_readback(), wp)
+    td1 = o.tables(dict(tab, mlp_w=w.astype(np.float64)))
+    td2 = o.tables(dict(tab, mlp_w=w.astype(np.float64), mlp_wp=wp.astype(np.float64)))
+    cfg = N.config(M=800, M_p=400, max_depth=6, proposal=2)
+    n_items = n_same = differs = proxies = 0
+    for it in (3, 4, 5):
+        tri, bary = o.light_pass(p, it)
+        ref = o.iteration(p, td2, it, tri, bary)
+        got = r.iteration(cfg, it, tri, bary, rhat=ref["rhat"])
+        same = ref["sig"] == got["sig"]
+        n_items += len(same)
+        n_same += int(same.sum())
+        a, b = ref["rgb"][same], got["rgb"][same]
+        mag = np.abs(a).max(1)
+        err = np.where(mag > 0, np.abs(a - b).max(1) / np.where(mag > 0, mag, 1.0), (np.abs(b).max(1) > 0) * 1.0)
+        assert err.max() <= REL, err.max()
+        one = o.iteration(p, td1, it, tri, bary, rhat=ref["rhat"])
+        differs += int((one["sig"] != ref["sig"]).sum())
+        proxies += ref["stats"]["n_proxy"]
+    assert n_same / n_items >= 0.995, n_same / n_items
+    assert proxies > 100 and differs > 0.05 * proxies   # the proxy network really changed the choices
+    r.close()

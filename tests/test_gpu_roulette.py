@@ -57,6 +57,8 @@ def test_booth_roulette_matches_oracle(N):
         es = ref["entry_sig"] == got["entry_sig"]
         n_ent += len(es)
         n_same += int(es.sum())
+        # a chain that reached the node cap (on either side) is a truncated estimate: no value to compare
+        es &= (ref["entry_nodes"] < (1 << 16)) & (got["entry_nodes"] < (1 << 16))
         # the same node count in every repeat where the signatures agree
         assert np.array_equal(ref["entry_nodes"][es], got["entry_nodes"][es])
         a = ref["rhat"][es]

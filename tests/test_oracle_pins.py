@@ -1022,9 +1022,11 @@ def test_furnace_with_glass_sphere_converges_to_closed_form():
 
 def test_proxy_on_off_and_path_tracing_agree_per_pixel():
     """Unbiasedness (Sec. 4.1, 5.2): with independent seeds, proxy on (with
-    the paper's RRS function or Booth's roulette), proxy off, and plain
-    PT+NEE give per-pixel means of a caustic scene that agree within their
-    standard errors (z-scores of an N(0,1) family)."""
+    the paper's RRS function or Booth's roulette, with cells left out of the
+    pool, or with learned proposals for both the connection's S and the
+    proxy's S'), proxy off, and plain PT+NEE give per-pixel means of a caustic
+    scene that agree within their standard errors (z-scores of an N(0,1)
+    family)."""
     sc = scenes.caustic_mini(8, 8)
     o = O.Oracle(sc)
     tab = scenes.random_tables(sc, KT=8, KS=8, KSp=4, KC=2)
@@ -1053,8 +1055,15 @@ def test_proxy_on_off_and_path_tracing_agree_per_pixel():
     gated["mis_tab"][0, :, 0] = 0.0
     td = o.tables(gated)
     m_ga, v_ga, k_ga = run(11, n, proxy=1)
-    assert k_on > 500 and k_bo > 500 and 0 < k_ga < k_on
-    for m, v in ((m_on, v_on), (m_off, v_off), (m_bo, v_bo), (m_ga, v_ga)):
+    # the learned proposals (random networks, sharp outputs) for the connection's S and the proxy's S'
+    wc = O.mlp_init(8, 8, seed=3)
+    wc[1024 + 4096 + 64:1024 + 4096 + 64 + 8 * 64] *= 30.0
+    wp = O.mlp_init(4, 8, seed=4)
+    wp[1024 + 4096 + 64:1024 + 4096 + 64 + 4 * 64] *= 30.0
+    td = o.tables(dict(tab, mlp_w=wc, mlp_wp=wp))
+    m_nn, v_nn, k_nn = run(12, n, proxy=1)
+    assert k_on > 500 and k_bo > 500 and 0 < k_ga < k_on and k_nn > 500
+    for m, v in ((m_on, v_on), (m_off, v_off), (m_bo, v_bo), (m_ga, v_ga), (m_nn, v_nn)):
         den = np.sqrt(v + v_pt)
         live = den > 0
         z = (m[live] - m_pt[live]) / den[live]
