@@ -166,6 +166,16 @@ typedef struct {
      * as a chain instead of reaching trial_cap. 0: 65536; negative: never
      * (the paper's rule throughout). */
     int split_cap;
+    /* Bound of the reciprocal estimator's nodes. 0: the raise rule -- a node
+     * that splits (|g| > 1, i.e. f/q > 2B) hands its children the bound
+     * B' = its own f/q, and its Taylor term becomes g / B'. The estimate stays
+     * unbiased for any bound fixed before a node's draw (1/beta = 1/B +
+     * (1 - beta/B) / beta for every B), chains whose draws stay below 2B are
+     * the paper's walk exactly, and a tree whose B sits far below the
+     * integrand's f/q (outside the convergence condition 0 < beta/B < 2)
+     * grows only as far as its own ratios instead of without end. 1: one B
+     * for the whole estimate (the paper's walk throughout). */
+    int fixed_bound;
 } pb_config;
 
 typedef struct {
@@ -341,7 +351,7 @@ pb_status pb_iteration(pb_ctx *ctx, const pb_config *cfg, int iteration, const i
  * estimator nodes over the repeats, may be NULL). *n_truncated (may be NULL)
  * counts entries with a repeat that hit trial_cap or its split stack. From
  * cfg only seed, repeats (1..8), trial_cap (> 0), side_in ([0, 1), 0 for an
- * even split) and split_cap are read; the roulette is always the paper's RRS
+ * even split), split_cap and fixed_bound are read; the roulette is always the paper's RRS
  * function.
  * An entry whose B is not positive (or NaN) gets a NaN estimate and the call
  * returns PB_ERR_ARG after writing the other entries' estimates. */

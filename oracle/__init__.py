@@ -60,7 +60,7 @@ class Params(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("max_depth", C.c_int), ("M", C.c_int), ("M_p", C.c_int),
                 ("repeats", C.c_int), ("proxy", C.c_int), ("trial_cap", C.c_int), ("conn", C.c_int),
                 ("pilot_min", C.c_int), ("pilot_max", C.c_int), ("side_in", C.c_double), ("booth", C.c_double),
-                ("film", C.c_int), ("split_cap", C.c_int)]
+                ("film", C.c_int), ("split_cap", C.c_int), ("fixed_bound", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -133,6 +133,8 @@ def lib():
                                 C.c_int, vp, C.POINTER(Stats)]
         L.or_set_split_default.argtypes = [C.c_int]
         L.or_set_split_default.restype = None
+        L.or_set_fixed_bound_default.argtypes = [C.c_int]
+        L.or_set_fixed_bound_default.restype = None
         L.or_learn.argtypes = [vp, C.POINTER(Params), C.POINTER(TablesDesc), C.c_int, C.c_int, C.c_int,
                                C.c_double, vp, vp, vp, vp, vp]
         _lib = L
@@ -294,16 +296,18 @@ SPLIT_CAP = 1 << 16   # default node index from which the estimator stops splitt
 
 
 def params(seed=7, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, trial_cap=1 << 16, conn=1, pilot_min=64,
-           pilot_max=1024, side_in=0.0, booth=0.0, film=0, split_cap=SPLIT_CAP):
+           pilot_max=1024, side_in=0.0, booth=0.0, film=0, split_cap=SPLIT_CAP, fixed_bound=0):
     """pilot_max = 0 turns the per-entry pilot off (B from the learned table);
     side_in = 0 is an even split of the cosine draws at dielectric vertices;
     booth > 0 estimates with Booth's Russian roulette of that scale;
     film = 1 keeps only the proxy strategy's weighted contributions in the
     pixel values, 2 all but those (the strategies and weights are unchanged);
     split_cap: from this pre-order node on, a node with |g| > 1 continues
-    with one child of weight g instead of splitting (<= 0: never)."""
+    with one child of weight g instead of splitting (<= 0: never);
+    fixed_bound = 1 keeps one B per estimate (the paper's walk), 0 lets a
+    node with f/q > 2B hand its children the bound f/q (the raise rule)."""
     return Params(seed, max_depth, M, M_p, repeats, proxy, trial_cap, conn, pilot_min, pilot_max, side_in, booth,
-                  film, split_cap)
+                  film, split_cap, fixed_bound)
 
 
 def philox(ctr, key):
@@ -379,6 +383,11 @@ def mlp_adam(w, g, m1, m2, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 def set_split_default(split):
     """split limit of recip_1d and Oracle.entry_recip (default 2^16; <= 0: never split-limited)"""
     lib().or_set_split_default(int(split))
+
+
+def set_fixed_bound_default(fixed):
+    """bound rule of recip_1d and Oracle.entry_recip (default 0: the raise rule; 1: one B per estimate)"""
+    lib().or_set_fixed_bound_default(int(fixed))
 
 
 def recip_1d(fn, B, n, seed=1, cap=1 << 20, booth=0.0):

@@ -11,6 +11,7 @@
  * Written out, the recursion is a sum over the nodes of the random tree:
  *   I~ = 1/B + sum_v (g_v / B) * prod_{a ancestor of v} sgn(g_a)
  *   I  =       sum_v (1 / B)   * prod_{a ancestor of v} sgn(g_a)   (Alg. I)
+ * (with B per node under the raise rule below).
  * visit() walks the tree in pre-order and adds each node's term. Node v
  * draws its variates from the counter-based stream with word c = its
  * pre-order index. A node cap bounds the work; reaching it truncates the
@@ -27,10 +28,12 @@
  * as the ablation reports). c > 0 selects this rule; c = 0 the paper's. */
 #include "or_internal.h"
 
-/* the split limit of the stand-alone estimator entry points (pins, tests) */
+/* the split limit and bound rule of the stand-alone estimator entry points (pins, tests) */
 static uint32_t or_split_default = 1u << 16;
+static int or_fixed_default = 0;
 
 void or_set_split_default(int split) { or_split_default = split > 0 ? (uint32_t)split : 0xFFFFFFFFu; }
+void or_set_fixed_bound_default(int fixed) { or_fixed_default = fixed != 0; }
 
 typedef struct {
     double (*ratio)(void *ctx, uint32_t node);    /* draw x ~ q, return f(x)/q(x) */
@@ -42,6 +45,7 @@ typedef struct {
     double sum_t, sum_i;
     double booth;       /* > 0: Booth's roulette with scale c (no splitting); 0: the paper's RRS */
     uint32_t split;     /* first pre-order node without splitting (see visit) */
+    int fixed;          /* 1: one B for the whole estimate (the paper's walk); 0: the raise rule */
 } rec_state;
 
 /* The split limit. Alg. I~ is unbiased for any number-of-children rule
@@ -53,18 +57,32 @@ typedef struct {
  * has exactly one child of weight g (r = 1), so a chain whose bound B sits
  * far below some f/q (a tree that would split without end) finishes as a
  * chain instead of hitting the node cap. Chains shorter than `split` are
- * unchanged. */
-static void visit(rec_state *st, double w_anc) {
+ * unchanged.
+ *
+ * The raise rule. The paper keeps one B for the whole estimate. Here a node
+ * that splits (|g| > 1, i.e. f/q > 2B) hands its children the bound
+ * B' = its own f/q. The estimate stays unbiased for any bound fixed before a
+ * node's draw, because 1/beta = 1/B + (1 - beta/B) (1/beta) holds for every
+ * B: a node with bound B, g = 1 - X/B and children that each estimate
+ * 1/beta has expectation 1/beta. Each child enters with its own term 1/B',
+ * so the node's Taylor term (the expected own term of its children) is
+ * g / B'; Alg. I's term stays 1/B, the node's own. A chain whose draws stay
+ * below 2B never raises its bound and is the paper's walk exactly; a tree
+ * whose B sits far below the integrand's typical f/q would split without
+ * end, and now grows only as far as its own ratios allow. */
+static void visit(rec_state *st, double w_anc, double B) {
     for (;;) {
         if (st->next >= st->cap) {
             st->truncated = 1;
             return;
         }
         uint32_t node = st->next++;
-        double g = 1.0 - st->ratio(st->ctx, node) / st->B;
-        st->sum_t += w_anc * g / st->B;
-        st->sum_i += w_anc / st->B;
+        double X = st->ratio(st->ctx, node);
+        double g = 1.0 - X / B;
         double r = fabs(g);
+        double Bc = (!st->fixed && r > 1.0) ? X : B;   /* the children's bound (the raise rule above) */
+        st->sum_t += w_anc * g / Bc;
+        st->sum_i += w_anc / B;
         int n;
         double child_w;
         if (r > 1.0 && node >= st->split) {
@@ -76,8 +94,13 @@ static void visit(rec_state *st, double w_anc) {
             child_w = w_anc * (g > 0.0 ? 1.0 : -1.0);
         }
         if (n == 0) return;
-        for (int i = 0; i < n - 1; ++i) visit(st, child_w);
+        if (!isfinite(child_w)) {   /* the weight left the double range: a truncated estimate */
+            st->truncated = 1;
+            return;
+        }
+        for (int i = 0; i < n - 1; ++i) visit(st, child_w, Bc);
         w_anc = child_w;   /* the last child continues in this loop */
+        B = Bc;
     }
 }
 
@@ -115,7 +138,7 @@ static double estimate(rec_state *st, double *I, double *nodes, int *trunc) {
     if (st->booth > 0.0)
         walk_booth(st);
     else
-        visit(st, 1.0);
+        visit(st, 1.0, st->B);
     *I = st->sum_i;
     *nodes = (double)st->next;
     *trunc = st->truncated;
@@ -166,7 +189,8 @@ int or_recip_1d(int fn, double B, int n_runs, uint32_t seed, int trial_cap, doub
 int or_recip_1d_booth(int fn, double B, double c, int n_runs, uint32_t seed, int trial_cap, double *out_t,
                       double *out_i, double *out_n) {
     one_d o = {fn, seed, 0};
-    rec_state st = {one_d_ratio, one_d_unif, &o, B, (uint32_t)trial_cap, 0, 0, 0, 0, c, or_split_default};
+    rec_state st = {one_d_ratio, one_d_unif, &o, B, (uint32_t)trial_cap, 0, 0, 0, 0, c, or_split_default,
+                    or_fixed_default};
     int ntr = 0;
     for (int r = 0; r < n_runs; ++r) {
         o.run = (uint32_t)r;
@@ -391,15 +415,15 @@ static void entry_setup(entry_ctx *e, const or_scene_t *s, const or_entry *en) {
  * roulette of scale `booth` when it is positive. Stream:
  * kind RECIP, a = iteration, b = entry*8 + repeat, c = node. */
 double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, double booth, uint32_t seed,
-                     uint32_t iteration, uint32_t entry, int repeats, int cap, int split, double *nodes,
-                     int *trunc, uint32_t *sig) {
+                     uint32_t iteration, uint32_t entry, int repeats, int cap, int split, int fixed,
+                     double *nodes, int *trunc, uint32_t *sig) {
     entry_ctx e;
     entry_setup(&e, s, en);
     e.seed = seed;
     e.kind = K_RECIP;
     e.a = iteration;
     rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)cap, 0, 0, 0, 0, booth,
-                    split > 0 ? (uint32_t)split : 0xFFFFFFFFu};
+                    split > 0 ? (uint32_t)split : 0xFFFFFFFFu, fixed != 0};
     double acc = 0.0, nn = 0.0;
     int tr = 0;
     uint32_t h = 2166136261u;
@@ -477,7 +501,8 @@ int or_entry_recip_booth(void *hs, const or_entry *en, double B, double c, int n
     entry_setup(&e, (const or_scene_t *)hs, en);
     e.seed = seed;
     e.kind = K_RECIP;
-    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)trial_cap, 0, 0, 0, 0, c, or_split_default};
+    rec_state st = {entry_ratio, entry_unif, &e, B, (uint32_t)trial_cap, 0, 0, 0, 0, c, or_split_default,
+                    or_fixed_default};
     int ntr = 0;
     for (int i = 0; i < n; ++i) {
         e.a = 0xFFFFu;

@@ -32,8 +32,8 @@
 
 double or_fwd_density(const or_scene_t *s, const or_vtx *ys, int j);
 double or_entry_rhat(const or_scene_t *s, const or_entry *en, double B, double booth, uint32_t seed,
-                     uint32_t iteration, uint32_t entry, int repeats, int cap, int split, double *nodes,
-                     int *trunc, uint32_t *sig);
+                     uint32_t iteration, uint32_t entry, int repeats, int cap, int split, int fixed,
+                     double *nodes, int *trunc, uint32_t *sig);
 double or_pilot_B(const or_scene_t *s, const or_entry *en, uint32_t seed, uint32_t iteration, uint32_t entry,
                   int min_draws, int max_draws);
 
@@ -265,8 +265,7 @@ static double entry_estimate(const or_scene_t *s, const or_params *p, const or_t
         if (Bp > 0.0) B = Bp;
     }
     return or_entry_rhat(s, &it->ent[k], B, p->booth, p->seed, iteration, (uint32_t)k, p->repeats, p->trial_cap,
-                         p->split_cap,
-                         nodes, trunc, sig);
+                         p->split_cap, p->fixed_bound, nodes, trunc, sig);
 }
 
 static void build_iter(const or_scene_t *s, const or_params *p, const or_tab *T, uint32_t iteration,

@@ -71,6 +71,8 @@ typedef struct {
                         * proxy strategy only, 2 all but the proxy strategy */
     int split_cap;     /* pre-order node index from which a node with |g| > 1 has one child of
                         * weight g instead of splitting (<= 0: never) */
+    int fixed_bound;   /* 1: one B per estimate (the paper's walk); 0: a node with f/q > 2B hands
+                        * its children the bound f/q (the raise rule) */
 } or_params;
 
 typedef struct {
@@ -184,6 +186,8 @@ void or_mlp_adam(int np, double *w, const double *g, double *m1, double *m2, int
 
 /* split limit of or_recip_1d*, or_entry_recip* (default 2^16; <= 0: never) */
 void or_set_split_default(int split);
+/* bound rule of the same entry points (default 0: the raise rule; 1: one B per estimate) */
+void or_set_fixed_bound_default(int fixed);
 
 /* Statistics / selection learning (Sec. 5.4-5.5 as read in the design notes).
  * Inputs: centroids in t (gamma/B/mis/pi entries are ignored and rebuilt).

@@ -144,7 +144,7 @@ pb_status check_cfg(pb_ctx *ctx, const pb_config *c) {
 }
 
 KParams kparams(const pb_ctx *ctx, const pb_config *c) {
-    KParams P;
+    KParams P{};   // every pointer the call does not set stays null (no eye queries, rows or sinks)
     P.seed = c->seed;
     P.max_depth = c->max_depth;
     P.M = c->M;
@@ -173,9 +173,13 @@ KParams kparams(const pb_ctx *ctx, const pb_config *c) {
     P.film = c->film;
     P.proposal = c->proposal;
     P.split = c->split_cap == 0 ? (1u << 16) : (c->split_cap < 0 ? 0xFFFFFFFFu : (uint32_t)c->split_cap);
+    P.fixed_bound = c->fixed_bound != 0;
     P.acc = LearnAcc{nullptr, nullptr, nullptr, nullptr};
     P.mlp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
     P.smp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    P.mlpp = MlpRows{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, 0};
+    P.smpp = SampleSink{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    P.q = EyeQueries{nullptr, nullptr, nullptr, nullptr, 0, nullptr, 0};
     P.iter_dev = nullptr;
     return P;
 }
@@ -619,6 +623,8 @@ pb_status wf_ensure(pb_ctx *ctx) {
     CK(dalloc(o, &W.node_q, nn));
     CK(dalloc(o, &W.node_g, nn));
     CK(dalloc(o, &W.node_n, nn));
+    CK(dalloc(o, &W.node_x, nn));
+    CK(dalloc(o, &W.node_u, nn));
     CK(dalloc(o, &W.list[0], nn));
     CK(dalloc(o, &W.list[1], nn));
     CK(dalloc(o, &W.ctl, (size_t)16));
@@ -926,6 +932,7 @@ static std::string tune_key(const pb_ctx *ctx, const pb_config *cfg) {
         key += buf;
     }
     if (cfg->trace) key += "|trace1";
+    if (cfg->fixed_bound) key += "|fixedB";   // longer chains where a bound sits below f/q / 2
     return key;
 }
 

@@ -67,8 +67,9 @@ struct WfBufs {
     int32_t *node_chain, *node_v, *node_nq;
     struct WfResult *node_res;         // WF_MAXQ per node
     struct WfQuery *node_q;
-    float *node_g;
+    float *node_g;                     // g and children under the estimate's own bound
     int32_t *node_n;
+    float *node_x, *node_u;            // f/q and the RRS uniform (the walk under a raised bound)
     int32_t *list[2];                  // nodes that need a step (ping-pong)
     int32_t *ctl;                      // counters (WF_CTL_* in pb_light.cu)
     int node_cap;
@@ -108,6 +109,7 @@ struct KParams {
     int trace;                  // wavefront trace stages: 0 a query per thread; 1 persistent warps, lane refill
     int film;                   // strategies reaching the film: 0 all, 1 the proxy strategy only, 2 all but it
     uint32_t split;             // first pre-order estimator node without splitting (split limit)
+    int fixed_bound;            // 1: one B per estimate; 0: the raise rule (est_child_invB)
     LearnAcc acc;
     MlpRows mlp;            // rows != nullptr: write rows (feature pass); sel != nullptr: select with them
     MlpRows mlpp;           // the proxy strategy's network: rows at the proxy's vertex, its S' selections
@@ -146,6 +148,96 @@ __device__ __forceinline__ float est_child_weight(float g, uint32_t v, uint32_t 
     return (fabsf(g) > 1.0f && v >= split) ? g : (g > 0.0f ? 1.0f : -1.0f);
 }
 
+// The bound a node hands its children. The paper keeps one B for a whole
+// estimate; here a node that splits (|g| > 1, i.e. f/q > 2B) gives its
+// children the bound B' = its own f/q. The estimate of 1/beta stays
+// unbiased under any bound fixed before a node's draw (1/beta = 1/B +
+// (1 - beta/B) / beta holds for every B, node by node), and the node's term
+// becomes g / B', the expected own term of its children, each of which
+// enters with 1 / B'. Chains whose draws stay below 2B never raise the
+// bound, so they are the paper's walk exactly; a tree that would split
+// without end under a low B grows only as far as its own ratios allow.
+__device__ __forceinline__ float est_child_invB(float g, float x, float invB, int fixed) {
+    return (!fixed && fabsf(g) > 1.0f) ? 1.0f / x : invB;
+}
+
+// One node of the exact walk on the stack form: frames of pending children
+// that share a weight and a bound; children whose weight and bound match the
+// frame on top join it. g0, n0 are the node's g and children under the
+// estimate's own bound invB0 (x = f/q, u = the node's RRS uniform), reused
+// while the current bound is that one.
+struct EstStep {
+    float g, cw, cib;   // g under the current bound; the children's weight and inverse bound
+    int n;
+    bool push;          // the children need a frame of their own
+};
+template <class St>
+__device__ __forceinline__ EstStep est_step(const St &st, float x, float u, float g0, int n0, float invB0, uint32_t v,
+                                            const KParams &P) {
+    EstStep e;
+    if (st.cur_ib == invB0) {
+        e.g = g0;
+        e.n = n0;
+    } else {
+        e.g = 1.0f - x * st.cur_ib;
+        e.n = est_children(e.g, u, v, P.split);
+    }
+    e.cib = est_child_invB(e.g, x, st.cur_ib, P.fixed_bound);
+    e.cw = st.cur_sign * est_child_weight(e.g, v, P.split);
+    e.push = e.n >= 1 && !(st.sp > 0 && st.fr_sign[st.sp - 1] == e.cw && st.fr_ib[st.sp - 1] == e.cib);
+    return e;
+}
+// Takes the node: adds its term and its children, then moves to the next
+// pending node. Returns 0 to go on, 1 when the chain has ended, 2 when the
+// children needed a frame beyond CAP or their weight left the float range
+// (a truncated estimate).
+template <int CAP, class St>
+__device__ __forceinline__ int est_take(St &st, const EstStep &e, double &sum_t) {
+    sum_t += (double)(st.cur_sign * e.g * e.cib);
+    if (e.n >= 1) {
+        if (!e.push) {
+            st.fr_rem[st.sp - 1] += e.n;
+        } else {
+            if (st.sp >= CAP || !isfinite(e.cw)) return 2;
+            st.fr_sign[st.sp] = e.cw;
+            st.fr_ib[st.sp] = e.cib;
+            st.fr_rem[st.sp] = e.n;
+            st.sp++;
+        }
+    }
+    if (st.sp == 0) return 1;
+    st.cur_sign = st.fr_sign[st.sp - 1];
+    st.cur_ib = st.fr_ib[st.sp - 1];
+    if (--st.fr_rem[st.sp - 1] == 0) st.sp--;
+    return 0;
+}
+// Whether the walk state is on the count form: every pending node has
+// weight +1 under the estimate's own bound. pend = pending nodes, the
+// current one included.
+template <class St>
+__device__ __forceinline__ bool est_count_form(const St &st, float invB0, int &pend) {
+    bool pos = st.cur_sign == 1.0f && st.cur_ib == invB0;
+    pend = 1;
+    for (int f = 0; f < st.sp; ++f) {
+        pos = pos && st.fr_sign[f] == 1.0f && st.fr_ib[f] == invB0;
+        pend += st.fr_rem[f];
+    }
+    return pos;
+}
+// the count form with `pend` pending nodes as a stack of at most one frame
+template <class St>
+__device__ __forceinline__ void est_from_count(St &st, int pend, float invB0) {
+    st.cur_sign = 1.0f;
+    st.cur_ib = invB0;
+    st.sp = 0;
+    if (pend - 1 > 0) {
+        st.fr_sign[0] = 1.0f;
+        st.fr_ib[0] = invB0;
+        st.fr_rem[0] = pend - 1;
+        st.sp = 1;
+    }
+}
+
 __device__ __forceinline__ uint32_t eff_iter(const KParams &P, uint32_t iter_base) {
     return P.iter_dev ? iter_base + *P.iter_dev : iter_base;
 }
@@ -157,9 +249,10 @@ __device__ __forceinline__ uint32_t eff_iter(const KParams &P, uint32_t iter_bas
 struct ChainState {
     int slot, k, rep, next;
     double sum_t;
-    float cur_sign;
+    float cur_sign, cur_ib;   // the current node's weight and inverse bound
     int sp;
-    float fr_sign[PB_MAXF];
+    float fr_sign[PB_MAXF];   // frames of pending children: weight, inverse bound, count
+    float fr_ib[PB_MAXF];
     int fr_rem[PB_MAXF];
     double prod, surv;   // Booth's roulette: product of g so far, product of the continuation probabilities
 };

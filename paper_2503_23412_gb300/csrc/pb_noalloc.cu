@@ -15,8 +15,8 @@
 //
 // The kernel is a one-phase form of the estimator (Sec. 4.2, App. Alg. I~):
 // one warp per (entry, repeat) draws 32 pre-order nodes at a time and
-// replays the sequential walk with a stack of 48 sign frames (children whose
-// sign matches the top frame join it). It uses the same
+// replays the sequential walk with a stack of 48 frames (children whose
+// weight and bound match the top frame join it). It uses the same
 // streams as the pooled estimator in pb_light.cu, so both produce the same
 // estimates.
 #include "pb_ctx.h"
@@ -25,6 +25,14 @@
 namespace {
 
 constexpr int NA_MAXF = 48;
+
+// the walk state a warp keeps (every lane holds the same copy)
+struct NAStack {
+    float cur_sign, cur_ib;
+    int sp;
+    float fr_sign[NA_MAXF], fr_ib[NA_MAXF];
+    int fr_rem[NA_MAXF];
+};
 
 struct NAScratch {
     int work;        // next (entry, repeat) to claim; cleared at the start of each call
@@ -72,54 +80,39 @@ __global__ void __launch_bounds__(128) k_na_recip(DScene S, KParams P, uint32_t 
         double sum_t = 0.0;
         int nodes = 0;
         bool done = false, trunc = false;
-        float fr_sign[NA_MAXF];
-        int fr_rem[NA_MAXF];
-        int sp = 0;
-        float cur_sign = 1.0f;
+        NAStack ws;
+        ws.cur_sign = 1.0f;
+        ws.cur_ib = invB;
+        ws.sp = 0;
         for (int base = 0; !done; base += 32) {
             int v = base + lane;
-            float g = 1.0f;
+            float g = 1.0f, x = 0.0f, u = 1.0f;
             int nch = 0;
             if (v < P.trial_cap) {
                 Rng R;
                 R.init(P.seed, K_RECIP, iteration, (uint32_t)(k * 8 + rep), (uint32_t)v);
-                float ratio = entry_ratio<false>(S, E, R, nullptr);
-                g = 1.0f - ratio * invB;
-                nch = est_children(g, R.u(18), (uint32_t)v, P.split);
+                x = entry_ratio<false>(S, E, R, nullptr);
+                u = R.u(18);
+                g = 1.0f - x * invB;
+                nch = est_children(g, u, (uint32_t)v, P.split);
             }
             for (int j = 0; j < 32; ++j) {
-                float gj = __shfl_sync(0xffffffffu, g, j);
-                int nj = __shfl_sync(0xffffffffu, nch, j);
+                const float gj = __shfl_sync(0xffffffffu, g, j), xj = __shfl_sync(0xffffffffu, x, j);
+                const float uj = __shfl_sync(0xffffffffu, u, j);
+                const int nj = __shfl_sync(0xffffffffu, nch, j);
                 if (done) continue;
                 if (base + j >= P.trial_cap) {
                     done = true;
                     trunc = true;
                     continue;
                 }
-                sum_t += (double)(cur_sign * gj * invB);
+                const EstStep e = est_step(ws, xj, uj, gj, nj, invB, (uint32_t)(base + j), P);
                 nodes++;
-                if (nj >= 1) {
-                    // children whose weight matches the pending frame on top join it
-                    const float cs = cur_sign * est_child_weight(gj, (uint32_t)(base + j), P.split);
-                    if (sp > 0 && fr_sign[sp - 1] == cs) {
-                        fr_rem[sp - 1] += nj;
-                    } else {
-                        if (sp >= NA_MAXF) {
-                            done = true;
-                            trunc = true;
-                            continue;
-                        }
-                        fr_sign[sp] = cs;
-                        fr_rem[sp] = nj;
-                        ++sp;
-                    }
-                }
-                if (sp == 0) {
+                const int r = est_take<NA_MAXF>(ws, e, sum_t);
+                if (r) {
                     done = true;
-                    continue;
+                    trunc = r == 2;
                 }
-                cur_sign = fr_sign[sp - 1];
-                if (--fr_rem[sp - 1] == 0) --sp;
             }
         }
         if (lane == 0) {

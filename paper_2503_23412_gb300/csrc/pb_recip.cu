@@ -70,6 +70,14 @@ __global__ void __launch_bounds__(128) k_recip_pilot(DScene S, DTables T, KParam
 #define MAXF PB_MAXF
 #define MAXF1 8          // walk frames a warp keeps; deeper walks continue in a block
 
+// the walk state a warp keeps (every lane holds the same copy)
+struct WarpStack {
+    float cur_sign, cur_ib;
+    int sp;
+    float fr_sign[MAXF1], fr_ib[MAXF1];
+    int fr_rem[MAXF1];
+};
+
 // Phase 1: one warp per (entry, repeat). The tree's nodes are numbered in
 // pre-order, so node v's sample depends only on v: the 32 lanes draw nodes
 // base..base+31 together, then every lane replays the same sequential walk
@@ -101,10 +109,10 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
         double sum_t = 0.0;   // long chains add thousands of terms
         int nodes = 0;
         bool done = false, trunc = false, handed = false;
-        float fr_sign[MAXF1];
-        int fr_rem[MAXF1];
-        int sp = 0;
-        float cur_sign = 1.0f;
+        WarpStack ws;
+        ws.cur_sign = 1.0f;
+        ws.cur_ib = invB;
+        ws.sp = 0;
         bool deep = false;   // the walk needs more frames than a warp keeps
         for (int base = 0; !done; base += 32) {
             if (base >= P.handoff || deep || long_chain) {
@@ -115,8 +123,12 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
                     if (lane == 0) {
                         ChainState &cs = B.chains[slot_q];
                         cs.slot = slot; cs.k = k; cs.rep = rep; cs.next = base;
-                        cs.sum_t = sum_t; cs.cur_sign = cur_sign; cs.sp = sp;
-                        for (int i = 0; i < sp; ++i) { cs.fr_sign[i] = fr_sign[i]; cs.fr_rem[i] = fr_rem[i]; }
+                        cs.sum_t = sum_t; cs.cur_sign = ws.cur_sign; cs.cur_ib = ws.cur_ib; cs.sp = ws.sp;
+                        for (int i = 0; i < ws.sp; ++i) {
+                            cs.fr_sign[i] = ws.fr_sign[i];
+                            cs.fr_ib[i] = ws.fr_ib[i];
+                            cs.fr_rem[i] = ws.fr_rem[i];
+                        }
                     }
                     handed = true;
                     break;
@@ -128,53 +140,41 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
                 }
             }
             int v = base + lane;
-            float g = 1.0f;
+            float g = 1.0f, x = 0.0f, u = 1.0f;
             int nch = 0;
             if (v < P.trial_cap) {
                 Rng R;
                 R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
-                float ratio = entry_ratio<COUNT>(S, E, R, &tc);
-                g = 1.0f - ratio * invB;
-                nch = est_children(g, R.u(18), (uint32_t)v, P.split);
+                x = entry_ratio<COUNT>(S, E, R, &tc);
+                u = R.u(18);
+                g = 1.0f - x * invB;
+                nch = est_children(g, u, (uint32_t)v, P.split);
             }
             // the walk stops before a node that would need a frame beyond MAXF1;
             // the block phase resumes from that node with the full stack
             int stop = 32;
             for (int j = 0; j < 32; ++j) {
-                float gj = __shfl_sync(0xffffffffu, g, j);
-                int nj = __shfl_sync(0xffffffffu, nch, j);
+                const float gj = __shfl_sync(0xffffffffu, g, j), xj = __shfl_sync(0xffffffffu, x, j);
+                const float uj = __shfl_sync(0xffffffffu, u, j);
+                const int nj = __shfl_sync(0xffffffffu, nch, j);
                 if (done || j >= stop) continue;
                 if (base + j >= P.trial_cap) {
                     done = true;
                     trunc = true;
                     continue;
                 }
-                // children whose weight matches the pending frame on top join it
-                // (the walk reads only the weight sequence and the pending count)
-                const float cs = cur_sign * est_child_weight(gj, (uint32_t)(base + j), P.split);
-                const bool merge = sp > 0 && fr_sign[sp - 1] == cs;
-                if (nj >= 1 && !merge && sp >= MAXF1) {
+                const EstStep e = est_step(ws, xj, uj, gj, nj, invB, (uint32_t)(base + j), P);
+                if (e.push && ws.sp >= MAXF1) {
                     stop = j;
                     deep = true;
                     continue;
                 }
-                sum_t += (double)(cur_sign * gj * invB);
                 nodes++;
-                if (nj >= 1) {
-                    if (merge) {
-                        fr_rem[sp - 1] += nj;
-                    } else {
-                        fr_sign[sp] = cs;
-                        fr_rem[sp] = nj;
-                        ++sp;
-                    }
-                }
-                if (sp == 0) {
+                const int r = est_take<MAXF1>(ws, e, sum_t);
+                if (r) {   // 2: the children's weight left the float range
                     done = true;
-                    continue;
+                    trunc = r == 2;
                 }
-                cur_sign = fr_sign[sp - 1];
-                if (--fr_rem[sp - 1] == 0) --sp;
             }
             if (deep) base = base + stop - 32;   // resume at node base + stop
         }

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
     iter_base = eff_iter(P, iter_base);
     __shared__ float sg[PH2_BATCH];
     __shared__ int sn[PH2_BATCH];
+    __shared__ float sx[PH2_BATCH], su[PH2_BATCH];   // f/q and RRS uniform (the walk under a raised bound)
     __shared__ uint8_t skey[PH2_BATCH];
     __shared__ int16_t sperm[PH2_BATCH];
     __shared__ int s_cnt[4];
@@ -102,22 +103,24 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
             for (int j = 0; j < npt; ++j) {
                 int idx = sperm[j * PH2_THREADS + tid];
                 int v = base + idx;
-                float g = 1.0f;
+                float g = 1.0f, x = 0.0f, u = 1.0f;
                 int nch = 0;
                 if (v < P.trial_cap) {
                     Rng R;
                     R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
-                    float ratio = entry_ratio<COUNT>(S, E, R, &tc);
-                    g = 1.0f - ratio * invB;
-                    nch = est_children(g, R.u(18), (uint32_t)v, P.split);
+                    x = entry_ratio<COUNT>(S, E, R, &tc);
+                    u = R.u(18);
+                    g = 1.0f - x * invB;
+                    nch = est_children(g, u, (uint32_t)v, P.split);
                 }
                 sg[idx] = g;
                 sn[idx] = nch;
+                sx[idx] = x;
+                su[idx] = u;
             }
             if (tid == 0) {
-                bool pos = st.cur_sign == 1.0f;   // weights other than +1 only arise past the split limit
-                for (int i = 0; i < st.sp; ++i) pos = pos && st.fr_sign[i] == 1.0f;
-                s_neg = pos ? 0 : 1;
+                int pend;
+                s_neg = est_count_form(st, invB, pend) ? 0 : 1;
             }
             __syncthreads();
             // any negative g in the batch?
@@ -172,13 +175,7 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
                     } else {
                         int pend = pend0 + s_pending[PH2_THREADS - 1];
                         st.next = base + nb;
-                        st.cur_sign = 1.0f;
-                        st.sp = 0;
-                        if (pend - 1 > 0) {
-                            st.fr_sign[0] = 1.0f;
-                            st.fr_rem[0] = pend - 1;
-                            st.sp = 1;
-                        }
+                        est_from_count(st, pend, invB);
                         s_done = 0;
                     }
                 }
@@ -193,34 +190,14 @@ __global__ void __launch_bounds__(PH2_THREADS) k_recip_long(DScene S, DTables T,
                         st.next = v;
                         break;
                     }
-                    float gj = sg[j];
-                    int nj = sn[j];
-                    st.sum_t += (double)(st.cur_sign * gj * invB);
-                    if (nj >= 1) {
-                        // children whose weight matches the pending frame on top join it
-                        const float cs = st.cur_sign * est_child_weight(gj, (uint32_t)v, P.split);
-                        if (st.sp > 0 && st.fr_sign[st.sp - 1] == cs) {
-                            st.fr_rem[st.sp - 1] += nj;
-                        } else {
-                            if (st.sp >= PB_MAXF) {
-                                s_done = 1;
-                                trunc = true;
-                                st.next = v + 1;
-                                break;
-                            }
-                            st.fr_sign[st.sp] = cs;
-                            st.fr_rem[st.sp] = nj;
-                            st.sp++;
-                        }
-                    }
-                    if (st.sp == 0) {
+                    const EstStep e = est_step(st, sx[j], su[j], sg[j], sn[j], invB, (uint32_t)v, P);
+                    const int r = est_take<PB_MAXF>(st, e, st.sum_t);
+                    st.next = v + 1;
+                    if (r) {
                         s_done = 1;
-                        st.next = v + 1;
+                        trunc = r == 2;
                         break;
                     }
-                    st.cur_sign = st.fr_sign[st.sp - 1];
-                    if (--st.fr_rem[st.sp - 1] == 0) st.sp--;
-                    st.next = v + 1;
                 }
             }
             __syncthreads();

@@ -53,6 +53,7 @@ __global__ void k_wf_init(KParams P, Pool B, WfBufs W, int slots) {
         st.next = 0;
         st.sum_t = 0.0;
         st.cur_sign = 1.0f;
+        st.cur_ib = 1.0f / B.eB[(size_t)slot * B.ML + st.k];
         st.sp = 0;
         st.prod = 1.0;
         st.surv = 1.0;
@@ -175,6 +176,8 @@ __global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, Wf
             atomicExch(&W.ctl[WF_CTL_ERR], 2);
             W.node_g[i] = 1.0f;
             W.node_n[i] = 0;
+            W.node_x[i] = 0.0f;
+            W.node_u[i] = 1.0f;
         } else if (T.susp) {
             W.node_q[i] = T.q;
             cg::coalesced_group g = cg::coalesced_threads();
@@ -184,9 +187,11 @@ __global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, Wf
         } else if (PILOT) {
             W.node_g[i] = ratio;
         } else {
-            float gv = 1.0f - ratio * invB;
+            const float gv = 1.0f - ratio * invB, u18 = R.u(18);
             W.node_g[i] = gv;
-            W.node_n[i] = est_children(gv, R.u(18), (uint32_t)W.node_v[i], P.split);
+            W.node_n[i] = est_children(gv, u18, (uint32_t)W.node_v[i], P.split);
+            W.node_x[i] = ratio;
+            W.node_u[i] = u18;
         }
     }
 }
@@ -519,6 +524,26 @@ __global__ void __launch_bounds__(128) k_wf_trace_pt(DScene S, KParams P, Pool B
     }
 }
 
+// the exact sequential walk over nodes [o, o + cnt) of a window, on the
+// stack form (one thread)
+__device__ __forceinline__ void walk_seq(const KParams &P, const WfBufs &W, ChainState &gst, int o, int cnt, float invB,
+                                         int &next, double &sum_t, int &done, int &trunc) {
+    for (int q = 0; q < cnt; ++q) {
+        const EstStep e = est_step(gst, W.node_x[o + q], W.node_u[o + q], W.node_g[o + q], W.node_n[o + q], invB,
+                                   (uint32_t)next, P);
+        next += 1;
+        const int r = est_take<PB_MAXF>(gst, e, sum_t);
+        if (r) {
+            done = 1;
+            trunc = r == 2;
+            return;
+        }
+    }
+}
+
+// windows at least this long are walked by a whole block (k_wf_walk_long)
+constexpr int WF_WALK_LONG = 8192;
+
 // one warp per chain: the walk over this round's window in chunks of 32
 // nodes. While every pending node has sign +1 and the chunk has no negative
 // g, the walk reduces to counts (pending_v = pending - 1 + n_v; the chain
@@ -530,22 +555,17 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
     const int items = W.ctl[WF_CTL_ITEMS];
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < items; c += warps) {
         const int w = W.ch_w[c];
-        if (W.ch_done[c] || w == 0) continue;
+        if (W.ch_done[c] || w == 0 || w >= WF_WALK_LONG) continue;
         ChainState &gst = B.chains[c];
         const int slot = gst.slot, k = gst.k, rep = gst.rep;
         const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
         const int off = W.ch_off[c];
         int next = gst.next;
         double sum_t = gst.sum_t;
-        // pending-count form of the walk state while all signs are +1
-        // (weights other than +1 only arise past the split limit)
-        bool pos = gst.cur_sign == 1.0f;
-        int pend = 1;
-        for (int f = 0; f < gst.sp; ++f) {
-            pos = pos && gst.fr_sign[f] == 1.0f;
-            pend += gst.fr_rem[f];
-        }
-        bool stack_form = !pos;   // gst holds the authoritative stack
+        // pending-count form of the walk state while every pending node has
+        // weight +1 under the estimate's own bound
+        int pend;
+        bool stack_form = !est_count_form(gst, invB, pend);   // gst holds the authoritative stack
         int done = 0, trunc = 0;
         // four chunks are loaded ahead of their walk (128 nodes per trip)
         float gq[4];
@@ -591,62 +611,18 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
             }
             // exact sequential walk of this chunk by lane 0, on the stack form
             if (!stack_form) {
-                if (lane == 0) {
-                    gst.cur_sign = 1.0f;
-                    gst.sp = 0;
-                    if (pend - 1 > 0) {
-                        gst.fr_sign[0] = 1.0f;
-                        gst.fr_rem[0] = pend - 1;
-                        gst.sp = 1;
-                    }
-                }
+                if (lane == 0) est_from_count(gst, pend, invB);
                 stack_form = true;
             }
-            if (lane == 0) {
-                const int cnt = min(32, w - j0);
-                for (int q = 0; q < cnt; ++q) {
-                    const float gj = W.node_g[off + j0 + q];
-                    const int nj = W.node_n[off + j0 + q];
-                    const uint32_t v = (uint32_t)next;
-                    sum_t += (double)(gst.cur_sign * gj * invB);
-                    next += 1;
-                    if (nj >= 1) {
-                        // children whose weight matches the pending frame on top join it
-                        const float cs = gst.cur_sign * est_child_weight(gj, v, P.split);
-                        if (gst.sp > 0 && gst.fr_sign[gst.sp - 1] == cs) {
-                            gst.fr_rem[gst.sp - 1] += nj;
-                        } else {
-                            if (gst.sp >= PB_MAXF) {
-                                done = 1;
-                                trunc = 1;
-                                break;
-                            }
-                            gst.fr_sign[gst.sp] = cs;
-                            gst.fr_rem[gst.sp] = nj;
-                            gst.sp++;
-                        }
-                    }
-                    if (gst.sp == 0) {
-                        done = 1;
-                        break;
-                    }
-                    gst.cur_sign = gst.fr_sign[gst.sp - 1];
-                    if (--gst.fr_rem[gst.sp - 1] == 0) gst.sp--;
-                }
-            }
+            if (lane == 0) walk_seq(P, W, gst, off + j0, min(32, w - j0), invB, next, sum_t, done, trunc);
             done = __shfl_sync(0xffffffffu, done, 0);
             trunc = __shfl_sync(0xffffffffu, trunc, 0);
             next = __shfl_sync(0xffffffffu, next, 0);
             sum_t = __shfl_sync(0xffffffffu, sum_t, 0);
             __syncwarp();
             // back to the count form when the stack turned all-positive again
-            bool p2 = gst.cur_sign == 1.0f;
-            int pe = 1;
-            for (int f = 0; f < gst.sp; ++f) {
-                p2 = p2 && gst.fr_sign[f] == 1.0f;
-                pe += gst.fr_rem[f];
-            }
-            if (p2) {
+            int pe;
+            if (est_count_form(gst, invB, pe)) {
                 stack_form = false;
                 pend = pe;
             }
@@ -657,15 +633,7 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
             trunc = 1;
         }
         if (lane == 0) {
-            if (!stack_form) {   // store the count form as a one-frame stack
-                gst.cur_sign = 1.0f;
-                gst.sp = 0;
-                if (pend - 1 > 0) {
-                    gst.fr_sign[0] = 1.0f;
-                    gst.fr_rem[0] = pend - 1;
-                    gst.sp = 1;
-                }
-            }
+            if (!stack_form) est_from_count(gst, pend, invB);   // store the count form as a one-frame stack
             gst.next = next;
             gst.sum_t = sum_t;
             if (done) {
@@ -680,6 +648,144 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
             }
         }
         __syncwarp();
+    }
+}
+
+// one block per chain whose window holds at least WF_WALK_LONG nodes: the
+// same walk, in tiles of 1024 nodes (4 per thread). A tile with no negative
+// g on the count form is walked in parallel: a block scan of (n - 1) gives
+// every node's pending count, the chain ends at the first node where it
+// reaches 0, and the terms g / B up to there are summed by a block
+// reduction. Otherwise thread 0 walks the tile on the stack form.
+constexpr int WF_LONG_THREADS = 256;
+__global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Pool B, WfBufs W) {
+    __shared__ int s_wsum[WF_LONG_THREADS / 32];
+    __shared__ double s_wpart[WF_LONG_THREADS / 32];
+    __shared__ int s_end, s_done, s_trunc, s_next, s_pend;
+    __shared__ double s_sum;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int items = W.ctl[WF_CTL_ITEMS];
+    for (int c = blockIdx.x; c < items; c += gridDim.x) {
+        const int w = W.ch_w[c];
+        if (W.ch_done[c] || w < WF_WALK_LONG) continue;   // uniform over the block
+        ChainState &gst = B.chains[c];
+        const int slot = gst.slot, k = gst.k, rep = gst.rep;
+        const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
+        const int off = W.ch_off[c];
+        if (tid == 0) {
+            int pend;
+            s_pend = est_count_form(gst, invB, pend) ? pend : -1;   // -1: the stack form holds the state
+            s_next = gst.next;
+            s_sum = gst.sum_t;
+            s_done = 0;
+            s_trunc = 0;
+        }
+        __syncthreads();
+        for (int j0 = 0; j0 < w; j0 += 4 * WF_LONG_THREADS) {
+            if (s_done) break;
+            const int cnt = min(4 * WF_LONG_THREADS, w - j0);
+            float g[4];
+            int n[4];
+            bool neg = false;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int jj = 4 * tid + i;
+                g[i] = jj < cnt ? W.node_g[off + j0 + jj] : 1.0f;
+                n[i] = jj < cnt ? W.node_n[off + j0 + jj] : 1;
+                neg |= jj < cnt && g[i] < 0.0f;
+            }
+            const bool anyneg = __syncthreads_or(neg) != 0;
+            const int pend0 = s_pend;
+            if (pend0 > 0 && !anyneg) {
+                int loc[4], acc = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    acc += n[i] - 1;
+                    loc[i] = acc;
+                }
+                // block exclusive scan of the threads' sums
+                int x = acc;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (lane == 31) s_wsum[wid] = x;
+                if (tid == 0) s_end = cnt;
+                __syncthreads();
+                int wbase = 0;
+                for (int q = 0; q < wid; ++q) wbase += s_wsum[q];
+                const int excl = pend0 + wbase + x - acc;   // pending count before this thread's first node
+                int first = cnt;
+#pragma unroll
+                for (int i = 3; i >= 0; --i)
+                    if (4 * tid + i < cnt && excl + loc[i] <= 0) first = 4 * tid + i;
+                if (first < cnt) atomicMin(&s_end, first);
+                __syncthreads();
+                const int end = s_end;   // last node of the chain in this tile, or cnt
+                double part = 0.0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (4 * tid + i < cnt && 4 * tid + i <= end) part += (double)(g[i] * invB);
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (lane == 0) s_wpart[wid] = part;
+                __syncthreads();
+                if (tid == 0) {
+                    double t = 0.0;
+                    int tot = 0;
+                    for (int q = 0; q < WF_LONG_THREADS / 32; ++q) {
+                        t += s_wpart[q];
+                        tot += s_wsum[q];
+                    }
+                    s_sum += t;
+                    if (end < cnt) {
+                        s_next += end + 1;
+                        s_done = 1;
+                    } else {
+                        s_next += cnt;
+                        s_pend = pend0 + tot;
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
+            // thread 0: the exact walk of this tile on the stack form
+            if (tid == 0) {
+                if (pend0 > 0) est_from_count(gst, pend0, invB);   // from the count form
+                int next = s_next, done = 0, trunc = 0;
+                double sum_t = s_sum;
+                walk_seq(P, W, gst, off + j0, cnt, invB, next, sum_t, done, trunc);
+                s_next = next;
+                s_sum = sum_t;
+                s_done = done;
+                s_trunc = trunc;
+                // back to the count form when the stack turned all-positive again
+                int pe;
+                s_pend = est_count_form(gst, invB, pe) ? pe : -1;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            int done = s_done, trunc = s_trunc;
+            const int next = s_next;
+            if (!done && next >= P.trial_cap) {
+                done = 1;
+                trunc = 1;
+            }
+            if (s_pend > 0) est_from_count(gst, s_pend, invB);   // store the count form as a one-frame stack
+            gst.next = next;
+            gst.sum_t = s_sum;
+            if (done) {
+                size_t o = ((size_t)slot * B.ML + k) * P.repeats + rep;
+                B.rep[o] = (float)((double)invB + s_sum);
+                B.repn[o] = (float)next;
+                B.reptr[o] = trunc;
+                W.ch_done[c] = 1;
+                atomicSub(&W.ctl[WF_CTL_ACTIVE], 1);
+            } else {
+                W.ch_win[c] = min(2 * W.ch_win[c], WF_WIN_MAX);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -810,32 +916,17 @@ __global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t
             }
             Rng R;
             R.init(P.seed, K_RECIP, iter_base + st.slot, (uint32_t)(st.k * 8 + st.rep), (uint32_t)st.next);
-            float ratio = entry_ratio<false>(S, E, R, nullptr);
-            float gj = 1.0f - ratio * invB;
+            const float ratio = entry_ratio<false>(S, E, R, nullptr), u18 = R.u(18);
+            const float gj = 1.0f - ratio * invB;
             const uint32_t v = (uint32_t)st.next;
-            int nj = est_children(gj, R.u(18), v, P.split);
-            st.sum_t += (double)(st.cur_sign * gj * invB);
+            const EstStep e = est_step(st, ratio, u18, gj, est_children(gj, u18, v, P.split), invB, v, P);
             st.next += 1;
-            if (nj >= 1) {
-                const float cs = st.cur_sign * est_child_weight(gj, v, P.split);
-                if (st.sp > 0 && st.fr_sign[st.sp - 1] == cs) {
-                    st.fr_rem[st.sp - 1] += nj;
-                } else {
-                    if (st.sp >= PB_MAXF) {
-                        done = trunc = 1;
-                        break;
-                    }
-                    st.fr_sign[st.sp] = cs;
-                    st.fr_rem[st.sp] = nj;
-                    st.sp++;
-                }
-            }
-            if (st.sp == 0) {
+            const int r = est_take<PB_MAXF>(st, e, st.sum_t);
+            if (r) {
                 done = 1;
+                trunc = r == 2;
                 break;
             }
-            st.cur_sign = st.fr_sign[st.sp - 1];
-            if (--st.fr_rem[st.sp - 1] == 0) st.sp--;
         }
         size_t o = ((size_t)st.slot * B.ML + st.k) * P.repeats + st.rep;
         B.rep[o] = (float)((double)invB + st.sum_t);
@@ -889,7 +980,10 @@ void launch_recip_wavefront(const DScene &S, const DTables &T, const KParams &P,
             launch_trace(S, P, B, W, s, num_sms, st);
         }
         if (P.booth > 0.0f) k_wf_walk_booth<<<num_sms * 16, 128, 0, st>>>(P, B, W, iter_base);
-        else k_wf_walk<<<num_sms * 16, 128, 0, st>>>(P, B, W);
+        else {
+            k_wf_walk<<<num_sms * 16, 128, 0, st>>>(P, B, W);
+            k_wf_walk_long<<<num_sms * 2, WF_LONG_THREADS, 0, st>>>(P, B, W);
+        }
     }
     k_wf_finish_rest<<<num_sms * 2, 128, 0, st>>>(S, P, B, W, iter_base);
 }

@@ -41,7 +41,8 @@ class pb_config(C.Structure):
                 ("trial_cap", C.c_int), ("iter0", C.c_int), ("batch", C.c_int), ("count_traversal", C.c_int),
                 ("chain_handoff", C.c_int), ("pilot_min", C.c_int), ("pilot_max", C.c_int), ("proposal", C.c_int),
                 ("graph", C.c_int), ("side_in", C.c_float), ("estimator", C.c_int), ("booth", C.c_float),
-                ("trace", C.c_int), ("film", C.c_int), ("split_cap", C.c_int)]
+                ("trace", C.c_int), ("film", C.c_int), ("split_cap", C.c_int),
+                ("fixed_bound", C.c_int)]
 
 
 class pb_stats(C.Structure):
@@ -164,16 +165,18 @@ class PBError(RuntimeError):
 
 def config(seed=7, spp=1, max_depth=6, M=10000, M_p=10000, repeats=5, proxy=1, conn=1, trial_cap=1 << 16, iter0=0,
            batch=0, count_traversal=0, chain_handoff=0, pilot_min=0, pilot_max=0, proposal=0, graph=0, side_in=0.0,
-           estimator=0, booth=0.0, trace=0, film=0, split_cap=0):
+           estimator=0, booth=0.0, trace=0, film=0, split_cap=0, fixed_bound=0):
     """booth > 0: Booth's Russian roulette of that scale in the reciprocal
     estimator (wavefront schedule only); 0: the paper's RRS function.
     trace = 1: the wavefront's trace stages run on persistent warps that
     refill idle lanes (same answers). film = 1 keeps only the proxy
     strategy's weighted contributions in the film, 2 all but those.
-    split_cap: the estimator's split limit (0: node 65536; negative: never)."""
+    split_cap: the estimator's split limit (0: node 65536; negative: never).
+    fixed_bound = 1: one B per estimate (the paper's walk); 0: a node with
+    f/q > 2B hands its children the bound f/q (the raise rule)."""
     return pb_config(seed, spp, max_depth, M, M_p, repeats, proxy, conn, trial_cap, iter0, batch, count_traversal,
                      chain_handoff, pilot_min, pilot_max, proposal, graph, side_in, estimator, booth, trace, film,
-                     split_cap)
+                     split_cap, fixed_bound)
 
 
 def render_batch(renderers, cfgs, allow_truncated=False):

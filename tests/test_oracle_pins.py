@@ -112,6 +112,7 @@ def test_split_limit_keeps_the_estimator_unbiased():
     of these cases is far shorter, and the estimates equal those of the
     unlimited rule exactly."""
     try:
+        O.set_fixed_bound_default(1)   # the paper's one B per estimate: the limit alone
         O.set_split_default(0)
         t0, _, n0, _ = O.recip_1d(1, 1.2, 100000, seed=17)
         O.set_split_default(1 << 16)
@@ -128,6 +129,7 @@ def test_split_limit_keeps_the_estimator_unbiased():
         assert np.any(t4 != t1)   # the limit changed some chains
     finally:
         O.set_split_default(1 << 16)
+        O.set_fixed_bound_default(0)
 
 
 # --- Booth's Russian roulette (the baseline of the paper's RR ablation) -----------
@@ -215,10 +217,49 @@ def test_booth_roulette_on_an_incomplete_sub_path_and_the_ablation_claim():
 
 def test_estimator_diverges_outside_convergence_domain():
     """App. "Convergence Condition": (1/B) int f must lie in (0, 2); at
-    B = 0.45 (ratio 2.2) the splitting tree grows without bound and hits
-    the node cap."""
-    t, i, nodes, tr = O.recip_1d(0, 0.45, 200, seed=1, cap=1 << 12)
-    assert tr > 20
+    B = 0.45 (ratio 2.2) the splitting tree of the paper's walk (one B per
+    estimate) grows without bound and hits the node cap."""
+    try:
+        O.set_fixed_bound_default(1)
+        t, i, nodes, tr = O.recip_1d(0, 0.45, 200, seed=1, cap=1 << 12)
+        assert tr > 20
+    finally:
+        O.set_fixed_bound_default(0)
+
+
+def test_raise_rule_converges_and_stays_unbiased_outside_the_domain():
+    """The raise rule: a node whose f/q exceeds 2B (|g| > 1) hands its
+    children the bound B' = f/q, and its Taylor term is g / B'. Since
+    1/beta = 1/B + (1 - beta/B) / beta for every B, a node whose bound is
+    fixed before its draw keeps the estimate unbiased, and the children's
+    expected own terms (each 1/B') sum to g / B'.
+
+    fn 0 (f = 1 + sin(2 pi x) / 2, q = 1, beta = 1) at B = 0.45 lies outside
+    the convergence condition: the paper's walk never ends (above), while
+    the raised walk ends in every one of 400k runs. Both of its estimators
+    keep the mean 1 (Alg. I~ and Alg. I, whose node term is the node's own
+    1/B), with about 3 nodes per run. Keeping Alg. I~'s term g / B instead of
+    g / B' moves its mean to about -0.26, and giving Alg. I the term 1/B'
+    moves its mean to about 0.33: both hundreds of standard errors away.
+    fn 1 (f = 3 x^2) at B = 1.6 never draws f/q > 2B, so the estimates equal
+    the paper's walk bit for bit."""
+    t, i, nodes, tr = O.recip_1d(0, 0.45, 400000, seed=23, cap=1 << 16)
+    assert tr == 0
+    for est in (t, i):
+        bm = est.reshape(40, -1).mean(1)
+        se = bm.std(ddof=1) / math.sqrt(len(bm))
+        assert abs(est.mean() - 1.0) < 4 * se, (est.mean(), se)
+        assert se < 0.01
+    assert nodes.mean() < 8
+    try:
+        O.set_fixed_bound_default(1)
+        tf, ifx, nf, _ = O.recip_1d(1, 1.6, 50000, seed=29)
+    finally:
+        O.set_fixed_bound_default(0)
+    tr_, ir_, nr_, _ = O.recip_1d(1, 1.6, 50000, seed=29)
+    np.testing.assert_array_equal(tf, tr_)
+    np.testing.assert_array_equal(ifx, ir_)
+    np.testing.assert_array_equal(nf, nr_)
 
 
 # --- materials -------------------------------------------------------------------
