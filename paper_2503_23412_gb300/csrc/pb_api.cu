@@ -365,13 +365,6 @@ pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *d) {
     if (d->tex_w > 0 && (!d->tex || d->tex_h <= 0)) return fail(ctx, PB_ERR_ARG, "scene: texture size without data");
     CK(cudaSetDevice(ctx->device));
     CK(cudaStreamSynchronize(ctx->stream));
-    free_graphs(ctx);   // captured renders point into the buffers replaced here
-    free_all(ctx->scene_mem);
-    free_all(ctx->pool_mem);
-    ctx->cap_slots = ctx->cap_ML = 0;
-    ctx->Lbuf = nullptr;
-    ctx->sigbuf = nullptr;
-    ctx->has_scene = false;
     int nt = d->nt;
     PbBvh bvh;
     int nn = pb_bvh_build(d->verts, d->nv, d->tris, nt, &bvh);
@@ -464,27 +457,66 @@ pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *d) {
     }
     DScene S{};
     auto &o = ctx->scene_mem;
-    float4 *nodes;
-    CK(upload(ctx, o, &nodes, reinterpret_cast<const float4 *>(bvh.nodes.data()), 4 * (size_t)nn));
-    int *par, *sib;
-    CK(upload(ctx, o, &par, bvh.parent.data(), (size_t)nn));
-    CK(upload(ctx, o, &sib, bvh.sibling.data(), (size_t)nn));
-    float4 *it_, *st_;
-    CK(upload(ctx, o, &it_, itri.data(), itri.size()));
-    CK(upload(ctx, o, &st_, stri.data(), stri.size()));
-    float *uvd;
-    CK(upload(ctx, o, &uvd, uv.data(), uv.size()));
-    DMat *md;
-    CK(upload(ctx, o, &md, mats.data(), mats.size()));
-    float *texd = nullptr;
-    if (d->tex_w > 0) CK(upload(ctx, o, &texd, d->tex, 3 * (size_t)d->tex_w * d->tex_h));
-    float *ecd, *epd;
-    int *etd;
-    CK(upload(ctx, o, &ecd, ecdf.data(), ecdf.size()));
-    CK(upload(ctx, o, &epd, epmf.data(), epmf.size()));
     std::vector<int> etv(etri);
     if (etv.empty()) etv.push_back(0);
-    CK(upload(ctx, o, &etd, etv.data(), etv.size()));
+    const int tw = d->tex_w > 0 ? d->tex_w : 0, th = d->tex_w > 0 ? d->tex_h : 0;
+    // A scene with the layout of the current one (same counts and resolution) is copied into the
+    // current buffers: the pool, the film and the captured renders stay valid, and are freed only
+    // if the scene's own parameters (camera, epsilon) changed. Any other scene replaces them all.
+    const bool reuse = ctx->has_scene && ctx->S.nnodes == nn && ctx->S.nt == nt && ctx->S.ne == ne &&
+                       ctx->scene_nm == d->nm && ctx->S.tw == tw && ctx->S.th == th && ctx->S.W == W &&
+                       ctx->S.H == H;
+    float4 *nodes, *it_, *st_;
+    int *par, *sib, *etd;
+    float *uvd, *texd = nullptr, *ecd, *epd;
+    DMat *md;
+    if (reuse) {
+        const DScene &C = ctx->S;   // the context's own buffers (DScene holds them as const)
+        nodes = const_cast<float4 *>(C.nodes);
+        par = const_cast<int *>(C.parent);
+        sib = const_cast<int *>(C.sibling);
+        it_ = const_cast<float4 *>(C.itri);
+        st_ = const_cast<float4 *>(C.stri);
+        uvd = const_cast<float *>(C.uv);
+        md = const_cast<DMat *>(C.mats);
+        texd = const_cast<float *>(C.tex);
+        ecd = const_cast<float *>(C.ecdf);
+        epd = const_cast<float *>(C.epmf);
+        etd = const_cast<int *>(C.etri);
+        auto put = [&](void *dst, const void *src, size_t bytes) {
+            return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream) : cudaSuccess;
+        };
+        CK(put(nodes, bvh.nodes.data(), 64 * (size_t)nn));
+        CK(put(par, bvh.parent.data(), 4 * (size_t)nn));
+        CK(put(sib, bvh.sibling.data(), 4 * (size_t)nn));
+        CK(put(it_, itri.data(), sizeof(float4) * itri.size()));
+        CK(put(st_, stri.data(), sizeof(float4) * stri.size()));
+        CK(put(uvd, uv.data(), 4 * uv.size()));
+        CK(put(md, mats.data(), sizeof(DMat) * mats.size()));
+        if (tw > 0) CK(put(texd, d->tex, 12 * (size_t)tw * th));
+        CK(put(ecd, ecdf.data(), 4 * ecdf.size()));
+        CK(put(epd, epmf.data(), 4 * epmf.size()));
+        CK(put(etd, etv.data(), 4 * etv.size()));
+    } else {
+        free_graphs(ctx);   // captured renders point into the buffers replaced here
+        free_all(ctx->scene_mem);
+        free_all(ctx->pool_mem);
+        ctx->cap_slots = ctx->cap_ML = 0;
+        ctx->Lbuf = nullptr;
+        ctx->sigbuf = nullptr;
+        ctx->has_scene = false;
+        CK(upload(ctx, o, &nodes, reinterpret_cast<const float4 *>(bvh.nodes.data()), 4 * (size_t)nn));
+        CK(upload(ctx, o, &par, bvh.parent.data(), (size_t)nn));
+        CK(upload(ctx, o, &sib, bvh.sibling.data(), (size_t)nn));
+        CK(upload(ctx, o, &it_, itri.data(), itri.size()));
+        CK(upload(ctx, o, &st_, stri.data(), stri.size()));
+        CK(upload(ctx, o, &uvd, uv.data(), uv.size()));
+        CK(upload(ctx, o, &md, mats.data(), mats.size()));
+        if (tw > 0) CK(upload(ctx, o, &texd, d->tex, 3 * (size_t)tw * th));
+        CK(upload(ctx, o, &ecd, ecdf.data(), ecdf.size()));
+        CK(upload(ctx, o, &epd, epmf.data(), epmf.size()));
+        CK(upload(ctx, o, &etd, etv.data(), etv.size()));
+    }
     S.nodes = nodes;
     S.parent = par;
     S.sibling = sib;
@@ -499,8 +531,8 @@ pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *d) {
     S.nt = nt;
     S.nnodes = nn;
     S.ne = ne;
-    S.tw = d->tex_w > 0 ? d->tex_w : 0;
-    S.th = d->tex_w > 0 ? d->tex_h : 0;
+    S.tw = tw;
+    S.th = th;
     S.W = W;
     S.H = H;
     float ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
@@ -522,13 +554,23 @@ pb_status pb_scene_upload(pb_ctx *ctx, const pb_scene_desc *d) {
     S.cup = make_float3((float)ux, (float)uy, (float)uz);
     S.tanh_ = (float)std::tan(0.5 * (double)c[9] * M_PI / 180.0);
     S.aspect = (float)W / (float)H;
-    S.lo = make_float3(0, 0, 0);
-    S.ext = make_float3(1, 1, 1);
+    if (reuse) {
+        // the feature box comes with the tables; keep the current one
+        S.lo = ctx->S.lo;
+        S.ext = ctx->S.ext;
+        if (std::memcmp(&S, &ctx->S, sizeof(DScene)) != 0) free_graphs(ctx);
+    } else {
+        S.lo = make_float3(0, 0, 0);
+        S.ext = make_float3(1, 1, 1);
+    }
     ctx->S = S;
+    ctx->scene_nm = d->nm;
     CK(cudaStreamSynchronize(ctx->stream));
-    if (ctx->film) cudaFree(ctx->film);
-    ctx->film = nullptr;
-    CK(cudaMalloc(&ctx->film, sizeof(float) * 3 * (size_t)W * H));
+    if (!reuse || !ctx->film) {
+        if (ctx->film) cudaFree(ctx->film);
+        ctx->film = nullptr;
+        CK(cudaMalloc(&ctx->film, sizeof(float) * 3 * (size_t)W * H));
+    }
     CK(cudaMemset(ctx->film, 0, sizeof(float) * 3 * (size_t)W * H));
     ctx->film_iters = 0;
     ctx->has_scene = true;
@@ -548,29 +590,54 @@ pb_status pb_tables_upload(pb_ctx *ctx, const pb_tables_desc *t) {
     for (int i = 0; i < ncell; ++i)
         if (!(t->B_tab[i] > 0.0f)) return fail(ctx, PB_ERR_ARG, "tables: B must be positive");
     CK(cudaStreamSynchronize(ctx->stream));
-    free_graphs(ctx);   // captured renders point into the buffers replaced here
-    free_all(ctx->table_mem);
+    // tables of the current sizes are copied into the current buffers (captured renders stay valid
+    // unless the feature box or the tile changed); other sizes replace them
+    const DTables &C = ctx->T;
+    const bool reuse = ctx->has_tables && C.KT == t->KT && C.KS == t->KS && C.KSp == t->KSp && C.KC == t->KC &&
+                       C.gw == gw && C.gh == gh;
     DTables T{};
     T.KT = t->KT; T.KS = t->KS; T.KSp = t->KSp; T.KC = t->KC;
-    auto &o = ctx->table_mem;
-    float *p;
-    CK(upload(ctx, o, &p, t->cent_T, (size_t)t->KT * 9)); T.cT = p;
-    CK(upload(ctx, o, &p, t->cent_S, (size_t)t->KS * 9)); T.cS = p;
-    CK(upload(ctx, o, &p, t->cent_Sp, (size_t)t->KSp * 6)); T.cSp = p;
-    CK(upload(ctx, o, &p, t->cent_C, (size_t)t->KC * 3)); T.cC = p;
-    CK(upload(ctx, o, &p, t->gamma_conn, (size_t)t->KT * t->KS)); T.gC = p;
-    CK(upload(ctx, o, &p, t->gamma_proxy, (size_t)t->KT * t->KSp)); T.gP = p;
-    CK(upload(ctx, o, &p, t->B_tab, (size_t)ncell)); T.Bt = p;
-    CK(upload(ctx, o, &p, t->mis_tab, (size_t)ncell)); T.mis = p;
-    CK(upload(ctx, o, &p, t->pi_grid, (size_t)gw * gh)); T.pi = p;
+    if (reuse) {
+        T = C;
+        auto put = [&](const float *dst, const float *src, size_t n) {   // the context's own table buffers
+            return cudaMemcpyAsync(const_cast<float *>(dst), src, 4 * n, cudaMemcpyHostToDevice, ctx->stream);
+        };
+        CK(put(T.cT, t->cent_T, (size_t)t->KT * 9));
+        CK(put(T.cS, t->cent_S, (size_t)t->KS * 9));
+        CK(put(T.cSp, t->cent_Sp, (size_t)t->KSp * 6));
+        CK(put(T.cC, t->cent_C, (size_t)t->KC * 3));
+        CK(put(T.gC, t->gamma_conn, (size_t)t->KT * t->KS));
+        CK(put(T.gP, t->gamma_proxy, (size_t)t->KT * t->KSp));
+        CK(put(T.Bt, t->B_tab, (size_t)ncell));
+        CK(put(T.mis, t->mis_tab, (size_t)ncell));
+        CK(put(T.pi, t->pi_grid, (size_t)gw * gh));
+    } else {
+        free_graphs(ctx);   // captured renders point into the buffers replaced here
+        free_all(ctx->table_mem);
+        auto &o = ctx->table_mem;
+        float *p;
+        CK(upload(ctx, o, &p, t->cent_T, (size_t)t->KT * 9)); T.cT = p;
+        CK(upload(ctx, o, &p, t->cent_S, (size_t)t->KS * 9)); T.cS = p;
+        CK(upload(ctx, o, &p, t->cent_Sp, (size_t)t->KSp * 6)); T.cSp = p;
+        CK(upload(ctx, o, &p, t->cent_C, (size_t)t->KC * 3)); T.cC = p;
+        CK(upload(ctx, o, &p, t->gamma_conn, (size_t)t->KT * t->KS)); T.gC = p;
+        CK(upload(ctx, o, &p, t->gamma_proxy, (size_t)t->KT * t->KSp)); T.gP = p;
+        CK(upload(ctx, o, &p, t->B_tab, (size_t)ncell)); T.Bt = p;
+        CK(upload(ctx, o, &p, t->mis_tab, (size_t)ncell)); T.mis = p;
+        CK(upload(ctx, o, &p, t->pi_grid, (size_t)gw * gh)); T.pi = p;
+    }
     T.tile = t->tile;
     T.gw = gw;
     T.gh = gh;
-    ctx->T = T;
     float3 lo = make_float3(t->bbox_lo[0], t->bbox_lo[1], t->bbox_lo[2]);
     float ex = t->bbox_hi[0] - t->bbox_lo[0], ey = t->bbox_hi[1] - t->bbox_lo[1], ez = t->bbox_hi[2] - t->bbox_lo[2];
+    const float3 ext = make_float3(ex > 0 ? ex : 1.0f, ey > 0 ? ey : 1.0f, ez > 0 ? ez : 1.0f);
+    if (reuse && (T.tile != C.tile || std::memcmp(&lo, &ctx->S.lo, sizeof(float3)) != 0 ||
+                  std::memcmp(&ext, &ctx->S.ext, sizeof(float3)) != 0))
+        free_graphs(ctx);
+    ctx->T = T;
     ctx->S.lo = lo;
-    ctx->S.ext = make_float3(ex > 0 ? ex : 1.0f, ey > 0 ? ey : 1.0f, ez > 0 ? ez : 1.0f);
+    ctx->S.ext = ext;
     // pool buffers that depend on the table sizes are re-checked by ensure_pool
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->has_tables = true;

@@ -2,6 +2,13 @@
 // axis over centroid bounds), leaves of at most 4 triangles (up to 15 when
 // the depth limit forces a leaf), depth <= 60 so a 64-bit trail holds a path.
 //
+// The build runs on the host's cores: the two subtrees of a node are built on
+// separate threads near the root, and a range of at least 2^16 triangles
+// computes its bounds, bins and stable partition in parallel parts (min/max
+// and counts reduce exactly). The split of a range depends only on the range,
+// so the tree is the same for any thread count, and internal nodes are
+// numbered in pre-order (a node, then its left subtree, then its right).
+//
 // Node layout (64 bytes = 4 x float4, child boxes stored in the parent so one
 // fetch tests both children):
 //   n0 = (left.lo.xyz,  left child)    n1 = (left.hi.xyz,  right child)
@@ -10,9 +17,14 @@
 // v = -child - 1, first = v >> 4 (index into the leaf-ordered triangle
 // arrays), count = v & 15. parent[] and sibling[] drive the backtracking.
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <cstdint>
 #include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "pb_bvh.h"
@@ -41,59 +53,111 @@ struct Box {
     }
 };
 
+constexpr int PAR_MIN = 1 << 16;     // ranges at least this long split their passes over threads
+constexpr int SPAWN_MIN = 1 << 13;   // subtrees at least this large may start a thread
+constexpr int NB = 16;                // SAH bins per axis
+
 struct Build {
     const float *V;
     const int32_t *T;
     std::vector<Box> tbox;
     std::vector<float> cen;   // 3 per tri
-    std::vector<int32_t> idx;
-    std::vector<float> nodes;  // 16 floats per node
-    std::vector<int32_t> parent, sibling;
+    std::vector<int32_t> idx, tmp;
+    int nth;                  // threads the build may use
+    std::atomic<int> running{1};   // threads working now (one waiting on a join does not count)
 };
 
 int32_t leaf_code(int first, int count) { return -(first * 16 + count) - 1; }
 
-void set_child(Build &b, int node, int side, const Box &bx, int32_t code) {
-    float *n = &b.nodes[(size_t)node * 16];
-    float *lo = side == 0 ? n + 0 : n + 8;
-    float *hi = side == 0 ? n + 4 : n + 12;
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = bx.lo[a];
-        hi[a] = bx.hi[a];
+// f(part, lo, hi) over [0, n) in `parts` contiguous parts, parts > 1 on threads
+template <class F>
+void par_parts(int parts, int n, F f) {
+    if (parts <= 1) {
+        f(0, 0, n);
+        return;
     }
-    int32_t *w = reinterpret_cast<int32_t *>(side == 0 ? n + 3 : n + 7);
-    *w = code;
+    std::vector<std::thread> th;
+    for (int q = 1; q < parts; ++q)
+        th.emplace_back(f, q, (int)((int64_t)n * q / parts), (int)((int64_t)n * (q + 1) / parts));
+    f(0, 0, (int)((int64_t)n / parts));
+    for (auto &t : th) t.join();
 }
 
-struct Task { int node, side, first, count, depth; };
+int parts_for(int count, int nt) { return count >= PAR_MIN ? std::max(1, std::min(nt, count / (PAR_MIN / 4))) : 1; }
+// threads for one range's passes: the idle ones plus the caller
+int range_threads(Build &b) { return std::max(1, b.nth - b.running.load() + 1); }
 
-Box range_box(const Build &b, int first, int count) {
+Box range_box(const Build &b, int first, int count, int nt) {
+    const int parts = parts_for(count, nt);
+    std::vector<Box> part(parts);
+    par_parts(parts, count, [&](int q, int lo, int hi) {
+        for (int i = first + lo; i < first + hi; ++i) part[q].grow(b.tbox[b.idx[i]]);
+    });
     Box bx;
-    for (int i = first; i < first + count; ++i) bx.grow(b.tbox[b.idx[i]]);
+    for (const Box &x : part) bx.grow(x);
     return bx;
 }
 
-// choose a split of idx[first, first+count); returns split position or -1 for a leaf
-int split(Build &b, int first, int count, int depth) {
+inline int bin_of(float c, float lo, float ext) {
+    int k = (int)((c - lo) / ext * NB);
+    return std::min(std::max(k, 0), NB - 1);
+}
+
+struct Bins {
+    Box box[3][NB];
+    int cnt[3][NB];
+};
+
+void bin_range(const Build &b, int lo, int hi, const Box &cb, const float *ext, Bins &B) {
+    std::memset(B.cnt, 0, sizeof(B.cnt));
+    for (int i = lo; i < hi; ++i) {
+        const int t = b.idx[i];
+        const Box &tb = b.tbox[t];
+        for (int a = 0; a < 3; ++a) {
+            if (!(ext[a] > 0.0f)) continue;
+            const int k = bin_of(b.cen[3 * (size_t)t + a], cb.lo[a], ext[a]);
+            B.cnt[a][k]++;
+            B.box[a][k].grow(tb);
+        }
+    }
+}
+
+// choose a split of idx[first, first+count), whose triangles' bounds are pb;
+// returns the split position or -1 for a leaf
+int split(Build &b, int first, int count, int depth, int nt, const Box &pb) {
     const int maxleaf = 4;
     if (count <= maxleaf) return -1;
+    const int parts = parts_for(count, nt);
+    // centroid bounds
     Box cb;
-    for (int i = first; i < first + count; ++i) cb.grow(&b.cen[3 * (size_t)b.idx[i]]);
-    const int NB = 16;
+    if (parts == 1) {
+        for (int i = first; i < first + count; ++i) cb.grow(&b.cen[3 * (size_t)b.idx[i]]);
+    } else {
+        std::vector<Box> pcb(parts);
+        par_parts(parts, count, [&](int q, int lo, int hi) {
+            for (int i = first + lo; i < first + hi; ++i) pcb[q].grow(&b.cen[3 * (size_t)b.idx[i]]);
+        });
+        for (const Box &x : pcb) cb.grow(x);
+    }
+    // bins of all three axes (per part, then reduced)
+    float ext[3];
+    for (int a = 0; a < 3; ++a) ext[a] = cb.hi[a] - cb.lo[a];
+    Bins one;
+    std::vector<Bins> pb_(parts > 1 ? parts : 0);
+    if (parts == 1) bin_range(b, first, first + count, cb, ext, one);
+    else par_parts(parts, count, [&](int q, int lo, int hi) { bin_range(b, first + lo, first + hi, cb, ext, pb_[q]); });
+    const Bins *bins_of = parts == 1 ? &one : pb_.data();
     double best = DBL_MAX;
     int best_axis = -1, best_bin = -1;
     for (int a = 0; a < 3; ++a) {
-        float ext = cb.hi[a] - cb.lo[a];
-        if (!(ext > 0.0f)) continue;
+        if (!(ext[a] > 0.0f)) continue;
         Box bins[NB];
         int cnt[NB] = {0};
-        for (int i = first; i < first + count; ++i) {
-            int t = b.idx[i];
-            int k = (int)((b.cen[3 * (size_t)t + a] - cb.lo[a]) / ext * NB);
-            k = std::min(std::max(k, 0), NB - 1);
-            cnt[k]++;
-            bins[k].grow(b.tbox[t]);
-        }
+        for (int q = 0; q < parts; ++q)
+            for (int k = 0; k < NB; ++k) {
+                bins[k].grow(bins_of[q].box[a][k]);
+                cnt[k] += bins_of[q].cnt[a][k];
+            }
         double la[NB], ra[NB];
         int lc[NB], rc[NB];
         Box acc;
@@ -122,19 +186,47 @@ int split(Build &b, int first, int count, int depth) {
             }
         }
     }
-    Box pb = range_box(b, first, count);
     double leaf_cost = pb.area() * count;
     bool force = depth >= 58 || best_axis < 0;
     if (!force && count <= 15 && leaf_cost <= best + pb.area() * 1.0) return -1;
     int mid;
     if (best_axis >= 0 && !(depth >= 58)) {
-        float ext = cb.hi[best_axis] - cb.lo[best_axis];
-        auto it = std::stable_partition(b.idx.begin() + first, b.idx.begin() + first + count, [&](int t) {
-            int k = (int)((b.cen[3 * (size_t)t + best_axis] - cb.lo[best_axis]) / ext * NB);
-            k = std::min(std::max(k, 0), NB - 1);
-            return k <= best_bin;
-        });
-        mid = (int)(it - b.idx.begin());
+        const int a = best_axis;
+        auto left = [&](int t) { return bin_of(b.cen[3 * (size_t)t + a], cb.lo[a], ext[a]) <= best_bin; };
+        if (parts == 1) {
+            auto it = std::stable_partition(b.idx.begin() + first, b.idx.begin() + first + count, left);
+            mid = (int)(it - b.idx.begin());
+        } else {
+            // stable partition in parts: count, place by prefix sums, copy back
+            std::vector<int> nl(parts, 0);
+            par_parts(parts, count, [&](int q, int lo, int hi) {
+                int c = 0;
+                for (int i = first + lo; i < first + hi; ++i) c += left(b.idx[i]) ? 1 : 0;
+                nl[q] = c;
+            });
+            int tot = 0;
+            std::vector<int> lb(parts), rb(parts);
+            for (int q = 0; q < parts; ++q) {
+                lb[q] = tot;
+                tot += nl[q];
+            }
+            for (int q = 0, r = 0; q < parts; ++q) {
+                rb[q] = tot + r;
+                r += (int)((int64_t)count * (q + 1) / parts - (int64_t)count * q / parts) - nl[q];
+            }
+            par_parts(parts, count, [&](int q, int lo, int hi) {
+                int l = first + lb[q], r = first + rb[q];
+                for (int i = first + lo; i < first + hi; ++i) {
+                    int t = b.idx[i];
+                    if (left(t)) b.tmp[l++] = t;
+                    else b.tmp[r++] = t;
+                }
+            });
+            par_parts(parts, count, [&](int, int lo, int hi) {
+                std::memcpy(&b.idx[first + lo], &b.tmp[first + lo], sizeof(int32_t) * (size_t)(hi - lo));
+            });
+            mid = first + tot;
+        }
     } else {
         // degenerate centroids or depth limit: median split by index
         if (count <= 15) return -1;
@@ -142,6 +234,105 @@ int split(Build &b, int first, int count, int depth) {
     }
     if (mid <= first || mid >= first + count) mid = first + count / 2;
     return mid;
+}
+
+// The tree before numbering: a child is a leaf code or an internal node held
+// in the arena of the thread that built it.
+struct TNode;
+struct Arena {
+    std::vector<TNode> v;
+};
+struct Ref {
+    Box box;
+    int32_t code;   // leaf code when ar == nullptr
+    Arena *ar;
+    int ix;
+};
+struct TNode {
+    Ref ch[2];
+};
+
+struct Arenas {
+    std::mutex mu;
+    std::deque<std::unique_ptr<Arena>> all;
+    Arena *make() {
+        std::lock_guard<std::mutex> g(mu);
+        all.push_back(std::make_unique<Arena>());
+        return all.back().get();
+    }
+};
+
+// the subtree over idx[first, first+count) at `depth`; the left subtree of a
+// large range goes to a new thread while fewer than nth threads are running
+Ref build(Build &b, Arenas &as, Arena *ar, int first, int count, int depth) {
+    Ref r;
+    const int nt = count >= PAR_MIN ? range_threads(b) : 1;
+    r.box = range_box(b, first, count, nt);
+    r.ar = nullptr;
+    r.ix = -1;
+    int m = split(b, first, count, depth, nt, r.box);
+    if (m < 0) {
+        r.code = leaf_code(first, count);
+        return r;
+    }
+    TNode nd;
+    bool spawn = false;
+    if (std::min(m - first, first + count - m) >= SPAWN_MIN) {
+        int cur = b.running.load();
+        while (cur < b.nth && !b.running.compare_exchange_weak(cur, cur + 1)) {
+        }
+        spawn = cur < b.nth;
+    }
+    if (spawn) {
+        Arena *la = as.make();
+        std::thread t([&]() {
+            nd.ch[0] = build(b, as, la, first, m - first, depth + 1);
+            b.running.fetch_sub(1);
+        });
+        nd.ch[1] = build(b, as, ar, m, first + count - m, depth + 1);
+        b.running.fetch_sub(1);   // idle while it waits
+        t.join();
+        b.running.fetch_add(1);
+    } else {
+        nd.ch[0] = build(b, as, ar, first, m - first, depth + 1);
+        nd.ch[1] = build(b, as, ar, m, first + count - m, depth + 1);
+    }
+    ar->v.push_back(nd);
+    r.code = 0;
+    r.ar = ar;
+    r.ix = (int)ar->v.size() - 1;
+    return r;
+}
+
+struct Emit {
+    std::vector<float> nodes;  // 16 floats per node
+    std::vector<int32_t> parent, sibling;
+};
+
+void set_child(Emit &e, int node, int side, const Box &bx, int32_t code) {
+    float *n = &e.nodes[(size_t)node * 16];
+    float *lo = side == 0 ? n + 0 : n + 8;
+    float *hi = side == 0 ? n + 4 : n + 12;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = bx.lo[a];
+        hi[a] = bx.hi[a];
+    }
+    int32_t *w = reinterpret_cast<int32_t *>(side == 0 ? n + 3 : n + 7);
+    *w = code;
+}
+
+// numbers internal nodes in pre-order and writes the 64-byte layout
+int emit(Emit &e, const TNode &nd, int parent) {
+    const int id = (int)e.parent.size();
+    e.nodes.resize(e.nodes.size() + 16, 0.0f);
+    e.parent.push_back(parent);
+    e.sibling.push_back(-1);
+    for (int s = 0; s < 2; ++s) {
+        const Ref &c = nd.ch[s];
+        const int32_t code = c.ar ? emit(e, c.ar->v[c.ix], id) : c.code;
+        set_child(e, id, s, c.box, code);
+    }
+    return id;
 }
 
 }  // namespace
@@ -154,62 +345,50 @@ int pb_bvh_build(const float *verts, int nv, const int32_t *tris, int nt, PbBvh 
     b.tbox.resize(nt);
     b.cen.resize(3 * (size_t)nt);
     b.idx.resize(nt);
-    for (int t = 0; t < nt; ++t) {
-        Box bx;
-        for (int k = 0; k < 3; ++k) bx.grow(&verts[3 * (size_t)tris[3 * (size_t)t + k]]);
-        b.tbox[t] = bx;
-        for (int a = 0; a < 3; ++a) b.cen[3 * (size_t)t + a] = 0.5f * (bx.lo[a] + bx.hi[a]);
-        b.idx[t] = t;
-    }
-    b.nodes.reserve(16 * (size_t)std::max(1, nt));
-    b.nodes.assign(16, 0.0f);
-    b.parent.push_back(-1);
-    b.sibling.push_back(-1);
-    // root is always an internal node; its children come from splitting all triangles
-    std::vector<Task> stack;
-    int mid = split(b, 0, nt, 0);
-    if (mid < 0) {
-        set_child(b, 0, 0, range_box(b, 0, nt), leaf_code(0, nt));
-        set_child(b, 0, 1, Box(), leaf_code(0, 0));
-    } else {
-        stack.push_back({0, 1, mid, nt - mid, 1});
-        stack.push_back({0, 0, 0, mid, 1});
-    }
-    std::vector<int> child_of[2];
-    while (!stack.empty()) {
-        Task tk = stack.back();
-        stack.pop_back();
-        Box bx = range_box(b, tk.first, tk.count);
-        int m = split(b, tk.first, tk.count, tk.depth);
-        if (m < 0) {
-            set_child(b, tk.node, tk.side, bx, leaf_code(tk.first, tk.count));
-            continue;
+    b.tmp.resize(nt);
+    const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    b.nth = nth;
+    par_parts(parts_for(nt, nth), nt, [&](int, int lo, int hi) {
+        for (int t = lo; t < hi; ++t) {
+            Box bx;
+            for (int k = 0; k < 3; ++k) bx.grow(&verts[3 * (size_t)tris[3 * (size_t)t + k]]);
+            b.tbox[t] = bx;
+            for (int a = 0; a < 3; ++a) b.cen[3 * (size_t)t + a] = 0.5f * (bx.lo[a] + bx.hi[a]);
+            b.idx[t] = t;
         }
-        int id = (int)(b.nodes.size() / 16);
-        b.nodes.resize(b.nodes.size() + 16, 0.0f);
-        b.parent.push_back(tk.node);
-        b.sibling.push_back(-1);
-        set_child(b, tk.node, tk.side, bx, id);
-        stack.push_back({id, 1, m, tk.first + tk.count - m, tk.depth + 1});
-        stack.push_back({id, 0, tk.first, m - tk.first, tk.depth + 1});
+    });
+    Emit e;
+    e.nodes.reserve(16 * (size_t)std::max(1, nt / 2));
+    // the root is always an internal node; its children come from splitting all triangles
+    Arenas as;
+    Arena *root_ar = as.make();
+    Ref root = build(b, as, root_ar, 0, nt, 0);
+    if (!root.ar) {
+        e.nodes.assign(16, 0.0f);
+        e.parent.push_back(-1);
+        e.sibling.push_back(-1);
+        set_child(e, 0, 0, root.box, leaf_code(0, nt));
+        set_child(e, 0, 1, Box(), leaf_code(0, 0));
+    } else {
+        emit(e, root.ar->v[root.ix], -1);
     }
-    int nn = (int)(b.nodes.size() / 16);
+    int nn = (int)(e.nodes.size() / 16);
     // sibling of each internal child
     for (int n = 0; n < nn; ++n) {
-        const int32_t *w = reinterpret_cast<const int32_t *>(&b.nodes[(size_t)n * 16]);
+        const int32_t *w = reinterpret_cast<const int32_t *>(&e.nodes[(size_t)n * 16]);
         int32_t l = w[3], r = w[7];
         if (l >= 0 && r >= 0) {
-            b.sibling[l] = r;
-            b.sibling[r] = l;
+            e.sibling[l] = r;
+            e.sibling[r] = l;
         } else if (l >= 0) {
-            b.sibling[l] = -1;
+            e.sibling[l] = -1;
         } else if (r >= 0) {
-            b.sibling[r] = -1;
+            e.sibling[r] = -1;
         }
     }
-    out->nodes = std::move(b.nodes);
-    out->parent = std::move(b.parent);
-    out->sibling = std::move(b.sibling);
+    out->nodes = std::move(e.nodes);
+    out->parent = std::move(e.parent);
+    out->sibling = std::move(e.sibling);
     out->order = std::move(b.idx);
     return nn;
 }

@@ -52,6 +52,7 @@ struct pb_ctx {
     std::string err;
     std::vector<void *> scene_mem, table_mem, pool_mem;
     bool has_scene = false, has_tables = false;
+    int scene_nm = 0;    // materials of the uploaded scene
     DScene S{};
     DTables T{};
     float3 scene_lo{}, scene_hi{};
