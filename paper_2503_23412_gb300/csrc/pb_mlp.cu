@@ -167,6 +167,7 @@ struct SelArgs {
     int32_t *sel;
     float *selq;
     int udim;                // camera dimension of the selection uniform (6 connection, 9 proxy)
+    int tcols;               // TMEM columns the CTA allocates (128, 256 or 512)
     // logits mode
     float *logits;           // nrows x K
     int *err;
@@ -183,8 +184,13 @@ __device__ __forceinline__ int select_cdf_row(const float *cdf, int K, float u) 
 }
 
 // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. (the rows of its quarter)
-// and handles half h = w / 4 of each accumulator's columns
+// and handles half h = w / 4 of each accumulator's columns. TMEM: layer 1 in
+// columns 0..63, layer 2 in 64..127, layer 3 from column 0 again (both hidden
+// accumulators are read before its MMAs start), so a CTA needs
+// max(128, Kpad) columns, rounded up to a power of two, and small networks
+// fit several CTAs on an SM.
 constexpr int SEL_THREADS = 256;
+__host__ __device__ inline int sel_tcols(int Kpad) { return Kpad <= 128 ? 128 : (Kpad <= 256 ? 256 : 512); }
 constexpr int MASK_WORDS = MLP_KMAX / 32;
 constexpr int MAX_SLOTS = 64;
 
@@ -238,7 +244,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, int col0, int
 }
 
 template <bool LOGITS>
-__global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
+__global__ void __launch_bounds__(SEL_THREADS, 2) k_mlp_select(SelArgs a) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, half = warp >> 2;
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(512)
+                     "r"(a.tcols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
     tc_after();
     const uint32_t tmem = *tslot;
     const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);   // this warp's TMEM lanes
-    const uint32_t d1 = tmem, d2 = tmem + 64, d3 = tmem + 128;
+    const uint32_t d1 = tmem, d2 = tmem + 64, d3 = tmem;
     const uint32_t sa1 = smem_u32(a1), sa23 = smem_u32(a23);
     const uint32_t sw1 = smem_u32(sm + IL.w1), sw2 = smem_u32(sm + IL.w2), sw3 = smem_u32(sm + IL.w3);
     const uint64_t TIMEOUT = 1000000000ull;   // 1 s per wait
@@ -319,6 +325,28 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
             umma_commit(bar);
         }
         pending = true;
+        // while the MMAs run: this row's cell, position and uniform, and the
+        // table draw (none of them depends on the logits)
+        const long long row = tile * TILE_M + r;
+        const bool inrow = row < nrows;
+        int T = -1, pos = 0, slot = 0, av = 0, pix = 0, gpick = -1;
+        float u = 0.0f;
+        if (!LOGITS && inrow) {
+            T = a.rowT[row];
+            pos = a.rowPos[row];
+            const long long per_slot = (long long)a.A * a.npix;
+            slot = (int)(pos / per_slot);
+            const long long rem = pos - (long long)slot * per_slot;
+            av = (int)(rem / a.npix) + 1;
+            pix = (int)(rem % a.npix);
+            if (T >= 0) {
+                Rng R;
+                const uint32_t ib = a.iter_dev ? a.iter_base + *a.iter_dev : a.iter_base;
+                R.init(a.seed, K_CAMERA, ib + (uint32_t)slot, (uint32_t)pix, (uint32_t)av);
+                u = R.u(a.udim);
+                if (u < MLP_EPS) gpick = select_cdf_row(a.cdfC + ((size_t)slot * a.KT + T) * a.K, a.K, u / MLP_EPS);
+            }
+        }
         if (mbar_wait(bar, phase, TIMEOUT)) {
             pending = false;
             phase ^= 1;
@@ -377,11 +405,10 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
         if (*abort_) break;
         tc_after();
         const float *b3 = sbias + MLP_H;
-        const long long row = tile * TILE_M + r;
         float v[32];
         if (LOGITS) {
             for (int c = c0; c < c1; ++c) {
-                tmem_ld32(trow + 128 + 32 * c, v);
+                tmem_ld32(trow + 32 * c, v);
                 if (row < nrows)
 #pragma unroll
                     for (int k = 0; k < 32; ++k) {
@@ -390,19 +417,12 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
                     }
             }
         } else {
-            const bool inrow = row < nrows;
-            const int T = inrow ? a.rowT[row] : -1;
-            const int pos = inrow ? a.rowPos[row] : 0;
-            const long long per_slot = (long long)a.A * a.npix;
-            const int slot = (int)(pos / per_slot);
-            const long long rem = pos - (long long)slot * per_slot;
-            const int av = (int)(rem / a.npix) + 1, pix = (int)(rem % a.npix);
             const uint32_t *mk = smask + slot * MASK_WORDS;
             // pass A over this half: online max and normaliser, last occupied subspace
             float m = -INFINITY, Z = 0.0f, vlast = 0.0f;
             int last = -1;
             for (int c = c0; c < c1; ++c) {
-                tmem_ld32(trow + 128 + 32 * c, v);
+                tmem_ld32(trow + 32 * c, v);
                 const uint32_t bits = mk[c];
                 float cm = -INFINITY;
 #pragma unroll
@@ -436,17 +456,10 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
             const float Zh1 = m1 == -INFINITY ? 0.0f : Q1[TILE_M + r] * __expf(m1 - mg);
             const float Zg = Zh0 + Zh1;
             const bool valid = T >= 0 && mg > -INFINITY;
-            // one uniform picks the mixture component and the subspace
-            int gpick = -1;
+            // one uniform picks the mixture component (the table row: gpick, drawn
+            // above) and the subspace
             float target = 0.0f;
-            if (valid) {
-                Rng R;
-                const uint32_t ib = a.iter_dev ? a.iter_base + *a.iter_dev : a.iter_base;
-                R.init(a.seed, K_CAMERA, ib + (uint32_t)slot, (uint32_t)pix, (uint32_t)av);
-                const float u = R.u(a.udim);
-                if (u < MLP_EPS) gpick = select_cdf_row(a.cdfC + ((size_t)slot * a.KT + T) * a.K, a.K, u / MLP_EPS);
-                else target = (u - MLP_EPS) / (1.0f - MLP_EPS) * Zg;
-            }
+            if (valid && gpick < 0) target = (u - MLP_EPS) / (1.0f - MLP_EPS) * Zg;
             // pass B over this half: the cumulative search (softmax branch, the
             // half that holds the target) or the drawn subspace's weight
             int pick = -1;
@@ -456,7 +469,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
             float cum = half ? Zh0 : 0.0f;
             for (int c = c0; c < c1; ++c) {
                 if (__all_sync(0xffffffffu, !mine || pick >= 0)) break;
-                tmem_ld32(trow + 128 + 32 * c, v);
+                tmem_ld32(trow + 32 * c, v);
                 if (!mine || pick >= 0) continue;
                 const uint32_t bits = mk[c];
 #pragma unroll
@@ -514,7 +527,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 1) k_mlp_select(SelArgs a) {
     __syncthreads();
     tc_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tcols) : "memory");
 }
 
 // ---- training (fp32, CUDA cores) -------------------------------------------
@@ -780,15 +793,20 @@ static pb_status set_select_attr(pb_ctx *ctx) {
 }
 
 static pb_status run_select(pb_ctx *ctx, SelArgs &a, bool device_count) {
-    // one CTA per SM: the kernel holds all 512 TMEM columns, and 120 KB of
-    // shared memory keeps a second CTA off the SM (the layout needs < 100 KB)
-    const int smem_req = 120 * 1024;
-    if ((int)sel_smem(a.Kpad).bytes > smem_req) return pb_fail(ctx, PB_ERR_ARG, "mlp: shared memory layout too large");
+    // as many CTAs per SM as registers, shared memory and TMEM columns allow
+    const int smem_req = (int)sel_smem(a.Kpad).bytes;
+    if (smem_req > 120 * 1024) return pb_fail(ctx, PB_ERR_ARG, "mlp: shared memory layout too large");
     pb_status s0 = set_select_attr(ctx);
     if (s0 != PB_OK) return s0;
+    a.tcols = sel_tcols(a.Kpad);
+    int occ = 1;
+    if (a.logits) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_select<true>, SEL_THREADS, smem_req));
+    else CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mlp_select<false>, SEL_THREADS, smem_req));
+    const int per_sm = std::max(1, std::min(occ, 512 / a.tcols));
     long long ntiles = (a.nrows + TILE_M - 1) / TILE_M;
-    // with the row count on the device every SM gets a CTA; idle ones exit at once
-    int grid = device_count ? ctx->num_sms : (int)std::min<long long>(ntiles, (long long)ctx->num_sms);
+    // with the row count on the device every CTA slot gets a CTA; idle ones exit at once
+    const long long slots_ = (long long)ctx->num_sms * per_sm;
+    int grid = device_count ? (int)slots_ : (int)std::min<long long>(ntiles, slots_);
     if (grid < 1) return PB_OK;
     if (a.logits) k_mlp_select<true><<<grid, SEL_THREADS, smem_req, ctx->stream>>>(a);
     else k_mlp_select<false><<<grid, SEL_THREADS, smem_req, ctx->stream>>>(a);
