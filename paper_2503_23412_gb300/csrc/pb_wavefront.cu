@@ -524,21 +524,26 @@ __global__ void __launch_bounds__(128) k_wf_trace_pt(DScene S, KParams P, Pool B
     }
 }
 
-// the exact sequential walk over nodes [o, o + cnt) of a window, on the
-// stack form (one thread)
-__device__ __forceinline__ void walk_seq(const KParams &P, const WfBufs &W, ChainState &gst, int o, int cnt, float invB,
-                                         int &next, double &sum_t, int &done, int &trunc) {
+// the exact sequential walk over cnt consecutive nodes (g, children, f/q and
+// RRS uniform of each), on the stack form (one thread)
+__device__ __forceinline__ void walk_seq_arr(const KParams &P, ChainState &st, const float *g, const int32_t *n,
+                                             const float *x, const float *u, int cnt, float invB, int &next,
+                                             double &sum_t, int &done, int &trunc) {
     for (int q = 0; q < cnt; ++q) {
-        const EstStep e = est_step(gst, W.node_x[o + q], W.node_u[o + q], W.node_g[o + q], W.node_n[o + q], invB,
-                                   (uint32_t)next, P);
+        const EstStep e = est_step(st, x[q], u[q], g[q], n[q], invB, (uint32_t)next, P);
         next += 1;
-        const int r = est_take<PB_MAXF>(gst, e, sum_t);
+        const int r = est_take<PB_MAXF>(st, e, sum_t);
         if (r) {
             done = 1;
             trunc = r == 2;
             return;
         }
     }
+}
+// the same over nodes [o, o + cnt) of a window, read from the node arrays
+__device__ __forceinline__ void walk_seq(const KParams &P, const WfBufs &W, ChainState &gst, int o, int cnt, float invB,
+                                         int &next, double &sum_t, int &done, int &trunc) {
+    walk_seq_arr(P, gst, W.node_g + o, W.node_n + o, W.node_x + o, W.node_u + o, cnt, invB, next, sum_t, done, trunc);
 }
 
 // windows at least this long are walked by a whole block (k_wf_walk_long)
@@ -656,9 +661,15 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
 // g on the count form is walked in parallel: a block scan of (n - 1) gives
 // every node's pending count, the chain ends at the first node where it
 // reaches 0, and the terms g / B up to there are summed by a block
-// reduction. Otherwise thread 0 walks the tile on the stack form.
+// reduction. Otherwise the block stages the tile's node values in shared
+// memory and thread 0 walks it on the stack form, which the block keeps in
+// shared memory for the whole window.
 constexpr int WF_LONG_THREADS = 256;
+constexpr int WF_LONG_TILE = 4 * WF_LONG_THREADS;
 __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Pool B, WfBufs W) {
+    __shared__ ChainState sst;
+    __shared__ float t_g[WF_LONG_TILE], t_x[WF_LONG_TILE], t_u[WF_LONG_TILE];
+    __shared__ int32_t t_n[WF_LONG_TILE];
     __shared__ int s_wsum[WF_LONG_THREADS / 32];
     __shared__ double s_wpart[WF_LONG_THREADS / 32];
     __shared__ int s_end, s_done, s_trunc, s_next, s_pend;
@@ -669,14 +680,16 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
         const int w = W.ch_w[c];
         if (W.ch_done[c] || w < WF_WALK_LONG) continue;   // uniform over the block
         ChainState &gst = B.chains[c];
-        const int slot = gst.slot, k = gst.k, rep = gst.rep;
-        const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
         const int off = W.ch_off[c];
+        if (tid == 0) sst = gst;
+        __syncthreads();
+        const int slot = sst.slot, k = sst.k, rep = sst.rep;
+        const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
         if (tid == 0) {
             int pend;
-            s_pend = est_count_form(gst, invB, pend) ? pend : -1;   // -1: the stack form holds the state
-            s_next = gst.next;
-            s_sum = gst.sum_t;
+            s_pend = est_count_form(sst, invB, pend) ? pend : -1;   // -1: the stack form holds the state
+            s_next = sst.next;
+            s_sum = sst.sum_t;
             s_done = 0;
             s_trunc = 0;
         }
@@ -748,19 +761,31 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
                 __syncthreads();
                 continue;
             }
-            // thread 0: the exact walk of this tile on the stack form
+            // the exact walk of this tile on the stack form: the block stages the
+            // tile, thread 0 walks it
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int jj = 4 * tid + i;
+                if (jj < cnt) {
+                    t_g[jj] = g[i];
+                    t_n[jj] = n[i];
+                    t_x[jj] = W.node_x[off + j0 + jj];
+                    t_u[jj] = W.node_u[off + j0 + jj];
+                }
+            }
+            __syncthreads();
             if (tid == 0) {
-                if (pend0 > 0) est_from_count(gst, pend0, invB);   // from the count form
+                if (pend0 > 0) est_from_count(sst, pend0, invB);   // from the count form
                 int next = s_next, done = 0, trunc = 0;
                 double sum_t = s_sum;
-                walk_seq(P, W, gst, off + j0, cnt, invB, next, sum_t, done, trunc);
+                walk_seq_arr(P, sst, t_g, t_n, t_x, t_u, cnt, invB, next, sum_t, done, trunc);
                 s_next = next;
                 s_sum = sum_t;
                 s_done = done;
                 s_trunc = trunc;
                 // back to the count form when the stack turned all-positive again
                 int pe;
-                s_pend = est_count_form(gst, invB, pe) ? pe : -1;
+                s_pend = est_count_form(sst, invB, pe) ? pe : -1;
             }
             __syncthreads();
         }
@@ -771,9 +796,10 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
                 done = 1;
                 trunc = 1;
             }
-            if (s_pend > 0) est_from_count(gst, s_pend, invB);   // store the count form as a one-frame stack
-            gst.next = next;
-            gst.sum_t = s_sum;
+            if (s_pend > 0) est_from_count(sst, s_pend, invB);   // store the count form as a one-frame stack
+            sst.next = next;
+            sst.sum_t = s_sum;
+            gst = sst;
             if (done) {
                 size_t o = ((size_t)slot * B.ML + k) * P.repeats + rep;
                 B.rep[o] = (float)((double)invB + s_sum);
