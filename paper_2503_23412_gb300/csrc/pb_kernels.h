@@ -224,6 +224,48 @@ __device__ __forceinline__ bool est_count_form(const St &st, float invB0, int &p
     }
     return pos;
 }
+// Whether the walk state is on the uniform count form: every pending node
+// (the current one and all frames) has one weight w and one inverse bound ib.
+// A run of nodes with g >= 0 under ib then keeps that form (their children
+// enter with weight w and bound ib), so the walk reduces to pending counts
+// and terms w g ib. pend = pending nodes, the current one included.
+template <class St>
+__device__ __forceinline__ bool est_uniform_form(const St &st, float &w, float &ib, int &pend) {
+    w = st.cur_sign;
+    ib = st.cur_ib;
+    pend = 1;
+    bool ok = true;
+    for (int f = 0; f < st.sp; ++f) {
+        ok = ok && st.fr_sign[f] == w && st.fr_ib[f] == ib;
+        pend += st.fr_rem[f];
+    }
+    return ok;
+}
+// the uniform form with `pend` pending nodes as a stack of at most one frame
+template <class St>
+__device__ __forceinline__ void est_from_uniform(St &st, int pend, float w, float ib) {
+    st.cur_sign = w;
+    st.cur_ib = ib;
+    st.sp = 0;
+    if (pend - 1 > 0) {
+        st.fr_sign[0] = w;
+        st.fr_ib[0] = ib;
+        st.fr_rem[0] = pend - 1;
+        st.sp = 1;
+    }
+}
+// g and children of a node under the inverse bound ib, as est_step computes
+// them (the values drawn under the estimate's own bound invB0 are reused)
+__device__ __forceinline__ void est_gn(float x, float u, float g0, int n0, float invB0, float ib, uint32_t v,
+                                       uint32_t split, float &g, int &n) {
+    if (ib == invB0) {
+        g = g0;
+        n = n0;
+    } else {
+        g = 1.0f - x * ib;
+        n = est_children(g, u, v, split);
+    }
+}
 // the count form with `pend` pending nodes as a stack of at most one frame
 template <class St>
 __device__ __forceinline__ void est_from_count(St &st, int pend, float invB0) {

@@ -567,10 +567,11 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
         const int off = W.ch_off[c];
         int next = gst.next;
         double sum_t = gst.sum_t;
-        // pending-count form of the walk state while every pending node has
-        // weight +1 under the estimate's own bound
+        // pending-count form of the walk state while every pending node has one
+        // weight uw and one inverse bound uib
         int pend;
-        bool stack_form = !est_count_form(gst, invB, pend);   // gst holds the authoritative stack
+        float uw, uib;
+        bool stack_form = !est_uniform_form(gst, uw, uib, pend);   // gst holds the authoritative stack
         int done = 0, trunc = 0;
         // four chunks are loaded ahead of their walk (128 nodes per trip)
         float gq[4];
@@ -595,6 +596,8 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
                     g = gq[q];
                     n = nq4[q];
                 }
+            if (!stack_form && uib != invB && in)   // under a raised bound: g and children from f/q
+                est_gn(W.node_x[off + j], W.node_u[off + j], g, n, invB, uib, (uint32_t)(next + lane), P.split, g, n);
             const bool anyneg = __any_sync(0xffffffffu, in && g < 0.0f);
             if (!stack_form && !anyneg) {
                 // inclusive scan of (n - 1) over the chunk
@@ -606,7 +609,7 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
                 const unsigned endm = __ballot_sync(0xffffffffu, in && pend + x <= 0);
                 const int cnt = min(32, w - j0);
                 const int last = endm ? __ffs(endm) - 1 : cnt - 1;   // last node processed
-                double t = (in && lane <= last) ? (double)(g * invB) : 0.0;
+                double t = (in && lane <= last) ? (double)(uw * g * uib) : 0.0;
                 for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
                 sum_t += t;
                 next += last + 1;
@@ -616,7 +619,7 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
             }
             // exact sequential walk of this chunk by lane 0, on the stack form
             if (!stack_form) {
-                if (lane == 0) est_from_count(gst, pend, invB);
+                if (lane == 0) est_from_uniform(gst, pend, uw, uib);
                 stack_form = true;
             }
             if (lane == 0) walk_seq(P, W, gst, off + j0, min(32, w - j0), invB, next, sum_t, done, trunc);
@@ -625,11 +628,14 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
             next = __shfl_sync(0xffffffffu, next, 0);
             sum_t = __shfl_sync(0xffffffffu, sum_t, 0);
             __syncwarp();
-            // back to the count form when the stack turned all-positive again
+            // back to the count form when the stack turned uniform again
             int pe;
-            if (est_count_form(gst, invB, pe)) {
+            float w2, ib2;
+            if (est_uniform_form(gst, w2, ib2, pe)) {
                 stack_form = false;
                 pend = pe;
+                uw = w2;
+                uib = ib2;
             }
             __syncwarp();
         }
@@ -638,7 +644,7 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
             trunc = 1;
         }
         if (lane == 0) {
-            if (!stack_form) est_from_count(gst, pend, invB);   // store the count form as a one-frame stack
+            if (!stack_form) est_from_uniform(gst, pend, uw, uib);   // store the count form as a one-frame stack
             gst.next = next;
             gst.sum_t = sum_t;
             if (done) {
@@ -673,6 +679,7 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
     __shared__ int s_wsum[WF_LONG_THREADS / 32];
     __shared__ double s_wpart[WF_LONG_THREADS / 32];
     __shared__ int s_end, s_done, s_trunc, s_next, s_pend;
+    __shared__ float s_w, s_ib;   // the uniform form's weight and inverse bound
     __shared__ double s_sum;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int items = W.ctl[WF_CTL_ITEMS];
@@ -687,7 +694,10 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
         const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
         if (tid == 0) {
             int pend;
-            s_pend = est_count_form(sst, invB, pend) ? pend : -1;   // -1: the stack form holds the state
+            float w0, ib0;
+            s_pend = est_uniform_form(sst, w0, ib0, pend) ? pend : -1;   // -1: the stack form holds the state
+            s_w = w0;
+            s_ib = ib0;
             s_next = sst.next;
             s_sum = sst.sum_t;
             s_done = 0;
@@ -697,7 +707,10 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
         for (int j0 = 0; j0 < w; j0 += 4 * WF_LONG_THREADS) {
             if (s_done) break;
             const int cnt = min(4 * WF_LONG_THREADS, w - j0);
-            float g[4];
+            const int pend0 = s_pend;
+            const float uw = s_w, uib = s_ib;
+            const bool raised = pend0 > 0 && uib != invB;   // the uniform form under a raised bound
+            float g[4], xv[4], uv[4];
             int n[4];
             bool neg = false;
 #pragma unroll
@@ -705,10 +718,16 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
                 const int jj = 4 * tid + i;
                 g[i] = jj < cnt ? W.node_g[off + j0 + jj] : 1.0f;
                 n[i] = jj < cnt ? W.node_n[off + j0 + jj] : 1;
+                xv[i] = 0.0f;
+                uv[i] = 1.0f;
+                if (raised && jj < cnt) {
+                    xv[i] = W.node_x[off + j0 + jj];
+                    uv[i] = W.node_u[off + j0 + jj];
+                    est_gn(xv[i], uv[i], g[i], n[i], invB, uib, (uint32_t)(s_next + jj), P.split, g[i], n[i]);
+                }
                 neg |= jj < cnt && g[i] < 0.0f;
             }
             const bool anyneg = __syncthreads_or(neg) != 0;
-            const int pend0 = s_pend;
             if (pend0 > 0 && !anyneg) {
                 int loc[4], acc = 0;
 #pragma unroll
@@ -738,7 +757,7 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
                 double part = 0.0;
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    if (4 * tid + i < cnt && 4 * tid + i <= end) part += (double)(g[i] * invB);
+                    if (4 * tid + i < cnt && 4 * tid + i <= end) part += (double)(uw * g[i] * uib);
                 for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
                 if (lane == 0) s_wpart[wid] = part;
                 __syncthreads();
@@ -762,20 +781,20 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
                 continue;
             }
             // the exact walk of this tile on the stack form: the block stages the
-            // tile, thread 0 walks it
+            // tile (g and children under the estimate's own bound), thread 0 walks it
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int jj = 4 * tid + i;
                 if (jj < cnt) {
-                    t_g[jj] = g[i];
-                    t_n[jj] = n[i];
+                    t_g[jj] = W.node_g[off + j0 + jj];
+                    t_n[jj] = W.node_n[off + j0 + jj];
                     t_x[jj] = W.node_x[off + j0 + jj];
                     t_u[jj] = W.node_u[off + j0 + jj];
                 }
             }
             __syncthreads();
             if (tid == 0) {
-                if (pend0 > 0) est_from_count(sst, pend0, invB);   // from the count form
+                if (pend0 > 0) est_from_uniform(sst, pend0, uw, uib);   // from the count form
                 int next = s_next, done = 0, trunc = 0;
                 double sum_t = s_sum;
                 walk_seq_arr(P, sst, t_g, t_n, t_x, t_u, cnt, invB, next, sum_t, done, trunc);
@@ -783,9 +802,12 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
                 s_sum = sum_t;
                 s_done = done;
                 s_trunc = trunc;
-                // back to the count form when the stack turned all-positive again
+                // back to the count form when the stack turned uniform again
                 int pe;
-                s_pend = est_count_form(sst, invB, pe) ? pe : -1;
+                float w2, ib2;
+                s_pend = est_uniform_form(sst, w2, ib2, pe) ? pe : -1;
+                s_w = w2;
+                s_ib = ib2;
             }
             __syncthreads();
         }
@@ -796,7 +818,7 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
                 done = 1;
                 trunc = 1;
             }
-            if (s_pend > 0) est_from_count(sst, s_pend, invB);   // store the count form as a one-frame stack
+            if (s_pend > 0) est_from_uniform(sst, s_pend, s_w, s_ib);   // store the count form as a one-frame stack
             sst.next = next;
             sst.sum_t = s_sum;
             gst = sst;

@@ -324,6 +324,57 @@ def test_wavefront_estimator_matches_phases_and_oracle(N, make):
     r.close()
 
 
+def test_estimator_walks_under_a_low_bound(N):
+    """A bound B at half the median positive f/q: many draws exceed B and
+    2B, so the walks carry negative weights, raised bounds (a node with
+    f/q > 2B hands its children the bound f/q) and long windows, which the
+    block walk takes in tiles on the uniform count form (one weight and one
+    bound for every pending node) or on the stack form. The wavefront
+    schedule must give the warp/block schedule's node counts exactly and its
+    estimates up to summation order, and the oracle's node counts and
+    estimates wherever the topology agrees."""
+    sc = scenes.cornell(16, 16)
+    o = O.Oracle(sc)
+    p = O.params(M=1500, M_p=1500, max_depth=8, pilot_max=0)
+    tri, bary = o.light_pass(p, 3)
+    ents, _ = o.entries(p, tri, bary)
+    rs = []
+    for k, e in enumerate(ents[:200]):
+        f, q = o.entry_fq(e, 64, a=3, b=k)
+        r = f[q > 0] / q[q > 0]
+        rs.extend(r[r > 0])
+    B = 0.5 * float(np.quantile(rs, 0.5))
+    tab = scenes.random_tables(sc, KT=8, KS=8, KSp=4, KC=2, B=B, mis=1.0)
+    td = o.tables(tab)
+    r = N.Renderer(sc, tab)
+    n_ent = n_same = long_chains = 0
+    for it in (3, 4):
+        tri, bary = o.light_pass(p, it)
+        cfg = dict(M=1500, M_p=1500, max_depth=8, pilot_max=-1)
+        a = r.iteration(N.config(estimator=1, **cfg), it, tri, bary)
+        b = r.iteration(N.config(**cfg), it, tri, bary)
+        np.testing.assert_array_equal(a["entry_nodes"], b["entry_nodes"])
+        np.testing.assert_array_equal(a["entry_sig"], b["entry_sig"])
+        np.testing.assert_allclose(b["rhat"], a["rhat"], rtol=1e-4)
+        assert b["stats"]["n_truncated"] == a["stats"]["n_truncated"]
+        long_chains += int((b["entry_nodes"] > 5 * 8192).sum())
+        ref = o.iteration(p, td, it, tri, bary, pix_lo=0, pix_hi=0)
+        es = ref["entry_sig"] == b["entry_sig"]
+        n_ent += len(es)
+        n_same += int(es.sum())
+        assert np.array_equal(ref["entry_nodes"][es], b["entry_nodes"][es])
+        # values of untruncated entries; signed sums can come close to zero, so
+        # the error is taken relative to max(|estimate|, median |estimate|)
+        es &= ref["entry_nodes"] < (1 << 16)
+        a64 = ref["rhat"][es]
+        scale = np.maximum(np.abs(a64), np.median(np.abs(a64)))
+        rel = np.abs(a64 - b["rhat"][es]) / scale
+        assert rel.max() <= 1e-3 and np.median(rel) <= 1e-5, (rel.max(), np.median(rel))
+    assert long_chains > 0
+    assert n_same / n_ent >= 0.9, n_same / n_ent
+    r.close()
+
+
 @pytest.mark.parametrize("film", [1, 2])
 def test_film_modes_match_oracle(N, film):
     """The film modes of the subspace-selection comparison (1: only the
