@@ -685,6 +685,87 @@ __device__ PB_TRAV_FN bool trav_occluded(TravView S, float3 a, float3 b, int s1,
 }
 
 // ---------------------------------------------------------------------------
+// Traversal one node visit at a time, for persistent warps that refill idle
+// lanes: a lane's ray state lives in a PtRay, and pt_step runs the loop body of
+// trav_closest / trav_occluded once, so a query answered in steps is answered
+// node for node as the one-call traversal answers it.
+constexpr int PT_STEPS = 8;   // node visits per lane between refills
+
+struct PtRay {
+    float3 o, d, inv;   // occlusion: d = b - a
+    Hit h;              // closest: best so far; occlusion: tri = 1 once blocked
+    uint64_t trail;
+    int node, kind, s1, s2, steps;   // kind 0 closest, 2 occlusion, 3 closest that must end on an emitter
+};
+
+// one node visit of r's traversal (the loop body of trav_closest or
+// trav_occluded); true when the traversal has ended
+template <bool COUNT>
+__device__ __forceinline__ bool pt_step(const TravView &S, PtRay &r, TravCount *tc) {
+    if (r.steps++ >= (1 << 22)) return true;
+    const bool occl = r.kind == 2;
+    bool hL, hR;
+    float tl, tr;
+    int cl, cr;
+    child_boxes(S, r.node, r.o, r.inv, occl ? 1.0f : r.h.t, hL, hR, tl, tr, cl, cr);
+    if (COUNT) tc->nodes++;
+    if (hL && cl < 0) {
+        int v = -cl - 1, first = v >> 4, n = v & 15;
+        if (occl) {
+            for (int i = 0; i < n; ++i) {
+                if (COUNT) tc->tris++;
+                if (seg_test(S, first + i, r.o, r.d, r.s1, r.s2)) {
+                    r.h.tri = 1;
+                    return true;
+                }
+            }
+        } else {
+            for (int i = 0; i < n; ++i) tri_test(S, first + i, r.o, r.d, r.s1, r.h);
+            if (COUNT) tc->tris += n;
+        }
+        hL = false;
+    }
+    if (hR && cr < 0) {
+        int v = -cr - 1, first = v >> 4, n = v & 15;
+        if (occl) {
+            for (int i = 0; i < n; ++i) {
+                if (COUNT) tc->tris++;
+                if (seg_test(S, first + i, r.o, r.d, r.s1, r.s2)) {
+                    r.h.tri = 1;
+                    return true;
+                }
+            }
+        } else {
+            for (int i = 0; i < n; ++i) tri_test(S, first + i, r.o, r.d, r.s1, r.h);
+            if (COUNT) tc->tris += n;
+        }
+        hR = false;
+    }
+    if (!occl) {
+        hL = hL && tl <= r.h.t;
+        hR = hR && tr <= r.h.t;
+    }
+    if (hL && hR) {
+        r.trail = (r.trail << 1) | 1ull;
+        r.node = tl <= tr ? cl : cr;
+        return false;
+    }
+    if (hL || hR) {
+        r.trail <<= 1;
+        r.node = hL ? cl : cr;
+        return false;
+    }
+    while ((r.trail & 1ull) == 0ull) {
+        if (r.trail == 0ull) return true;
+        r.trail >>= 1;
+        r.node = __ldg(S.parent + r.node);
+    }
+    r.trail ^= 1ull;
+    r.node = __ldg(S.sibling + r.node);
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 // Subspace labels: nearest centroid in bbox-normalised feature space, ties to
 // the lowest index (Sec. 3.2: subspaces by position, normal and direction).
 __device__ __forceinline__ int nearest(const float *f, int dim, int K, const float *cent) {
