@@ -131,6 +131,11 @@ __host__ __device__ inline int wf_pilot_rounds(const KParams &P) {
     return nr;
 }
 
+// g = 1 - (f/q) / B of an estimator node, given 1/B, with one rounding (a fused
+// multiply-add written out): every kernel that evaluates a node gets the same
+// bits, whatever the compiler would contract at each site
+__device__ __forceinline__ float est_g(float x, float invB) { return __fmaf_rn(-x, invB, 1.0f); }
+
 // Children of an estimator node (Alg. I~ with the split limit): the paper's
 // r = |g|, i.e. floor(|g|) + Bernoulli(frac) children entering with weight
 // sign(g); from pre-order node `split` on, a node with |g| > 1 has one child
@@ -179,7 +184,7 @@ __device__ __forceinline__ EstStep est_step(const St &st, float x, float u, floa
         e.g = g0;
         e.n = n0;
     } else {
-        e.g = 1.0f - x * st.cur_ib;
+        e.g = est_g(x, st.cur_ib);
         e.n = est_children(e.g, u, v, P.split);
     }
     e.cib = est_child_invB(e.g, x, st.cur_ib, P.fixed_bound);
@@ -262,7 +267,7 @@ __device__ __forceinline__ void est_gn(float x, float u, float g0, int n0, float
         g = g0;
         n = n0;
     } else {
-        g = 1.0f - x * ib;
+        g = est_g(x, ib);
         n = est_children(g, u, v, split);
     }
 }

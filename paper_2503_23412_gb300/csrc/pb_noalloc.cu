@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(128) k_na_recip(DScene S, KParams P, uint32_t 
                 R.init(P.seed, K_RECIP, iteration, (uint32_t)(k * 8 + rep), (uint32_t)v);
                 x = entry_ratio<false>(S, E, R, nullptr);
                 u = R.u(18);
-                g = 1.0f - x * invB;
+                g = est_g(x, invB);
                 nch = est_children(g, u, (uint32_t)v, P.split);
             }
             for (int j = 0; j < 32; ++j) {

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128) k_recip(DScene S, DTables T, KParams P, P
                 R.init(P.seed, K_RECIP, iter_base + slot, (uint32_t)(k * 8 + rep), (uint32_t)v);
                 x = entry_ratio<COUNT>(S, E, R, &tc);
                 u = R.u(18);
-                g = 1.0f - x * invB;
+                g = est_g(x, invB);
                 nch = est_children(g, u, (uint32_t)v, P.split);
             }
             // the walk stops before a node that would need a frame beyond MAXF1;

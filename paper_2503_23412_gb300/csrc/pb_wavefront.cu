@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(128) k_wf_step(DScene S, KParams P, Pool B, Wf
         } else if (PILOT) {
             W.node_g[i] = ratio;
         } else {
-            const float gv = 1.0f - ratio * invB, u18 = R.u(18);
+            const float gv = est_g(ratio, invB), u18 = R.u(18);
             W.node_g[i] = gv;
             W.node_n[i] = est_children(gv, u18, (uint32_t)W.node_v[i], P.split);
             W.node_x[i] = ratio;
@@ -869,7 +869,7 @@ __global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t
             Rng R;
             R.init(P.seed, K_RECIP, iter_base + st.slot, (uint32_t)(st.k * 8 + st.rep), (uint32_t)st.next);
             float ratio = entry_ratio<false>(S, E, R, nullptr);
-            float gj = 1.0f - ratio * invB;
+            float gj = est_g(ratio, invB);
             st.prod *= (double)gj;
             const double tb = st.prod / st.surv * (double)invB;
             if (!isfinite(tb)) {   // the weight left the double range: report the chain as truncated
@@ -890,7 +890,7 @@ __global__ void k_wf_finish_rest(DScene S, KParams P, Pool B, WfBufs W, uint32_t
             Rng R;
             R.init(P.seed, K_RECIP, iter_base + st.slot, (uint32_t)(st.k * 8 + st.rep), (uint32_t)st.next);
             const float ratio = entry_ratio<false>(S, E, R, nullptr), u18 = R.u(18);
-            const float gj = 1.0f - ratio * invB;
+            const float gj = est_g(ratio, invB);
             const uint32_t v = (uint32_t)st.next;
             const EstStep e = est_step(st, ratio, u18, gj, est_children(gj, u18, v, P.split), invB, v, P);
             st.next += 1;
