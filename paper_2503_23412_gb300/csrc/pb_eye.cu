@@ -695,12 +695,13 @@ __global__ void __launch_bounds__(128) k_eye_occ_pt(DScene S, KParams P, unsigne
 
 // The feature pass on persistent warps (KParams.trace = 1). A lane takes the
 // next camera path (slot, pixel) from a counter when its path ends, and every
-// trip advances each busy lane's ray by up to PT_STEPS node visits; a lane
-// whose ray has its answer runs that vertex's step of k_eye_feat (store the
-// hit, network rows, BSDF draw) and starts the next bounce's ray. A path's
-// hits, rows and draws are those of k_eye_feat: only which lane traces it,
-// and when, changes (rows are appended in another order, each with its dense
-// position).
+// trip advances each tracing lane's ray by up to PT_STEPS node visits. A lane
+// whose ray has its answer waits until at least half of the warp's busy lanes
+// wait too (or none is tracing); then the waiting lanes run their vertex's
+// step of k_eye_feat together (store the hit, network rows, BSDF draw) and
+// start the next bounce's ray. A path's hits, rows and draws are those of
+// k_eye_feat: only which lane traces it, and when, changes (rows are appended
+// in another order, each with its dense position).
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_eye_feat_pt(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base,
                                                      int slots, unsigned int *fetch) {
@@ -710,7 +711,7 @@ __global__ void __launch_bounds__(128) k_eye_feat_pt(DScene S, DTables T, KParam
     const TravView V = trav_view(S);
     const unsigned int total = (unsigned int)slots * (unsigned int)P.npix;
     const int lane = threadIdx.x & 31;
-    bool busy = false, drained = false;
+    bool busy = false, drained = false, ready = false;   // busy: a path; ready: its ray has an answer
     int slot = 0, pix = 0, a = 0;
     uint32_t it = 0;
     float pi_pix = 0.0f;
@@ -768,14 +769,16 @@ __global__ void __launch_bounds__(128) k_eye_feat_pt(DScene S, DTables T, KParam
             if (__all_sync(FULL, drained)) break;
             continue;
         }
-        if (!busy) continue;
-        bool answered = false;
-        for (int st = 0; st < PT_STEPS; ++st)
-            if (pt_step<COUNT>(V, r, &tc)) {
-                answered = true;
-                break;
-            }
-        if (!answered) continue;
+        if (busy && !ready)
+            for (int st = 0; st < PT_STEPS; ++st)
+                if (pt_step<COUNT>(V, r, &tc)) {
+                    ready = true;
+                    break;
+                }
+        const unsigned rm = __ballot_sync(FULL, ready), bm = __ballot_sync(FULL, busy);
+        if (!(rm == bm || 2 * __popc(rm) >= __popc(bm))) continue;   // too few answers to step together
+        if (!ready) continue;
+        ready = false;
         // the vertex step of bounce a (the loop body of k_eye_feat)
         const Hit h = r.h;
         P.mlp.hits[((size_t)slot * P.max_depth + (a - 1)) * P.npix + pix] =
