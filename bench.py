@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpaths/s and equal-time MAPE vs CPU oracle; learned vs plain proposal, 1 GB300"
 ENTRY_TARGET = 400          # incomplete light sub-paths estimated per iteration (paper: up to 400)
 BOOTH = 0.0                 # --booth: Booth's Russian roulette scale in the estimator (0: the paper's RRS)
-TRACE = 1                   # --trace: 1 = traversal kernels on persistent warps with lane refill, 0 = one ray per thread
+TRACE = 1                   # --trace: 1 = estimator traces and occlusion answers on persistent warps, 0 = one ray per thread
 TRIAL_CAP = 1 << 20         # node cap per reciprocal estimate
 
 
@@ -824,7 +824,7 @@ def run_ours(args):
                    "estimator_bound": ("per-entry pilot maximum of f/q (learned cell value when the pilot saw no f > 0)"
                                        if pilot >= 0 else "learned (u, S', C) cell maximum of f/q, %d draws per entry "
                                        "over %d learning iterations" % (WL.get("learn_nb", 32), n_learn)),
-                   "traversal": "persistent warps, lane refill (estimator trace stages, feature pass, occlusion answers)" if TRACE else "one ray per thread"},
+                   "traversal": "persistent warps, lane refill (estimator trace stages, occlusion answers)" if TRACE else "one ray per thread"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for(dom, sha),
                      "algorithmic_bytes_per_launch": b, "launch_ms": ms, "src_sha": sha},
@@ -869,7 +869,7 @@ def main():
                     help="Booth's Russian roulette of this scale in the reciprocal estimator (the RR ablation's "
                          "baseline; 0: the paper's RRS function)")
     ap.add_argument("--trace", type=int, default=1, choices=[0, 1],
-                    help="1 (default): the estimator's trace stages and the eye pass's traversal kernels on "
+                    help="1 (default): the estimator's trace stages and the eye pass's occlusion answers on "
                          "persistent warps that refill idle lanes; 0: one ray per thread")
     ap.add_argument("--no-study", action="store_true", help="skip the equal-time study and the oracle validation")
     args = ap.parse_args()

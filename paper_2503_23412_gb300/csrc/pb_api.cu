@@ -736,7 +736,7 @@ pb_status pb_eye_ensure(pb_ctx *ctx, int slots, int depth) {
     CK(dalloc(o, &ctx->eye_qa, nq));
     CK(dalloc(o, &ctx->eye_qb, nq));
     CK(dalloc(o, &ctx->eye_dst, nq));
-    CK(dalloc(o, &ctx->eye_count, (size_t)3));   // queries appended; paths and queries taken by persistent warps
+    CK(dalloc(o, &ctx->eye_count, (size_t)2));   // queries appended; queries taken by persistent warps
     ctx->eye_cap_px = px;
     ctx->eye_cap_q = nq;
     return PB_OK;
@@ -752,7 +752,7 @@ pb_status pb_eye_stages(pb_ctx *ctx, const KParams &P0, int slots, uint32_t iter
         P.mlp.rows = nullptr;
         P.mlp.sel = nullptr;
         P.mlp.selq = nullptr;
-        launch_eye_feat(ctx->S, ctx->T, P, ctx->B, slots, iter_base, st, ctx->eye_count + 1, ctx->num_sms);
+        launch_eye_feat(ctx->S, ctx->T, P, ctx->B, slots, iter_base, st);
         if (ev && ev->feat_end) CK(cudaEventRecordWithFlags(ev->feat_end, st, ev->flags));
     }
     const size_t npix = (size_t)ctx->S.W * ctx->S.H;
@@ -762,7 +762,7 @@ pb_status pb_eye_stages(pb_ctx *ctx, const KParams &P0, int slots, uint32_t iter
     CK(cudaMemsetAsync(ctx->eye_count, 0, sizeof(unsigned int), st));
     launch_eye(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->Lbuf, nullptr, st, EYE_EMIT);
     if (ev && ev->emit_end) CK(cudaEventRecordWithFlags(ev->emit_end, st, ev->flags));
-    launch_eye_occ(ctx->S, P, ctx->B, ctx->num_sms, st, ctx->eye_count + 2);
+    launch_eye_occ(ctx->S, P, ctx->B, ctx->num_sms, st, ctx->eye_count + 1);
     if (ev && ev->occ_end) CK(cudaEventRecordWithFlags(ev->occ_end, st, ev->flags));
     launch_eye(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->Lbuf, sig, st, EYE_READ);
     CK(cudaGetLastError());

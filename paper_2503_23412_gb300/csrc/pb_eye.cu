@@ -693,154 +693,6 @@ __global__ void __launch_bounds__(128) k_eye_occ_pt(DScene S, KParams P, unsigne
     }
 }
 
-// The feature pass on persistent warps (KParams.trace = 1). A lane takes the
-// next camera path (slot, pixel) from a counter when its path ends, and every
-// trip advances each tracing lane's ray by up to PT_STEPS node visits. A lane
-// whose ray has its answer waits until at least half of the warp's busy lanes
-// wait too (or none is tracing); then the waiting lanes run their vertex's
-// step of k_eye_feat together (store the hit, network rows, BSDF draw) and
-// start the next bounce's ray. A path's hits, rows and draws are those of
-// k_eye_feat: only which lane traces it, and when, changes (rows are appended
-// in another order, each with its dense position).
-template <bool COUNT>
-__global__ void __launch_bounds__(128) k_eye_feat_pt(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base,
-                                                     int slots, unsigned int *fetch) {
-    iter_base = eff_iter(P, iter_base);
-    const unsigned FULL = 0xffffffffu;
-    TravCount tc{0, 0, 0};
-    const TravView V = trav_view(S);
-    const unsigned int total = (unsigned int)slots * (unsigned int)P.npix;
-    const int lane = threadIdx.x & 31;
-    bool busy = false, drained = false, ready = false;   // busy: a path; ready: its ray has an answer
-    int slot = 0, pix = 0, a = 0;
-    uint32_t it = 0;
-    float pi_pix = 0.0f;
-    bool conn = false, proxy_row = false;
-    float3 d = f3(0.0f, 0.0f, 0.0f);
-    PtRay r;
-    auto start_ray = [&](float3 o, float3 dir, int skip) {
-        r.o = o;
-        r.d = dir;
-        r.inv = safe_inv(dir);
-        r.s1 = skip;
-        r.s2 = -1;
-        r.kind = 0;
-        r.node = 0;
-        r.trail = 0ull;
-        r.steps = 0;
-        r.h.tri = -1;
-        r.h.t = INFINITY;
-        r.h.b1 = r.h.b2 = 0.0f;
-        if (COUNT) tc.rays++;
-    };
-    for (;;) {
-        const bool need = !busy && !drained;
-        const unsigned m = __ballot_sync(FULL, need);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            unsigned int base = 0;
-            if (lane == leader) base = atomicAdd(fetch, (unsigned int)__popc(m));
-            base = __shfl_sync(FULL, base, leader);
-            if (need) {
-                const unsigned int k = base + (unsigned int)__popc(m & ((1u << lane) - 1u));
-                if (k < total) {
-                    busy = true;
-                    slot = (int)(k / (unsigned int)P.npix);
-                    pix = (int)(k % (unsigned int)P.npix);
-                    it = iter_base + (uint32_t)slot;
-                    const int px = pix % S.W, py = pix / S.W;
-                    Rng r0;
-                    r0.init(P.seed, K_CAMERA, it, (uint32_t)pix, 0);
-                    const float j0 = r0.u(0), j1 = r0.u(1);
-                    const float sx = 2.0f * ((float)px + j0) / (float)S.W - 1.0f;
-                    const float sy = 1.0f - 2.0f * ((float)py + j1) / (float)S.H;
-                    d = normalize(S.cfwd + (S.cright * (sx * S.tanh_ * S.aspect) + S.cup * (sy * S.tanh_)));
-                    a = 1;
-                    conn = P.conn && B.npool[slot] > 0;
-                    proxy_row = P.mlpp.rows && P.proxy && B.nent[slot] > 0;
-                    pi_pix = T.pi[(py / T.tile) * T.gw + (px / T.tile)];
-                    start_ray(S.cpos, d, -1);
-                } else {
-                    drained = true;
-                }
-            }
-        }
-        if (!__any_sync(FULL, busy)) {
-            if (__all_sync(FULL, drained)) break;
-            continue;
-        }
-        if (busy && !ready)
-            for (int st = 0; st < PT_STEPS; ++st)
-                if (pt_step<COUNT>(V, r, &tc)) {
-                    ready = true;
-                    break;
-                }
-        const unsigned rm = __ballot_sync(FULL, ready), bm = __ballot_sync(FULL, busy);
-        if (!(rm == bm || 2 * __popc(rm) >= __popc(bm))) continue;   // too few answers to step together
-        if (!ready) continue;
-        ready = false;
-        // the vertex step of bounce a (the loop body of k_eye_feat)
-        const Hit h = r.h;
-        P.mlp.hits[((size_t)slot * P.max_depth + (a - 1)) * P.npix + pix] =
-            make_int4(h.tri, __float_as_int(h.t), __float_as_int(h.b1), __float_as_int(h.b2));
-        busy = false;
-        if (h.tri < 0) continue;
-        Vtx z = vertex_at(S, h.tri, h.b1, h.b2);
-        const DMat &mz = S.mats[z.mat];
-        float3 we = -d;
-        if (absorbing(S, z, we)) continue;
-        if (proxy_row && !mz.specular) {
-            proxy_row = false;   // only the first non-specular vertex
-            Rng Rc;
-            Rc.init(P.seed, K_CAMERA, it, (uint32_t)pix, (uint32_t)a);
-            if (pi_pix > 0.0f && a + 2 <= P.max_depth && Rc.u(8) < pi_pix) {
-                int Tl = label_dir(S, z, we, T.KT, T.cT);
-                cg::coalesced_group g = cg::coalesced_threads();
-                unsigned int b0 = 0;
-                if (g.thread_rank() == 0) b0 = atomicAdd(P.mlpp.count, (unsigned int)g.size());
-                unsigned int idx = g.shfl(b0, 0) + g.thread_rank();
-                if (idx < (unsigned int)P.mlpp.cap) {
-                    float raw[MLP_NRAW];
-                    mlp_raw(S, z, we, raw);
-                    mlp_pack_row(raw, Tl, P.mlpp.emb, P.mlpp.rows + (size_t)MLP_NX * idx);
-                    P.mlpp.rowT[idx] = Tl;
-                    P.mlpp.rowPos[idx] = (int32_t)(((size_t)slot * P.mlpp.A + (a - 1)) * P.npix + pix);
-                }
-            }
-        }
-        if (conn && P.mlp.rows && !mz.specular && a + 2 <= P.max_depth) {
-            int Tl = label_dir(S, z, we, T.KT, T.cT);
-            cg::coalesced_group g = cg::coalesced_threads();
-            unsigned int b0 = 0;
-            if (g.thread_rank() == 0) b0 = atomicAdd(P.mlp.count, (unsigned int)g.size());
-            unsigned int idx = g.shfl(b0, 0) + g.thread_rank();
-            if (idx < (unsigned int)P.mlp.cap) {
-                float raw[MLP_NRAW];
-                mlp_raw(S, z, we, raw);
-                mlp_pack_row(raw, Tl, P.mlp.emb, P.mlp.rows + (size_t)MLP_NX * idx);
-                P.mlp.rowT[idx] = Tl;
-                P.mlp.rowPos[idx] = (int32_t)(((size_t)slot * P.mlp.A + (a - 1)) * P.npix + pix);
-            }
-        }
-        if (a + 1 > P.max_depth) continue;
-        Rng R;
-        R.init(P.seed, K_CAMERA, it, (uint32_t)pix, (uint32_t)a);
-        float3 wl;
-        if (!bsdf_sample(mz, z.n, we, R.u(0), R.u(1), R.u(2), wl)) continue;
-        float pw = bsdf_pdf(mz, z.n, we, wl);
-        if (!(pw > 0.0f)) continue;
-        d = wl;
-        start_ray(z.p, d, z.tri);
-        ++a;
-        busy = true;
-    }
-    if (COUNT) {
-        atomicAdd(&B.counters[CNT_CAM_NODES], (unsigned long long)tc.nodes);
-        atomicAdd(&B.counters[CNT_CAM_TRIS], (unsigned long long)tc.tris);
-        atomicAdd(&B.counters[CNT_CAM_RAYS], (unsigned long long)tc.rays);
-    }
-}
-
 __global__ void k_film_add(KParams P, int slots, const float4 *Lbuf, float *film) {
     int pix = blockIdx.x * blockDim.x + threadIdx.x;
     if (pix >= P.npix) return;
@@ -885,14 +737,12 @@ void launch_eye_occ(const DScene &S, const KParams &P, const Pool &B, int num_sm
     else k_eye_occ<false><<<blocks, 128, 0, st>>>(S, P, B.counters);
 }
 
+// The feature pass stays one camera path per thread for either trace mode: a
+// persistent variant that refilled lanes with new paths (and batched their
+// vertex steps) measured 167 ms against 140 ms on the 1024^2 glossy step, as
+// refilled lanes lose the coherence of neighbouring camera paths.
 void launch_eye_feat(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
-                     cudaStream_t st, unsigned int *fetch, int num_sms) {
-    if (P.trace && fetch) {
-        cudaMemsetAsync(fetch, 0, sizeof(unsigned int), st);
-        if (P.count) k_eye_feat_pt<true><<<num_sms * 8, 128, 0, st>>>(S, T, P, B, iter_base, slots, fetch);
-        else k_eye_feat_pt<false><<<num_sms * 8, 128, 0, st>>>(S, T, P, B, iter_base, slots, fetch);
-        return;
-    }
+                     cudaStream_t st) {
     dim3 grid((P.npix + 127) / 128, slots);
     if (P.count) k_eye_feat<true><<<grid, 128, 0, st>>>(S, T, P, B, iter_base);
     else k_eye_feat<false><<<grid, 128, 0, st>>>(S, T, P, B, iter_base);

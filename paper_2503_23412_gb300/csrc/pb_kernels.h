@@ -368,11 +368,11 @@ void launch_recip_wavefront(const DScene &S, const DTables &T, const KParams &P,
 void launch_eye(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                 float4 *Lbuf, uint32_t *sigbuf, cudaStream_t st, int mode = EYE_INLINE);
 // traversal-only answers of the queries the EYE_EMIT pass appended
+// fetch: a device counter for the persistent variant (KParams.trace = 1; nullptr: one query per thread)
 void launch_eye_occ(const DScene &S, const KParams &P, const Pool &B, int num_sms, cudaStream_t st,
                     unsigned int *fetch = nullptr);
-// fetch: a device counter for the persistent variants (KParams.trace = 1; nullptr: one path per thread)
 void launch_eye_feat(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
-                     cudaStream_t st, unsigned int *fetch = nullptr, int num_sms = 0);
+                     cudaStream_t st);
 void launch_film_add(const KParams &P, int slots, const float4 *Lbuf, float *film, cudaStream_t st);
 void launch_trace(const DScene &S, const float *rays, int n, float *hits, int count, unsigned long long *counters,
                   cudaStream_t st);

@@ -880,8 +880,7 @@ pb_status mlp_wave(pb_ctx *ctx, KParams &P, int slots, uint32_t iter_base, const
         CK(cudaMemsetAsync(MP.rcount, 0, sizeof(unsigned int), ctx->stream));
         P.mlpp = MlpRows{MP.rows, MP.rowT, MP.rowPos, MP.rcount, (int)n, nullptr, nullptr, nullptr, MP.emb, A};
     }
-    if ((s = pb_eye_ensure(ctx, slots, P.max_depth)) != PB_OK) return s;
-    launch_eye_feat(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->stream, ctx->eye_count + 1, ctx->num_sms);
+    launch_eye_feat(ctx->S, ctx->T, P, ctx->B, slots, iter_base, ctx->stream);
     CK(cudaGetLastError());
     if (ev && ev->feat_end) CK(cudaEventRecordWithFlags(ev->feat_end, ctx->stream, ev->flags));
     SelArgs a = sel_base(ctx);

@@ -93,8 +93,7 @@ def test_graph_replay_with_learned_proposal(N):
     b, st = _film(N, r, N.config(spp=8, iter0=300, proposal=1, graph=1, **base))
     np.testing.assert_array_equal(a, b)
     assert st["ms_mlp"] > 0
-    # persistent feature pass: network rows are appended in another order,
-    # each with its dense position, so the selections and the film are the same
+    # persistent traversal stages: the same rays, answered node for node
     c, _ = _film(N, r, N.config(spp=8, iter0=300, proposal=1, graph=1, trace=1, **base))
     np.testing.assert_array_equal(a, c)
     r.close()

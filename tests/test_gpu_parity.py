@@ -415,11 +415,11 @@ def test_film_modes_match_oracle(N, film):
 
 
 def test_persistent_trace_stages_give_identical_estimates(N):
-    """trace = 1 runs the wavefront's trace stages, the eye pass's feature
-    pass and its occlusion answers on persistent warps whose lanes take the
-    next query (or camera path) when theirs is answered; each ray is still
-    traced node by node as with one ray per thread, so estimates, node
-    counts, signatures and pixels are bit-identical."""
+    """trace = 1 runs the wavefront's trace stages and the eye pass's
+    occlusion answers on persistent warps whose lanes take the next query
+    when theirs is answered; each ray is still traced node by node as with
+    one ray per thread, so estimates, node counts, signatures and pixels are
+    bit-identical."""
     sc = scenes.projector(24, 24, lens_tris_per_cap=1500, flat=True)
     o = O.Oracle(sc)
     tab = learned(sc, o, M=1500, M_p=1500, max_depth=8)
