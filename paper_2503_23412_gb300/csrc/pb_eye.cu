@@ -98,7 +98,7 @@ __device__ __forceinline__ bool eye_visible(const DScene &S, const KParams &P, s
 }
 
 template <bool COUNT, int MODE>
-__global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base,
+__global__ void __launch_bounds__(128, 4) k_eye(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base,
                                              float4 *Lbuf, uint32_t *sigbuf) {
     constexpr bool SHADE = MODE != EYE_EMIT;   // the emit pass only walks the paths and appends queries
     iter_base = eff_iter(P, iter_base);
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(128) k_eye(DScene S, DTables T, KParams P, Poo
 // k_eye makes a subspace connection (row order is arbitrary; each row's
 // result depends on its own content only).
 template <bool COUNT>
-__global__ void __launch_bounds__(128) k_eye_feat(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base) {
+__global__ void __launch_bounds__(128, 8) k_eye_feat(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base) {
     iter_base = eff_iter(P, iter_base);
     TravCount tc{0, 0, 0};
     int pix = blockIdx.x * blockDim.x + threadIdx.x;
