@@ -518,11 +518,15 @@ def run_subspace_ablation(args):
     spp, ref_spp, depth, Ma = 128, 2048, 8, 10000
     sc = scenes.water(Wa, Ha)
     r = N.Renderer(sc, None, device=local)
-    r.prepare(N.config(M=Ma, M_p=Ma, max_depth=depth), n_iter=4, iter0=1 << 22, n_bsamples=32, lloyd_iters=8,
-              KT=64, KS=64, KSp=32, KC=4)
+    st = r.prepare(N.config(M=Ma, M_p=Ma, max_depth=depth), n_iter=4, iter0=1 << 22, n_bsamples=32, lloyd_iters=8,
+                   KT=64, KS=64, KSp=32, KC=4)
     learned = r.tables_readback()
     uniform = dict(learned, gamma_proxy=np.full_like(learned["gamma_proxy"], 1.0 / learned["gamma_proxy"].shape[1]))
-    base = dict(M=Ma, M_p=Ma, max_depth=depth, seed=7, film=1)
+    # about ENTRY_TARGET incomplete sub-paths per iteration (the paper's practical limit), as the
+    # other workloads; with all M light paths the water scene's pool outgrows the chain slots
+    frac = st["n_entries"] / float(4 * Ma)
+    M_p = int(min(Ma, max(1, round(ENTRY_TARGET / max(frac, 1e-9)))))
+    base = dict(M=Ma, M_p=M_p, max_depth=depth, seed=7, film=1)
 
     def render(tables, n, iter0):
         r.upload_tables(tables)
@@ -535,8 +539,8 @@ def run_subspace_ablation(args):
     img_u, st_u = render(uniform, spp, 0)
     out = {"metric": "proxy-only MAPE at equal iterations, importance vs uniform subspace selection",
            "unit": "MAPE", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
-           "config": {"workload": "water pool %dx%d, depth %d, M=%d, %d iterations each, reference %d iterations"
-                      % (Wa, Ha, depth, Ma, spp, ref_spp), "film": "proxy strategy only"},
+           "config": {"workload": "water pool %dx%d, depth %d, M=%d, M_p=%d, %d iterations each, reference %d "
+                                  "iterations" % (Wa, Ha, depth, Ma, M_p, spp, ref_spp), "film": "proxy strategy only"},
            "mape": {"importance": mape(img_l, ref), "uniform": mape(img_u, ref)},
            "proxy_ok": {"importance": st_l["n_proxy_ok"], "uniform": st_u["n_proxy_ok"]},
            "ms": {"importance": st_l["ms"], "uniform": st_u["ms"]}}
