@@ -587,14 +587,16 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
     }
 }
 
-// one block per chain whose window holds at least WF_WALK_LONG nodes: the
-// same walk, in tiles of 1024 nodes (4 per thread). A tile with no negative
-// g on the count form is walked in parallel: a block scan of (n - 1) gives
-// every node's pending count, the chain ends at the first node where it
-// reaches 0, and the terms g / B up to there are summed by a block
-// reduction. Otherwise the block stages the tile's node values in shared
-// memory and thread 0 walks it on the stack form, which the block keeps in
-// shared memory for the whole window.
+// one block per chain whose window holds at least WF_WALK_LONG nodes, in
+// tiles of 1024 nodes staged in shared memory together with the chain's walk
+// state. While every pending node shares one weight and one bound (the
+// uniform count form), the run of tile nodes up to the first node with a
+// negative g under that bound is walked in parallel: a block scan of
+// (children - 1) gives each node's pending count, the chain ends at the first
+// node where it reaches 0, and the terms w g / B up to there are summed by a
+// block reduction. The node that breaks the run, and any stretch where the
+// pending nodes differ in weight or bound, are walked by thread 0 on the
+// stack form, node by node, until the form is uniform again.
 constexpr int WF_LONG_THREADS = 256;
 constexpr int WF_LONG_TILE = 4 * WF_LONG_THREADS;
 __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Pool B, WfBufs W) {
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
     __shared__ int32_t t_n[WF_LONG_TILE];
     __shared__ int s_wsum[WF_LONG_THREADS / 32];
     __shared__ double s_wpart[WF_LONG_THREADS / 32];
-    __shared__ int s_end, s_done, s_trunc, s_next, s_pend;
+    __shared__ int s_end, s_brk, s_done, s_trunc, s_next, s_pend, s_pos;
     __shared__ float s_w, s_ib;   // the uniform form's weight and inverse bound
     __shared__ double s_sum;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -629,112 +631,166 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
             s_trunc = 0;
         }
         __syncthreads();
-        for (int j0 = 0; j0 < w; j0 += 4 * WF_LONG_THREADS) {
+        for (int j0 = 0; j0 < w; j0 += WF_LONG_TILE) {
             if (s_done) break;
-            const int cnt = min(4 * WF_LONG_THREADS, w - j0);
-            const int pend0 = s_pend;
-            const float uw = s_w, uib = s_ib;
-            const bool raised = pend0 > 0 && uib != invB;   // the uniform form under a raised bound
-            float g[4], xv[4], uv[4];
-            int n[4];
-            bool neg = false;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int jj = 4 * tid + i;
-                g[i] = jj < cnt ? W.node_g[off + j0 + jj] : 1.0f;
-                n[i] = jj < cnt ? W.node_n[off + j0 + jj] : 1;
-                xv[i] = 0.0f;
-                uv[i] = 1.0f;
-                if (raised && jj < cnt) {
-                    xv[i] = W.node_x[off + j0 + jj];
-                    uv[i] = W.node_u[off + j0 + jj];
-                    est_gn(xv[i], uv[i], g[i], n[i], invB, uib, (uint32_t)(s_next + jj), P.split, g[i], n[i]);
-                }
-                neg |= jj < cnt && g[i] < 0.0f;
+            const int cnt = min(WF_LONG_TILE, w - j0);
+            // stage the tile: g and children under the estimate's own bound, f/q, uniform
+            for (int jj = tid; jj < cnt; jj += WF_LONG_THREADS) {
+                t_g[jj] = W.node_g[off + j0 + jj];
+                t_n[jj] = W.node_n[off + j0 + jj];
+                t_x[jj] = W.node_x[off + j0 + jj];
+                t_u[jj] = W.node_u[off + j0 + jj];
             }
-            const bool anyneg = __syncthreads_or(neg) != 0;
-            if (pend0 > 0 && !anyneg) {
-                int loc[4], acc = 0;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    acc += n[i] - 1;
-                    loc[i] = acc;
-                }
-                // block exclusive scan of the threads' sums
-                int x = acc;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                if (lane == 31) s_wsum[wid] = x;
-                if (tid == 0) s_end = cnt;
-                __syncthreads();
-                int wbase = 0;
-                for (int q = 0; q < wid; ++q) wbase += s_wsum[q];
-                const int excl = pend0 + wbase + x - acc;   // pending count before this thread's first node
-                int first = cnt;
-#pragma unroll
-                for (int i = 3; i >= 0; --i)
-                    if (4 * tid + i < cnt && excl + loc[i] <= 0) first = 4 * tid + i;
-                if (first < cnt) atomicMin(&s_end, first);
-                __syncthreads();
-                const int end = s_end;   // last node of the chain in this tile, or cnt
-                double part = 0.0;
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (4 * tid + i < cnt && 4 * tid + i <= end) part += (double)(uw * g[i] * uib);
-                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-                if (lane == 0) s_wpart[wid] = part;
-                __syncthreads();
-                if (tid == 0) {
-                    double t = 0.0;
-                    int tot = 0;
-                    for (int q = 0; q < WF_LONG_THREADS / 32; ++q) {
-                        t += s_wpart[q];
-                        tot += s_wsum[q];
-                    }
-                    s_sum += t;
-                    if (end < cnt) {
-                        s_next += end + 1;
-                        s_done = 1;
-                    } else {
-                        s_next += cnt;
-                        s_pend = pend0 + tot;
-                    }
-                }
-                __syncthreads();
-                continue;
-            }
-            // the exact walk of this tile on the stack form: the block stages the
-            // tile (g and children under the estimate's own bound), thread 0 walks it
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int jj = 4 * tid + i;
-                if (jj < cnt) {
-                    t_g[jj] = W.node_g[off + j0 + jj];
-                    t_n[jj] = W.node_n[off + j0 + jj];
-                    t_x[jj] = W.node_x[off + j0 + jj];
-                    t_u[jj] = W.node_u[off + j0 + jj];
-                }
-            }
+            if (tid == 0) s_pos = 0;
             __syncthreads();
-            if (tid == 0) {
-                if (pend0 > 0) est_from_uniform(sst, pend0, uw, uib);   // from the count form
-                int next = s_next, done = 0, trunc = 0;
-                double sum_t = s_sum;
-                walk_seq_arr(P, sst, t_g, t_n, t_x, t_u, cnt, invB, next, sum_t, done, trunc);
-                s_next = next;
-                s_sum = sum_t;
-                s_done = done;
-                s_trunc = trunc;
-                // back to the count form when the stack turned uniform again
-                int pe;
-                float w2, ib2;
-                s_pend = est_uniform_form(sst, w2, ib2, pe) ? pe : -1;
-                s_w = w2;
-                s_ib = ib2;
+            for (;;) {
+                const int pos = s_pos;
+                if (pos >= cnt || s_done) break;
+                const int pend0 = s_pend;
+                if (pend0 > 0) {
+                    // the uniform form: g and children of this thread's nodes under the shared bound
+                    const float uw = s_w, uib = s_ib;
+                    const int base_v = s_next - pos;   // pre-order index of tile node 0
+                    float g[4];
+                    int n[4];
+                    int brk = cnt;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int jj = 4 * tid + i;
+                        g[i] = 1.0f;
+                        n[i] = 1;
+                        if (jj >= pos && jj < cnt) {
+                            est_gn(t_x[jj], t_u[jj], t_g[jj], t_n[jj], invB, uib, (uint32_t)(base_v + jj), P.split,
+                                   g[i], n[i]);
+                            if (g[i] < 0.0f && jj < brk) brk = jj;
+                        }
+                    }
+                    if (tid == 0) {
+                        s_brk = cnt;
+                        s_end = cnt;
+                    }
+                    __syncthreads();
+                    if (brk < cnt) atomicMin(&s_brk, brk);
+                    __syncthreads();
+                    const int b = s_brk;   // the run is [pos, b)
+                    if (b < cnt && b - pos < 64) {
+                        // a short run: thread 0 walks it and its breaking node on the stack form
+                        if (tid == 0) {
+                            est_from_uniform(sst, pend0, uw, uib);
+                            int next = s_next, done = 0, trunc = 0;
+                            double sum_t = s_sum;
+                            walk_seq_arr(P, sst, t_g + pos, t_n + pos, t_x + pos, t_u + pos, b - pos + 1, invB, next,
+                                         sum_t, done, trunc);
+                            s_next = next;
+                            s_sum = sum_t;
+                            s_done = done;
+                            s_trunc = trunc;
+                            int pe = -1;
+                            float w2 = 1.0f, ib2 = invB;
+                            s_pend = (!done && est_uniform_form(sst, w2, ib2, pe)) ? pe : -1;
+                            s_w = w2;
+                            s_ib = ib2;
+                            s_pos = b + 1;
+                        }
+                        __syncthreads();
+                        continue;
+                    }
+                    int loc[4], acc = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int jj = 4 * tid + i;
+                        if (jj >= pos && jj < b) acc += n[i] - 1;
+                        loc[i] = acc;
+                    }
+                    int x = acc;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    if (lane == 31) s_wsum[wid] = x;
+                    __syncthreads();
+                    int wbase = 0;
+                    for (int q = 0; q < wid; ++q) wbase += s_wsum[q];
+                    const int excl = pend0 + wbase + x - acc;   // pending count before this thread's first node
+                    int first = cnt;
+#pragma unroll
+                    for (int i = 3; i >= 0; --i) {
+                        const int jj = 4 * tid + i;
+                        if (jj >= pos && jj < b && excl + loc[i] <= 0) first = jj;
+                    }
+                    if (first < cnt) atomicMin(&s_end, first);
+                    __syncthreads();
+                    const int end = s_end;   // last node of the chain in the run, or cnt
+                    const int stop = min(b, end + 1);   // nodes [pos, stop) are taken
+                    double part = 0.0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int jj = 4 * tid + i;
+                        if (jj >= pos && jj < stop) part += (double)(uw * g[i] * uib);
+                    }
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    if (lane == 0) s_wpart[wid] = part;
+                    __syncthreads();
+                    if (tid == 0) {
+                        double t = 0.0;
+                        int tot = 0;
+                        for (int q = 0; q < WF_LONG_THREADS / 32; ++q) {
+                            t += s_wpart[q];
+                            tot += s_wsum[q];
+                        }
+                        s_sum += t;
+                        s_next += stop - pos;
+                        if (end < b) {
+                            s_done = 1;
+                        } else {
+                            s_pend = pend0 + tot;
+                            if (b < cnt) {
+                                // the breaking node, on the stack form
+                                est_from_uniform(sst, s_pend, uw, uib);
+                                int next = s_next, done = 0, trunc = 0;
+                                double sum_t = s_sum;
+                                walk_seq_arr(P, sst, t_g + b, t_n + b, t_x + b, t_u + b, 1, invB, next, sum_t, done,
+                                             trunc);
+                                s_next = next;
+                                s_sum = sum_t;
+                                s_done = done;
+                                s_trunc = trunc;
+                                int pe;
+                                float w2, ib2;
+                                s_pend = est_uniform_form(sst, w2, ib2, pe) ? pe : -1;
+                                s_w = w2;
+                                s_ib = ib2;
+                            }
+                        }
+                        s_pos = b < cnt ? b + 1 : cnt;
+                    }
+                    __syncthreads();
+                } else {
+                    // the stack form: thread 0 walks node by node until the form is uniform again
+                    if (tid == 0) {
+                        int next = s_next, done = 0, trunc = 0, q = pos;
+                        double sum_t = s_sum;
+                        int pe = -1;
+                        float w2 = 1.0f, ib2 = invB;
+                        while (q < cnt && !done) {
+                            walk_seq_arr(P, sst, t_g + q, t_n + q, t_x + q, t_u + q, 1, invB, next, sum_t, done,
+                                         trunc);
+                            ++q;
+                            if (!done && est_uniform_form(sst, w2, ib2, pe)) break;
+                            pe = -1;
+                        }
+                        s_next = next;
+                        s_sum = sum_t;
+                        s_done = done;
+                        s_trunc = trunc;
+                        s_pend = done ? -1 : pe;
+                        s_w = w2;
+                        s_ib = ib2;
+                        s_pos = q;
+                    }
+                    __syncthreads();
+                }
             }
-            __syncthreads();
         }
         if (tid == 0) {
             int done = s_done, trunc = s_trunc;
