@@ -259,6 +259,47 @@ __device__ __forceinline__ void est_from_uniform(St &st, int pend, float w, floa
         st.sp = 1;
     }
 }
+// The top region of the walk state: the current node and the frames on top
+// that share its weight w and inverse bound ib. Until those pending nodes and
+// their descendants are walked, the frames below are not touched, so a run of
+// nodes with g >= 0 under ib is a pending-count walk of the region alone.
+// est_take_top removes the region from the stack and returns its pending
+// count; est_put_top pushes it back (one frame, which differs from the frame
+// below it); est_pop_below moves to the first pending node under an exhausted
+// region (false: none is left, the chain has ended).
+template <class St>
+__device__ __forceinline__ int est_take_top(St &st, float &w, float &ib) {
+    w = st.cur_sign;
+    ib = st.cur_ib;
+    int pend = 1;
+    while (st.sp > 0 && st.fr_sign[st.sp - 1] == w && st.fr_ib[st.sp - 1] == ib) {
+        pend += st.fr_rem[st.sp - 1];
+        st.sp--;
+    }
+    return pend;
+}
+// (false: the region needs a frame beyond CAP, a truncated estimate)
+template <int CAP, class St>
+__device__ __forceinline__ bool est_put_top(St &st, int pend, float w, float ib) {
+    st.cur_sign = w;
+    st.cur_ib = ib;
+    if (pend - 1 > 0) {
+        if (st.sp >= CAP) return false;
+        st.fr_sign[st.sp] = w;
+        st.fr_ib[st.sp] = ib;
+        st.fr_rem[st.sp] = pend - 1;
+        st.sp++;
+    }
+    return true;
+}
+template <class St>
+__device__ __forceinline__ bool est_pop_below(St &st) {
+    if (st.sp == 0) return false;
+    st.cur_sign = st.fr_sign[st.sp - 1];
+    st.cur_ib = st.fr_ib[st.sp - 1];
+    if (--st.fr_rem[st.sp - 1] == 0) st.sp--;
+    return true;
+}
 // g and children of a node under the inverse bound ib, as est_step computes
 // them (the values drawn under the estimate's own bound invB0 are reused)
 __device__ __forceinline__ void est_gn(float x, float u, float g0, int n0, float invB0, float ib, uint32_t v,

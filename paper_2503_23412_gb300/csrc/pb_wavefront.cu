@@ -589,24 +589,24 @@ __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
 
 // one block per chain whose window holds at least WF_WALK_LONG nodes, in
 // tiles of 1024 nodes staged in shared memory together with the chain's walk
-// state. While every pending node shares one weight and one bound (the
-// uniform count form), the run of tile nodes up to the first node with a
-// negative g under that bound is walked in parallel: a block scan of
-// (children - 1) gives each node's pending count, the chain ends at the first
-// node where it reaches 0, and the terms w g / B up to there are summed by a
-// block reduction. The node that breaks the run, and any stretch where the
-// pending nodes differ in weight or bound, are walked by thread 0 on the
-// stack form, node by node, until the form is uniform again.
+// state. The block works on the top region of the state (est_take_top): the
+// run of tile nodes up to the first node with a negative g under the region's
+// bound is walked in parallel, a block scan of (children - 1) giving each
+// node's pending count within the region; where that count reaches 0 the
+// region is exhausted, and the walk moves to the pending node below it (or the
+// chain ends). The terms w g / B of the run are summed by a block reduction.
+// A node with a negative g, and runs of fewer than 64 nodes before one, are
+// walked by thread 0 on the full stack.
 constexpr int WF_LONG_THREADS = 256;
 constexpr int WF_LONG_TILE = 4 * WF_LONG_THREADS;
 __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Pool B, WfBufs W) {
-    __shared__ ChainState sst;
+    __shared__ ChainState sst;   // the frames below the top region
     __shared__ float t_g[WF_LONG_TILE], t_x[WF_LONG_TILE], t_u[WF_LONG_TILE];
     __shared__ int32_t t_n[WF_LONG_TILE];
     __shared__ int s_wsum[WF_LONG_THREADS / 32];
     __shared__ double s_wpart[WF_LONG_THREADS / 32];
     __shared__ int s_end, s_brk, s_done, s_trunc, s_next, s_pend, s_pos;
-    __shared__ float s_w, s_ib;   // the uniform form's weight and inverse bound
+    __shared__ float s_w, s_ib;   // the top region: pending count, weight, inverse bound
     __shared__ double s_sum;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int items = W.ctl[WF_CTL_ITEMS];
@@ -620,9 +620,8 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
         const int slot = sst.slot, k = sst.k, rep = sst.rep;
         const float invB = 1.0f / B.eB[(size_t)slot * B.ML + k];
         if (tid == 0) {
-            int pend;
             float w0, ib0;
-            s_pend = est_uniform_form(sst, w0, ib0, pend) ? pend : -1;   // -1: the stack form holds the state
+            s_pend = est_take_top(sst, w0, ib0);
             s_w = w0;
             s_ib = ib0;
             s_next = sst.next;
@@ -647,149 +646,137 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
                 const int pos = s_pos;
                 if (pos >= cnt || s_done) break;
                 const int pend0 = s_pend;
-                if (pend0 > 0) {
-                    // the uniform form: g and children of this thread's nodes under the shared bound
-                    const float uw = s_w, uib = s_ib;
-                    const int base_v = s_next - pos;   // pre-order index of tile node 0
-                    float g[4];
-                    int n[4];
-                    int brk = cnt;
+                const float uw = s_w, uib = s_ib;
+                const int base_v = s_next - pos;   // pre-order index of tile node 0
+                float g[4];
+                int n[4];
+                int brk = cnt;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int jj = 4 * tid + i;
-                        g[i] = 1.0f;
-                        n[i] = 1;
-                        if (jj >= pos && jj < cnt) {
-                            est_gn(t_x[jj], t_u[jj], t_g[jj], t_n[jj], invB, uib, (uint32_t)(base_v + jj), P.split,
-                                   g[i], n[i]);
-                            if (g[i] < 0.0f && jj < brk) brk = jj;
-                        }
+                for (int i = 0; i < 4; ++i) {
+                    const int jj = 4 * tid + i;
+                    g[i] = 1.0f;
+                    n[i] = 1;
+                    if (jj >= pos && jj < cnt) {
+                        est_gn(t_x[jj], t_u[jj], t_g[jj], t_n[jj], invB, uib, (uint32_t)(base_v + jj), P.split, g[i],
+                               n[i]);
+                        if (g[i] < 0.0f && jj < brk) brk = jj;
                     }
+                }
+                if (tid == 0) {
+                    s_brk = cnt;
+                    s_end = cnt;
+                }
+                __syncthreads();
+                if (brk < cnt) atomicMin(&s_brk, brk);
+                __syncthreads();
+                const int b = s_brk;   // the run is [pos, b)
+                if (b < cnt && b - pos < 64) {
+                    // a short run: thread 0 walks it and its breaking node on the full stack
                     if (tid == 0) {
-                        s_brk = cnt;
-                        s_end = cnt;
-                    }
-                    __syncthreads();
-                    if (brk < cnt) atomicMin(&s_brk, brk);
-                    __syncthreads();
-                    const int b = s_brk;   // the run is [pos, b)
-                    if (b < cnt && b - pos < 64) {
-                        // a short run: thread 0 walks it and its breaking node on the stack form
-                        if (tid == 0) {
-                            est_from_uniform(sst, pend0, uw, uib);
-                            int next = s_next, done = 0, trunc = 0;
-                            double sum_t = s_sum;
+                        int next = s_next, done = 0, trunc = 0;
+                        double sum_t = s_sum;
+                        if (est_put_top<PB_MAXF>(sst, pend0, uw, uib))
                             walk_seq_arr(P, sst, t_g + pos, t_n + pos, t_x + pos, t_u + pos, b - pos + 1, invB, next,
                                          sum_t, done, trunc);
+                        else
+                            done = trunc = 1;
+                        s_next = next;
+                        s_sum = sum_t;
+                        s_done = done;
+                        s_trunc = trunc;
+                        if (!done) {
+                            float w2, ib2;
+                            s_pend = est_take_top(sst, w2, ib2);
+                            s_w = w2;
+                            s_ib = ib2;
+                        }
+                        s_pos = b + 1;
+                    }
+                    __syncthreads();
+                    continue;
+                }
+                int loc[4], acc = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int jj = 4 * tid + i;
+                    if (jj >= pos && jj < b) acc += n[i] - 1;
+                    loc[i] = acc;
+                }
+                int x = acc;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (lane == 31) s_wsum[wid] = x;
+                __syncthreads();
+                int wbase = 0;
+                for (int q = 0; q < wid; ++q) wbase += s_wsum[q];
+                const int excl = pend0 + wbase + x - acc;   // the region's pending count before this thread's first node
+                int first = cnt;
+#pragma unroll
+                for (int i = 3; i >= 0; --i) {
+                    const int jj = 4 * tid + i;
+                    if (jj >= pos && jj < b && excl + loc[i] <= 0) first = jj;
+                }
+                if (first < cnt) atomicMin(&s_end, first);
+                __syncthreads();
+                const int end = s_end;   // the node that exhausts the region, or cnt
+                const int stop = min(b, end + 1);   // nodes [pos, stop) are taken
+                double part = 0.0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int jj = 4 * tid + i;
+                    if (jj >= pos && jj < stop) part += (double)(uw * g[i] * uib);
+                }
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (lane == 0) s_wpart[wid] = part;
+                __syncthreads();
+                if (tid == 0) {
+                    double t = 0.0;
+                    int tot = 0;
+                    for (int q = 0; q < WF_LONG_THREADS / 32; ++q) {
+                        t += s_wpart[q];
+                        tot += s_wsum[q];
+                    }
+                    s_sum += t;
+                    s_next += stop - pos;
+                    if (end < b) {
+                        // the region is exhausted: the next node is the first pending one below it
+                        if (!est_pop_below(sst)) {
+                            s_done = 1;
+                        } else {
+                            float w2, ib2;
+                            s_pend = est_take_top(sst, w2, ib2);
+                            s_w = w2;
+                            s_ib = ib2;
+                        }
+                        s_pos = end + 1;
+                    } else {
+                        s_pend = pend0 + tot;
+                        if (b < cnt) {
+                            // the breaking node, on the full stack
+                            int next = s_next, done = 0, trunc = 0;
+                            double sum_t = s_sum;
+                            if (est_put_top<PB_MAXF>(sst, s_pend, uw, uib))
+                                walk_seq_arr(P, sst, t_g + b, t_n + b, t_x + b, t_u + b, 1, invB, next, sum_t, done,
+                                             trunc);
+                            else
+                                done = trunc = 1;
                             s_next = next;
                             s_sum = sum_t;
                             s_done = done;
                             s_trunc = trunc;
-                            int pe = -1;
-                            float w2 = 1.0f, ib2 = invB;
-                            s_pend = (!done && est_uniform_form(sst, w2, ib2, pe)) ? pe : -1;
-                            s_w = w2;
-                            s_ib = ib2;
-                            s_pos = b + 1;
-                        }
-                        __syncthreads();
-                        continue;
-                    }
-                    int loc[4], acc = 0;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int jj = 4 * tid + i;
-                        if (jj >= pos && jj < b) acc += n[i] - 1;
-                        loc[i] = acc;
-                    }
-                    int x = acc;
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, x, o);
-                        if (lane >= o) x += y;
-                    }
-                    if (lane == 31) s_wsum[wid] = x;
-                    __syncthreads();
-                    int wbase = 0;
-                    for (int q = 0; q < wid; ++q) wbase += s_wsum[q];
-                    const int excl = pend0 + wbase + x - acc;   // pending count before this thread's first node
-                    int first = cnt;
-#pragma unroll
-                    for (int i = 3; i >= 0; --i) {
-                        const int jj = 4 * tid + i;
-                        if (jj >= pos && jj < b && excl + loc[i] <= 0) first = jj;
-                    }
-                    if (first < cnt) atomicMin(&s_end, first);
-                    __syncthreads();
-                    const int end = s_end;   // last node of the chain in the run, or cnt
-                    const int stop = min(b, end + 1);   // nodes [pos, stop) are taken
-                    double part = 0.0;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int jj = 4 * tid + i;
-                        if (jj >= pos && jj < stop) part += (double)(uw * g[i] * uib);
-                    }
-                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-                    if (lane == 0) s_wpart[wid] = part;
-                    __syncthreads();
-                    if (tid == 0) {
-                        double t = 0.0;
-                        int tot = 0;
-                        for (int q = 0; q < WF_LONG_THREADS / 32; ++q) {
-                            t += s_wpart[q];
-                            tot += s_wsum[q];
-                        }
-                        s_sum += t;
-                        s_next += stop - pos;
-                        if (end < b) {
-                            s_done = 1;
-                        } else {
-                            s_pend = pend0 + tot;
-                            if (b < cnt) {
-                                // the breaking node, on the stack form
-                                est_from_uniform(sst, s_pend, uw, uib);
-                                int next = s_next, done = 0, trunc = 0;
-                                double sum_t = s_sum;
-                                walk_seq_arr(P, sst, t_g + b, t_n + b, t_x + b, t_u + b, 1, invB, next, sum_t, done,
-                                             trunc);
-                                s_next = next;
-                                s_sum = sum_t;
-                                s_done = done;
-                                s_trunc = trunc;
-                                int pe;
+                            if (!done) {
                                 float w2, ib2;
-                                s_pend = est_uniform_form(sst, w2, ib2, pe) ? pe : -1;
+                                s_pend = est_take_top(sst, w2, ib2);
                                 s_w = w2;
                                 s_ib = ib2;
                             }
                         }
                         s_pos = b < cnt ? b + 1 : cnt;
                     }
-                    __syncthreads();
-                } else {
-                    // the stack form: thread 0 walks node by node until the form is uniform again
-                    if (tid == 0) {
-                        int next = s_next, done = 0, trunc = 0, q = pos;
-                        double sum_t = s_sum;
-                        int pe = -1;
-                        float w2 = 1.0f, ib2 = invB;
-                        while (q < cnt && !done) {
-                            walk_seq_arr(P, sst, t_g + q, t_n + q, t_x + q, t_u + q, 1, invB, next, sum_t, done,
-                                         trunc);
-                            ++q;
-                            if (!done && est_uniform_form(sst, w2, ib2, pe)) break;
-                            pe = -1;
-                        }
-                        s_next = next;
-                        s_sum = sum_t;
-                        s_done = done;
-                        s_trunc = trunc;
-                        s_pend = done ? -1 : pe;
-                        s_w = w2;
-                        s_ib = ib2;
-                        s_pos = q;
-                    }
-                    __syncthreads();
                 }
+                __syncthreads();
             }
         }
         if (tid == 0) {
@@ -799,7 +786,10 @@ __global__ void __launch_bounds__(WF_LONG_THREADS) k_wf_walk_long(KParams P, Poo
                 done = 1;
                 trunc = 1;
             }
-            if (s_pend > 0) est_from_uniform(sst, s_pend, s_w, s_ib);   // store the count form as a one-frame stack
+            if (!s_done && !est_put_top<PB_MAXF>(sst, s_pend, s_w, s_ib)) {   // the full stack again
+                done = 1;
+                trunc = 1;
+            }
             sst.next = next;
             sst.sum_t = s_sum;
             gst = sst;
