@@ -516,7 +516,8 @@ def test_gpu_proxy_on_off_and_pt_agree(N):
     # A truncated chain is a biased estimate. A few entries per thousand
     # iterations have an integrand whose f > 0 on a set the pilot never hits
     # (B falls back to the learned cell value) and need chains beyond 2^20
-    # nodes; they must stay that rare.
+    # nodes; they must stay that rare. (A cap of 2^22 still left 5 of
+    # 545,090 entries truncated: their chains are not merely long.)
     assert n_tr <= 2e-4 * max(n_est, 1), (n_tr, n_est)
     for a in ("on", "off"):
         m, s = out[a]
