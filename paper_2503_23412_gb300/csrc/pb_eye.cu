@@ -526,21 +526,15 @@ __global__ void __launch_bounds__(128, 4) k_eye(DScene S, DTables T, KParams P, 
 // network's input row, eye subspace and dense index of every vertex where
 // k_eye makes a subspace connection (row order is arbitrary; each row's
 // result depends on its own content only).
-// A block takes a 16 x 8 pixel tile, a warp an 8 x 4 quarter of it, so that the
-// camera paths of a warp start from neighbouring pixels in both directions.
-constexpr int FEAT_TW = 16, FEAT_TH = 8;
 template <bool COUNT>
 __global__ void __launch_bounds__(128, 8) k_eye_feat(DScene S, DTables T, KParams P, Pool B, uint32_t iter_base) {
     iter_base = eff_iter(P, iter_base);
     TravCount tc{0, 0, 0};
-    const int tiles_x = (S.W + FEAT_TW - 1) / FEAT_TW;
-    const int wq = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    const int px = (blockIdx.x % tiles_x) * FEAT_TW + (wq & 1) * 8 + (ln & 7);
-    const int py = (blockIdx.x / tiles_x) * FEAT_TH + (wq >> 1) * 4 + (ln >> 3);
+    int pix = blockIdx.x * blockDim.x + threadIdx.x;
     int slot = blockIdx.y;
-    if (px >= S.W || py >= S.H) return;
-    const int pix = py * S.W + px;
+    if (pix >= P.npix) return;
     uint32_t it = iter_base + (uint32_t)slot;
+    int px = pix % S.W, py = pix / S.W;
     Rng r0;
     r0.init(P.seed, K_CAMERA, it, (uint32_t)pix, 0);
     float j0 = r0.u(0), j1 = r0.u(1);
@@ -749,7 +743,7 @@ void launch_eye_occ(const DScene &S, const KParams &P, const Pool &B, int num_sm
 // refilled lanes lose the coherence of neighbouring camera paths.
 void launch_eye_feat(const DScene &S, const DTables &T, const KParams &P, const Pool &B, int slots, uint32_t iter_base,
                      cudaStream_t st) {
-    dim3 grid(((S.W + FEAT_TW - 1) / FEAT_TW) * ((S.H + FEAT_TH - 1) / FEAT_TH), slots);
+    dim3 grid((P.npix + 127) / 128, slots);
     if (P.count) k_eye_feat<true><<<grid, 128, 0, st>>>(S, T, P, B, iter_base);
     else k_eye_feat<false><<<grid, 128, 0, st>>>(S, T, P, B, iter_base);
 }
