@@ -474,11 +474,12 @@ __device__ __forceinline__ void walk_seq(const KParams &P, const WfBufs &W, Chai
 // windows at least this long are walked by a whole block (k_wf_walk_long)
 constexpr int WF_WALK_LONG = 8192;
 
-// one warp per chain: the walk over this round's window in chunks of 32
-// nodes. While every pending node has sign +1 and the chunk has no negative
-// g, the walk reduces to counts (pending_v = pending - 1 + n_v; the chain
-// ends at the first node where pending reaches 0), a warp scan; otherwise
-// lane 0 replays the exact sequential walk over the chunk.
+// one warp per chain: the walk over this round's window (below WF_WALK_LONG
+// nodes) in chunks of 32. While every pending node shares one weight and one
+// bound (est_uniform_form) and the chunk has no negative g under that bound,
+// the walk reduces to counts (pending_v = pending - 1 + n_v; the chain ends
+// at the first node where pending reaches 0), a warp scan; otherwise lane 0
+// replays the exact sequential walk over the chunk.
 __global__ void __launch_bounds__(128) k_wf_walk(KParams P, Pool B, WfBufs W) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
