@@ -17,7 +17,8 @@ namespace {
 // nodes are evaluated grouped by the branch their first uniforms select
 // (mixture component, side of the lens), so that whole warps trace alike;
 // the walk still consumes them in pre-order. While every pending node has
-// sign +1 and the batch has no negative g, the walk reduces to counts:
+// weight +1 under the estimate's own bound and the batch has no negative g,
+// the walk reduces to counts:
 // pending_v = pending - 1 + n_v per node, the chain ends at the first node
 // where pending reaches 0, and the estimate adds g_v / B for the nodes up to
 // there -- a block prefix sum. Otherwise one thread replays the exact
