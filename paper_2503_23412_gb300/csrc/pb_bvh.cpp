@@ -250,7 +250,9 @@ struct Ref {
 };
 struct TNode {
     Ref ch[2];
+    int size;   // internal nodes of the subtree, this one included
 };
+inline int subtree_size(const Ref &c) { return c.ar ? c.ar->v[c.ix].size : 0; }
 
 struct Arenas {
     std::mutex mu;
@@ -297,6 +299,7 @@ Ref build(Build &b, Arenas &as, Arena *ar, int first, int count, int depth) {
         nd.ch[0] = build(b, as, ar, first, m - first, depth + 1);
         nd.ch[1] = build(b, as, ar, m, first + count - m, depth + 1);
     }
+    nd.size = 1 + subtree_size(nd.ch[0]) + subtree_size(nd.ch[1]);
     ar->v.push_back(nd);
     r.code = 0;
     r.ar = ar;
@@ -321,18 +324,24 @@ void set_child(Emit &e, int node, int side, const Box &bx, int32_t code) {
     *w = code;
 }
 
-// numbers internal nodes in pre-order and writes the 64-byte layout
-int emit(Emit &e, const TNode &nd, int parent) {
-    const int id = (int)e.parent.size();
-    e.nodes.resize(e.nodes.size() + 16, 0.0f);
-    e.parent.push_back(parent);
-    e.sibling.push_back(-1);
-    for (int s = 0; s < 2; ++s) {
-        const Ref &c = nd.ch[s];
-        const int32_t code = c.ar ? emit(e, c.ar->v[c.ix], id) : c.code;
-        set_child(e, id, s, c.box, code);
+// Writes the 64-byte layout of the subtree whose root gets index id, in
+// pre-order: the left child (if internal) is id + 1, the right one follows
+// the left subtree. Subtrees of large nodes near the root are written on
+// their own threads; the indices do not depend on the order of writing.
+constexpr int EMIT_PAR = 1 << 14;
+void emit(Emit &e, const TNode &nd, int id, int parent, int depth) {
+    e.parent[id] = parent;
+    const int ids[2] = {id + 1, id + 1 + subtree_size(nd.ch[0])};
+    for (int s = 0; s < 2; ++s) set_child(e, id, s, nd.ch[s].box, nd.ch[s].ar ? ids[s] : nd.ch[s].code);
+    const Ref &l = nd.ch[0], &r = nd.ch[1];
+    if (l.ar && r.ar && depth < 5 && nd.size >= EMIT_PAR) {
+        std::thread t([&]() { emit(e, l.ar->v[l.ix], ids[0], id, depth + 1); });
+        emit(e, r.ar->v[r.ix], ids[1], id, depth + 1);
+        t.join();
+        return;
     }
-    return id;
+    if (l.ar) emit(e, l.ar->v[l.ix], ids[0], id, depth + 1);
+    if (r.ar) emit(e, r.ar->v[r.ix], ids[1], id, depth + 1);
 }
 
 }  // namespace
@@ -358,7 +367,6 @@ int pb_bvh_build(const float *verts, int nv, const int32_t *tris, int nt, PbBvh 
         }
     });
     Emit e;
-    e.nodes.reserve(16 * (size_t)std::max(1, nt / 2));
     // the root is always an internal node; its children come from splitting all triangles
     Arenas as;
     Arena *root_ar = as.make();
@@ -370,7 +378,11 @@ int pb_bvh_build(const float *verts, int nv, const int32_t *tris, int nt, PbBvh 
         set_child(e, 0, 0, root.box, leaf_code(0, nt));
         set_child(e, 0, 1, Box(), leaf_code(0, 0));
     } else {
-        emit(e, root.ar->v[root.ix], -1);
+        const TNode &rn = root.ar->v[root.ix];
+        e.nodes.assign(16 * (size_t)rn.size, 0.0f);
+        e.parent.assign((size_t)rn.size, -1);
+        e.sibling.assign((size_t)rn.size, -1);
+        emit(e, rn, 0, -1, 0);
     }
     int nn = (int)(e.nodes.size() / 16);
     // sibling of each internal child
