@@ -24,6 +24,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -77,8 +78,13 @@ void par_parts(int parts, int n, F f) {
         return;
     }
     std::vector<std::thread> th;
-    for (int q = 1; q < parts; ++q)
-        th.emplace_back(f, q, (int)((int64_t)n * q / parts), (int)((int64_t)n * (q + 1) / parts));
+    int q = 1;
+    try {
+        for (; q < parts; ++q)
+            th.emplace_back(f, q, (int)((int64_t)n * q / parts), (int)((int64_t)n * (q + 1) / parts));
+    } catch (const std::system_error &) {   // no thread to be had: the remaining parts run here
+    }
+    for (int r = q; r < parts; ++r) f(r, (int)((int64_t)n * r / parts), (int)((int64_t)n * (r + 1) / parts));
     f(0, 0, (int)((int64_t)n / parts));
     for (auto &t : th) t.join();
 }
@@ -285,12 +291,20 @@ Ref build(Build &b, Arenas &as, Arena *ar, int first, int count, int depth) {
         }
         spawn = cur < b.nth;
     }
+    std::thread t;
     if (spawn) {
         Arena *la = as.make();
-        std::thread t([&]() {
-            nd.ch[0] = build(b, as, la, first, m - first, depth + 1);
+        try {
+            t = std::thread([&nd, &b, &as, la, first, m, depth]() {
+                nd.ch[0] = build(b, as, la, first, m - first, depth + 1);
+                b.running.fetch_sub(1);
+            });
+        } catch (const std::system_error &) {   // no thread to be had: build both sides here
             b.running.fetch_sub(1);
-        });
+            spawn = false;
+        }
+    }
+    if (spawn) {
         nd.ch[1] = build(b, as, ar, m, first + count - m, depth + 1);
         b.running.fetch_sub(1);   // idle while it waits
         t.join();
@@ -335,10 +349,16 @@ void emit(Emit &e, const TNode &nd, int id, int parent, int depth) {
     for (int s = 0; s < 2; ++s) set_child(e, id, s, nd.ch[s].box, nd.ch[s].ar ? ids[s] : nd.ch[s].code);
     const Ref &l = nd.ch[0], &r = nd.ch[1];
     if (l.ar && r.ar && depth < 5 && nd.size >= EMIT_PAR) {
-        std::thread t([&]() { emit(e, l.ar->v[l.ix], ids[0], id, depth + 1); });
-        emit(e, r.ar->v[r.ix], ids[1], id, depth + 1);
-        t.join();
-        return;
+        std::thread t;
+        try {
+            t = std::thread([&e, &l, &ids, id, depth]() { emit(e, l.ar->v[l.ix], ids[0], id, depth + 1); });
+        } catch (const std::system_error &) {   // no thread to be had: write both sides here
+        }
+        if (t.joinable()) {
+            emit(e, r.ar->v[r.ix], ids[1], id, depth + 1);
+            t.join();
+            return;
+        }
     }
     if (l.ar) emit(e, l.ar->v[l.ix], ids[0], id, depth + 1);
     if (r.ar) emit(e, r.ar->v[r.ix], ids[1], id, depth + 1);
