@@ -147,10 +147,10 @@ typedef struct {
      * schedule only (estimator 0; PB_ERR_ARG otherwise); table learning
      * always uses the paper's function. */
     float booth;
-    /* How the wavefront estimator's trace stages map queries to threads: 0 =
-     * one query per thread; 1 = persistent warps whose lanes take the next
-     * query as soon as theirs is answered (ray replacement). The answers are
-     * the same either way. */
+    /* How the wavefront estimator's trace stages and the eye pass's
+     * occlusion answers map queries to threads: 0 = one query per thread;
+     * 1 = persistent warps whose lanes take the next query as soon as theirs
+     * is answered (ray replacement). The answers are the same either way. */
     int trace;
     /* Strategies whose weighted contributions reach the film: 0 = all; 1 =
      * only the proxy strategy (the paper's subspace-selection comparison
